@@ -1,0 +1,338 @@
+"""Benchmark of the slicing hot path on GB300.
+
+One step = one pass of the whole path over the workload: bin, evaluate the
+field on every pixel of every layer, threshold, trace and stitch the contours
+(contours stay in device memory). The default workload is the adaptive graded
+lattice of about 100M struts (4000 x 4000 pixels of 0.05 mm, 1000 layers).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cslice|reference]
+
+Prints one JSON line (rank 0). Under torchrun, every rank slices its own
+1000 layers (the job's layers shifted by r dz / N: the ranks together slice
+the part at N times the layer resolution), so per-GPU work is fixed (weak
+scaling) and no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel-evals/s and layers/s at 10M and 100M struts; backward/forward time ratio"
+F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the field kernel
+N_SM = 152
+FP32_LANES = 128
+MAX_SM_MHZ = 2070.0
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- workload
+
+def workload(name):
+    import synth
+    if name == "graded-100M":
+        return synth.config(3)
+    if name == "graded-10M":
+        nodes, edges, radius, r_ref = synth.adaptive_graded(box=100.0, level_min=4, level_max=7)
+        return dict(name=f"adaptive graded lattice, {edges.shape[0]} struts, 2000^2 px x 500 "
+                         "layers", nodes=nodes, edges=edges, radius=radius, R=1.5 * r_ref, C=1.0,
+                    x0=0.0, y0=0.0, nx=2000, ny=2000, pixel=0.05, z0=0.1, dz=0.2, n_layers=500)
+    if name == "freudenthal-430k":
+        return synth.config(2)
+    if name == "cubic-bcc-812":
+        return synth.config(1)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def slice_kwargs(cfg, rank, world):
+    z0 = cfg["z0"] + cfg["dz"] * rank / world
+    return dict(z0=z0, dz=cfg["dz"], n_layers=cfg["n_layers"], x0=cfg["x0"], y0=cfg["y0"],
+                nx=cfg["nx"], ny=cfg["ny"], pixel=cfg["pixel"])
+
+
+# --------------------------------------------------------------------------- oracle sample
+
+def oracle_sample(cfg, window=256, layer=None, min_seconds=8.0):
+    """Times the FP64 oracle (single thread) on a window of one layer: the
+    oracle gets the edges whose xy box grown by R meets the window and whose
+    z range grown by R contains the layer (its own Eq. 8 sweep then runs)."""
+    import oracle
+    nl = cfg["n_layers"]
+    layer = nl // 2 if layer is None else layer
+    z = cfg["z0"] + layer * cfg["dz"]
+    w = min(window, cfg["nx"], cfg["ny"])
+    i0 = (cfg["nx"] - w) // 2
+    j0 = (cfg["ny"] - w) // 2
+    px = cfg["pixel"]
+    wx0, wy0 = cfg["x0"] + i0 * px, cfg["y0"] + j0 * px
+    R = cfg["R"]
+    nodes, edges = cfg["nodes"], cfg["edges"]
+    a = nodes[edges[:, 0]].astype(np.float64)
+    b = nodes[edges[:, 1]].astype(np.float64)
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    keep = ((lo[:, 2] - R <= z) & (hi[:, 2] + R >= z) & (hi[:, 0] + R >= wx0)
+            & (lo[:, 0] - R <= wx0 + w * px) & (hi[:, 1] + R >= wy0) & (lo[:, 1] - R <= wy0 + w * px))
+    sel = np.nonzero(keep)[0]
+    used = np.unique(edges[sel])
+    remap = np.full(nodes.shape[0], -1, np.int64)
+    remap[used] = np.arange(used.size)
+    sub_nodes = nodes[used]
+    sub_edges = remap[edges[sel]].astype(np.int32)
+    sub_r = cfg["radius"][sel]
+    rows = w
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle.slice_sigma(sub_nodes, sub_edges, sub_r, R=R, C=cfg["C"], z0=z, dz=cfg["dz"],
+                           n_layers=1, x0=wx0, y0=wy0 + done * px, nx=w, ny=rows, pixel=px)
+        done += rows
+        el = time.perf_counter() - t0
+        if el >= min_seconds or done >= 4 * w:
+            break
+    t = time.perf_counter() - t0
+    evals = done * w
+    return {"value": evals / t, "unit": "pixel-evals/s", "cores": 1, "kind": "oracle",
+            "seconds": t,
+            "sample": f"{done}x{w} pixels of layer {layer} (z={z:.2f} mm), "
+                      f"{sel.size} edges meeting the window given to the oracle"}
+
+
+# --------------------------------------------------------------------------- main
+
+def run_reference(args, cfg, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        oracle_sample(cfg, window=64, min_seconds=0.5)
+    for _ in range(args.steps):
+        steps.append(oracle_sample(cfg, window=128, min_seconds=3.0))
+    v = float(np.mean([s["value"] for s in steps]))
+    t_step = float(np.mean([s["seconds"] for s in steps]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pixel-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "parallelism": "single host thread"},
+            "cpu_baseline": {"value": v, "unit": "pixel-evals/s", "cores": 1, "kind": "oracle",
+                             "sample": steps[0]["sample"]},
+            "e2e": {"value": v, "unit": "pixel-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cslice", choices=["cslice", "reference"])
+    ap.add_argument("--workload", default="graded-100M")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        cfg = workload(args.workload) if rank == 0 else None
+        run_reference(args, cfg, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import paper_2101_05031_gb300 as cs
+    cs.load()
+    t_gen = time.perf_counter()
+    cfg = workload(args.workload)
+    t_gen = time.perf_counter() - t_gen
+    kw = slice_kwargs(cfg, rank, world)
+    stream = torch.cuda.current_stream()
+
+    t_up = time.perf_counter()
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    t_up = time.perf_counter() - t_up
+
+    def step(flags_time=False):
+        c = lat.slice(**kw, on_device=True, time_kernels=flags_time)
+        st = cs.last_stats()
+        n = (c.n_loops, c.n_verts)
+        c.free()
+        return st, n
+
+    for _ in range(args.warmup):
+        step()
+    # exact count of nonzero terms, once, outside the timed region
+    lat.slice(**kw, contours=False, count_pairs=True)
+    pairs = cs.last_stats().contributing_pairs
+    cand = cs.last_stats().candidate_pairs
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    field_ms = 0.0
+    field_launches = 0
+    launches = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, (n_loops, n_verts) = step(flags_time=True)
+            field_ms += st.field_ms
+            field_launches += st.field_launches
+            launches += st.kernel_launches
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    px_per_step = cfg["nx"] * cfg["ny"] * cfg["n_layers"]
+    value = px_per_step * args.steps * world / (t_max / 1e3)
+    layers_per_s = cfg["n_layers"] * args.steps * world / (t_max / 1e3)
+    clocks = clk.summary()
+
+    # roofline of the field kernel: FP32 ALU
+    t_field = field_ms / max(field_launches, 1) / 1e3            # s per launch
+    flops_per_launch = pairs * F_PAIR / max(field_launches // args.steps, 1)
+    achieved = flops_per_launch / t_field / 1e12 if t_field > 0 else 0.0
+    peak = N_SM * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_field", "flops_per_term": F_PAIR,
+            "nonzero_terms_per_step": pairs, "candidate_entries_per_step": cand,
+            "field_share_of_step": field_ms / ms if ms > 0 else None,
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_observed_clock"] = achieved / (peak * clocks["sm_mhz"] / MAX_SM_MHZ)
+
+    line = {"metric": METRIC, "value": value, "unit": "pixel-evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "layers_per_s": layers_per_s,
+            "config": {"workload": cfg["name"], "struts": int(cfg["edges"].shape[0]),
+                       "pixel_mm": cfg["pixel"], "layers": cfg["n_layers"],
+                       "l2": "inputs larger than L2 (32-byte records x struts)",
+                       "parallelism": f"{world} GPU(s), layers offset per rank"},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+            "contours_per_step": {"loops": n_loops, "vertices": n_verts},
+            "setup_s": {"generate": t_gen, "upload_and_sort": t_up}}
+
+    if not args.no_e2e:
+        # end to end through the public API: pinned host inputs, upload + prepare,
+        # slice, contours copied back to host memory
+        pn = torch.from_numpy(cfg["nodes"]).pin_memory()
+        pe = torch.from_numpy(cfg["edges"]).pin_memory()
+        pr = torch.from_numpy(cfg["radius"]).pin_memory()
+        h2d = pn.numel() * 4 + pe.numel() * 4 + pr.numel() * 4
+        barrier()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            L2 = cs.Lattice(pn, pe, pr, R=cfg["R"], C=cfg["C"])
+            cont = L2.slice(**kw)
+            d2h = cont.layer_loop_off.nbytes + cont.loop_vert_off.nbytes + cont.xy.nbytes
+            L2.close()
+            del cont
+        a1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = a0.elapsed_time(a1) / args.e2e_steps
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": px_per_step * world / (e2e_ms / 1e3), "unit": "pixel-evals/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": e2e_ms}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

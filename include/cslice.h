@@ -1,0 +1,211 @@
+/*
+ * cslice: slicing of convolution-surface lattices on one GPU (sm_103a).
+ *
+ * C ABI of libcslice.so. Plain pointers and sizes only; nothing throws across
+ * this boundary. Every call returns a csl_status; on failure
+ * csl_last_error() returns a message for the calling thread.
+ *
+ * The method (arxiv 2101.05031):
+ *   - lattice: graph of nodes v_i (float3) and edges e_j = (v_s, v_e, r_j)
+ *     (Sec. 3.1);
+ *   - field:  Sigma(p) = sum_j w_j * int_{e_j} f(p - x) de with the quartic
+ *     compact kernel f = (1 - |p - x|^2 / R^2)^2 inside radius R (Eq. 5, 6),
+ *     evaluated per edge in closed form (Eq. 7, arc-length measure);
+ *   - solid:  p is inside iff Sigma(p) >= C (the paper's F = -C + Sigma, with
+ *     its sign read so that the skeleton is inside);
+ *   - slicing: planes z_k = z0 + k dz, only edges whose swept sphere meets the
+ *     plane contribute (Eq. 8, Sec. 4 Steps 1-6); the binary image is traced by
+ *     marching squares into closed contours (Sec. 4, last paragraph);
+ *   - density: per-cell volume fraction of the solid (Eq. 9), here smoothed by
+ *     a sigmoid so that it can be differentiated for radius tuning (Sec. 5.4).
+ *
+ * Weight of an edge (csl_params.mode):
+ *   CSL_MODE_PHYSICAL  radius[j] is the physical strut radius rho_j and
+ *                      w_j = C * 15 R^4 / (16 (R^2 - rho_j^2)^(5/2)), which
+ *                      puts the iso-surface of an isolated long strut at
+ *                      distance rho_j; requires 0 < rho_j < R.
+ *   CSL_MODE_RAW       w_j = radius[j], the paper's r_i taken literally.
+ *
+ * Streams: every call enqueues its GPU work on the caller's CUDA stream
+ * (a cudaStream_t passed as void*; NULL = legacy default stream). Calls that
+ * return host data synchronise that stream before returning.
+ * Memory: the library allocates its own device memory with the stream-ordered
+ * allocator (cudaMallocAsync) on that stream and frees it the same way.
+ */
+#ifndef CSLICE_H
+#define CSLICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t csl_status;
+#define CSL_OK 0
+#define CSL_ERR_INVALID_ARG 1   /* bad pointer, size, index, NaN/Inf, radius out of range */
+#define CSL_ERR_OOM 2           /* a device or host allocation failed */
+#define CSL_ERR_CUDA 3          /* a CUDA runtime call or kernel failed */
+#define CSL_ERR_TIMEOUT 4       /* a bounded device-side wait gave up */
+#define CSL_ERR_CAPACITY 5      /* a count exceeded a fixed-size buffer or int range */
+#define CSL_ERR_NOT_READY 6     /* no GPU, or the object is not in a usable state */
+
+#define CSL_MODE_PHYSICAL 0
+#define CSL_MODE_RAW 1
+
+/* Lattice parameters (Sec. 3.2). */
+typedef struct csl_params {
+    double R;                 /* kernel support; <= 0 selects 1.5 x the largest radius */
+    double C;                 /* iso-value, > 0 (default 1 when 0 is passed)           */
+    int32_t mode;             /* CSL_MODE_PHYSICAL or CSL_MODE_RAW                     */
+    int32_t input_on_device;  /* 1: nodes/edges/radius are device pointers, 0: host    */
+} csl_params;
+
+typedef struct csl_lattice csl_lattice;   /* opaque; device-resident lattice */
+
+typedef struct csl_lattice_info {
+    int64_t n_nodes, n_edges;
+    double R, C;
+    int32_t mode, pad_;
+    float bbox_lo[3], bbox_hi[3];   /* node bounding box (mm) */
+    float max_dz;                   /* largest |v_e^z - v_s^z| over edges */
+    float max_radius;
+} csl_lattice_info;
+
+/*
+ * csl_lattice_upload -- copy a lattice to the GPU and prepare it for slicing.
+ *   nodes_xyz  float[n_nodes][3]  node positions in mm (host or device, see
+ *                                 params->input_on_device)
+ *   edges_ij   int32[n_edges][2]  node indices of each edge's endpoints
+ *   radius     float[n_edges]     per-edge radius (PHYSICAL) or weight (RAW)
+ *   params     may be NULL (R = 1.5 max radius, C = 1, PHYSICAL, host input)
+ *   stream     cudaStream_t or NULL
+ *   out        receives the handle; release it with csl_lattice_free
+ * Preparation (Sec. 4): each edge is ordered so that v_s^z <= v_e^z (Eq. 8),
+ * turned into a 32-byte record (v_s, unit direction, length, weight) and the
+ * records are sorted by v_s^z with a stable device radix sort.
+ * Errors: INVALID_ARG for n_edges > 2^31 - 1, an index outside [0, n_nodes),
+ * a non-finite coordinate or radius, radius <= 0, or (PHYSICAL) radius >= R.
+ * The inputs are not retained; the library keeps its own device copy.
+ * Synchronises the stream (to report validation errors).
+ */
+csl_status csl_lattice_upload(const float* nodes_xyz, int64_t n_nodes, const int32_t* edges_ij,
+                              const float* radius, int64_t n_edges, const csl_params* params,
+                              void* stream, csl_lattice** out);
+
+/*
+ * csl_lattice_update -- replace node positions and/or radii of an uploaded
+ * lattice (same edges), e.g. inside a radius-tuning loop (Sec. 5.4).
+ * nodes_xyz (float[n_nodes][3]) and radius (float[n_edges]) are device
+ * pointers; either may be NULL to keep the current values. R is kept as it
+ * was at upload. Re-sorts the records. Synchronises the stream.
+ */
+csl_status csl_lattice_update(csl_lattice* lat, const float* nodes_xyz, const float* radius,
+                              void* stream);
+
+csl_status csl_lattice_get_info(const csl_lattice* lat, csl_lattice_info* out);
+void csl_lattice_free(csl_lattice* lat);
+
+/* Slicing request (Sec. 4). */
+#define CSL_SLICE_CONTOURS_ON_DEVICE 1   /* leave the contour arrays in device memory */
+#define CSL_SLICE_EDGE_IDS 2             /* also return the grid-edge id of every vertex */
+#define CSL_SLICE_NO_CONTOURS 4          /* field (and sigma_out) only; no marching squares */
+#define CSL_SLICE_TIME_KERNELS 8         /* time the field kernel with CUDA events (csl_stats) */
+#define CSL_SLICE_COUNT_PAIRS 16         /* count (pixel, layer, edge) pairs with a nonzero term */
+
+typedef struct csl_slice_desc {
+    double z0, dz;            /* layer k is the plane z = z0 + k dz                     */
+    int32_t n_layers;         /* >= 0                                                   */
+    int32_t nx, ny;           /* pixels per layer, 1 .. 32000 each                      */
+    int32_t flags;            /* CSL_SLICE_* bits                                       */
+    double x0, y0;            /* pixel (i, j) has its centre at (x0 + (i + 1/2) pixel,  */
+    double pixel;             /*                                 y0 + (j + 1/2) pixel)  */
+    float* sigma_out;         /* optional device float[n_layers][ny][nx]: Sigma per pixel */
+    int32_t tile;             /* pixels per tile side: 0 (auto) or 16                   */
+    int32_t slab;             /* layers per slab: 0 (auto), 1, 2, 4 or 8               */
+    int32_t chunk_layers;     /* layers per streamed chunk: 0 (auto) or a multiple of slab */
+    int32_t reserved_;
+} csl_slice_desc;
+
+/*
+ * Contours of all layers. Loops are closed polygons with the inside of the
+ * solid on their left (outer boundaries counter-clockwise with x right, y up).
+ * The pixel grid is padded by one ring of outside samples, so every loop
+ * closes. Within a layer, loops are listed by their smallest grid-edge id and
+ * each loop starts at that edge; the grid edge from padded sample (I, J) to
+ * (I+1, J) has id 2 (J (nx+2) + I) and the one to (I, J+1) has id
+ * 2 (J (nx+2) + I) + 1, where padded sample (I, J) is pixel (I-1, J-1).
+ * Each vertex is the zero of the linear interpolant of Sigma - C along its
+ * grid edge; a saddle cell joins its inside corners when the mean of its four
+ * corner values is >= C.
+ */
+typedef struct csl_contours {
+    int32_t n_layers;
+    int32_t on_device;        /* 1: the arrays below are device pointers           */
+    int64_t n_loops;
+    int64_t n_verts;
+    int64_t* layer_loop_off;  /* [n_layers + 1] first loop of each layer            */
+    int64_t* loop_vert_off;   /* [n_loops + 1] first vertex of each loop            */
+    float* xy;                /* [n_verts][2] vertex positions in mm                */
+    int32_t* edge_id;         /* [n_verts] grid-edge ids, or NULL without CSL_SLICE_EDGE_IDS */
+} csl_contours;
+
+/*
+ * csl_slice_layers -- evaluate the field on every pixel of every layer,
+ * threshold it at C and trace the contours.
+ *   lat   lattice from csl_lattice_upload
+ *   desc  slicing request; desc->sigma_out, when set, receives Sigma
+ *   out   receives the contours (library-owned; csl_contours_free); may be
+ *         NULL with CSL_SLICE_NO_CONTOURS
+ * Errors: INVALID_ARG for n_layers < 0, dz <= 0 (when n_layers > 1),
+ * pixel <= 0, nx or ny outside [1, 32000], a non-finite origin, an
+ * unsupported tile/slab/chunk value. CAPACITY when an internal count exceeds
+ * 32-bit range per streamed chunk. Synchronises the stream.
+ */
+csl_status csl_slice_layers(csl_lattice* lat, const csl_slice_desc* desc, void* stream,
+                            csl_contours** out);
+void csl_contours_free(csl_contours* c);
+
+/*
+ * csl_contours_copy -- copy the arrays of c into caller buffers (each may be
+ * NULL to skip it). dst_on_device: 1 if the destinations are device memory.
+ * Sizes: layer_loop_off [n_layers + 1], loop_vert_off [n_loops + 1],
+ * xy [2 n_verts], edge_id [n_verts] (only when c has edge ids).
+ * Synchronises the stream.
+ */
+csl_status csl_contours_copy(const csl_contours* c, int64_t* layer_loop_off, int64_t* loop_vert_off,
+                             float* xy, int32_t* edge_id, int32_t dst_on_device, void* stream);
+
+/*
+ * Bins of one slab, for inspection: the edges (as sorted-record positions
+ * mapped back to original edge ids, ascending) that the binner assigns to each
+ * tile of the slab made of layers [first_layer, first_layer + n_slab_layers).
+ * tile_off: host int64[ntx * nty + 1]; ids: host int32[capacity]. Returns the
+ * number of ids in *n_ids (CAPACITY if it exceeds capacity). Tiles are
+ * row-major, tile (tx, ty) covering pixels [tx T, tx T + T) x [ty T, ty T + T).
+ */
+csl_status csl_debug_slab_bins(csl_lattice* lat, const csl_slice_desc* desc, int32_t first_layer,
+                               int32_t n_slab_layers, int64_t* tile_off, int32_t* ids,
+                               int64_t capacity, int64_t* n_ids, void* stream);
+
+/* Statistics of the last csl_slice_layers call on this thread. */
+typedef struct csl_stats {
+    int64_t candidate_pairs;  /* (slab, tile, edge) entries produced by the binner */
+    int64_t crossings;        /* marching-squares vertices                          */
+    int64_t loops;
+    int64_t chunks;
+    int64_t device_bytes_peak;/* largest workspace held at once                     */
+    int64_t kernel_launches;  /* kernels this library launched during the call      */
+    int64_t field_launches;   /* launches of the field kernel                       */
+    double field_ms;          /* their summed CUDA-event time (CSL_SLICE_TIME_KERNELS) */
+    int64_t contributing_pairs; /* pairs with a nonzero term (CSL_SLICE_COUNT_PAIRS) */
+} csl_stats;
+csl_status csl_last_stats(csl_stats* out);
+
+const char* csl_last_error(void);
+const char* csl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSLICE_H */

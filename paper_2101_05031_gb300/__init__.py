@@ -1,0 +1,9 @@
+"""GB300-native slicer for convolution-surface lattices (arxiv 2101.05031).
+
+The compute path is libcslice.so (hand-written CUDA for sm_103a, C ABI in
+include/cslice.h). This package only marshals arguments to it.
+"""
+from ._lib import CslError, load  # noqa: F401
+from .slicer import ContourSet, DeviceContours, Lattice, last_stats  # noqa: F401
+
+__all__ = ["Lattice", "ContourSet", "DeviceContours", "CslError", "load", "last_stats"]

@@ -1,0 +1,116 @@
+"""ctypes declarations for libcslice.so (see include/cslice.h).
+
+The library is built in-tree by ``paper_2101_05031_gb300.build``; loading
+fails loudly when it is missing. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_i32, c_i64, c_f32, c_f64, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                    ctypes.c_double, ctypes.c_void_p)
+
+CSL_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "CAPACITY",
+                6: "NOT_READY"}
+MODE_PHYSICAL = 0
+MODE_RAW = 1
+SLICE_CONTOURS_ON_DEVICE = 1
+SLICE_EDGE_IDS = 2
+SLICE_NO_CONTOURS = 4
+SLICE_TIME_KERNELS = 8
+SLICE_COUNT_PAIRS = 16
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("R", c_f64), ("C", c_f64), ("mode", c_i32), ("input_on_device", c_i32)]
+
+
+class LatticeInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", c_i64), ("n_edges", c_i64), ("R", c_f64), ("C", c_f64),
+                ("mode", c_i32), ("pad_", c_i32), ("bbox_lo", c_f32 * 3), ("bbox_hi", c_f32 * 3),
+                ("max_dz", c_f32), ("max_radius", c_f32)]
+
+
+class SliceDesc(ctypes.Structure):
+    _fields_ = [("z0", c_f64), ("dz", c_f64), ("n_layers", c_i32), ("nx", c_i32), ("ny", c_i32),
+                ("flags", c_i32), ("x0", c_f64), ("y0", c_f64), ("pixel", c_f64),
+                ("sigma_out", c_vp), ("tile", c_i32), ("slab", c_i32), ("chunk_layers", c_i32),
+                ("reserved_", c_i32)]
+
+
+class Contours(ctypes.Structure):
+    _fields_ = [("n_layers", c_i32), ("on_device", c_i32), ("n_loops", c_i64), ("n_verts", c_i64),
+                ("layer_loop_off", c_vp), ("loop_vert_off", c_vp), ("xy", c_vp),
+                ("edge_id", c_vp)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("candidate_pairs", c_i64), ("crossings", c_i64), ("loops", c_i64),
+                ("chunks", c_i64), ("device_bytes_peak", c_i64), ("kernel_launches", c_i64),
+                ("field_launches", c_i64), ("field_ms", c_f64), ("contributing_pairs", c_i64)]
+
+
+class CellsDesc(ctypes.Structure):
+    _fields_ = [("origin", c_f64 * 3), ("h", c_f64), ("dims", c_i32 * 3), ("m", c_i32),
+                ("temperature", c_f64)]
+
+
+class CslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes); every entry point the header declares
+SIGNATURES = [
+    ("csl_last_error", ctypes.c_char_p, []),
+    ("csl_version", ctypes.c_char_p, []),
+    ("csl_last_stats", c_i32, [ctypes.POINTER(Stats)]),
+    ("csl_lattice_upload", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, ctypes.POINTER(Params), c_vp,
+                                   ctypes.POINTER(c_vp)]),
+    ("csl_lattice_update", c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    ("csl_lattice_get_info", c_i32, [c_vp, ctypes.POINTER(LatticeInfo)]),
+    ("csl_lattice_free", None, [c_vp]),
+    ("csl_slice_layers", c_i32, [c_vp, ctypes.POINTER(SliceDesc), c_vp,
+                                 ctypes.POINTER(ctypes.POINTER(Contours))]),
+    ("csl_contours_free", None, [ctypes.POINTER(Contours)]),
+    ("csl_contours_copy", c_i32, [ctypes.POINTER(Contours), c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
+    ("csl_debug_slab_bins", c_i32, [c_vp, ctypes.POINTER(SliceDesc), c_i32, c_i32, c_vp, c_vp,
+                                    c_i64, ctypes.POINTER(c_i64), c_vp]),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libcslice.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.is_stale():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcslice.so is not built ({path}); run "
+                           "python -m paper_2101_05031_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != CSL_OK:
+        msg = load().csl_last_error()
+        raise CslError(status, msg.decode() if msg else "")

@@ -1,0 +1,472 @@
+// C ABI entry points and the streamed slicing driver (Sec. 4): the layers are
+// processed in chunks; per chunk the binner, the field kernel and the contour
+// kernels run on the caller's stream, and the chunk's contours are appended
+// to the result.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <new>
+
+#include "slice.cuh"
+
+using namespace csl;
+
+namespace {
+
+thread_local csl_stats t_stats = {};
+
+csl_status guard(const std::function<void()>& f) {
+    try {
+        f();
+        return CSL_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return CSL_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return CSL_ERR_CUDA;
+    } catch (...) {
+        set_last_error("unknown error");
+        return CSL_ERR_CUDA;
+    }
+}
+
+void require(bool ok, const char* msg) {
+    if (!ok) fail(CSL_ERR_INVALID_ARG, msg);
+}
+
+void copy_in(DevBuf& dst, const void* src, size_t bytes, bool on_device, cudaStream_t s) {
+    dst.ensure_persistent(bytes);
+    if (bytes == 0) return;
+    CSL_CUDA(cudaMemcpyAsync(dst.get(), src, bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+// Resolves tile / slab / chunk sizes and the rounding margins of the binner.
+struct Plan {
+    int S, chunk, ntx, nty;
+    float margin;
+};
+
+Plan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
+    require(d.tile == 0 || d.tile == kTile, "tile must be 0 or 16");
+    Plan p;
+    int S = d.slab;
+    if (S == 0) S = d.n_layers >= 8 ? 8 : (d.n_layers >= 4 ? 4 : (d.n_layers >= 2 ? 2 : 1));
+    require(S == 1 || S == 2 || S == 4 || S == 8, "slab must be 0, 1, 2, 4 or 8");
+    p.S = S;
+    p.ntx = (int)ceil_div(d.nx, kTile);
+    p.nty = (int)ceil_div(d.ny, kTile);
+    const int64_t plane = (int64_t)d.nx * d.ny;
+    int chunk = d.chunk_layers;
+    if (chunk == 0) {
+        // about 1 GiB of Sigma per chunk, whole slabs, at least one slab
+        int64_t c = ((int64_t)1 << 30) / (4 * plane);
+        c = std::max<int64_t>(S, c - c % S);
+        c = std::min<int64_t>(c, std::max(d.n_layers, 1));
+        chunk = (int)c;
+    }
+    require(chunk > 0 && (chunk % S == 0 || chunk >= d.n_layers),
+            "chunk_layers must be a positive multiple of the slab depth");
+    // marching squares needs < 2^27 edge words per chunk
+    const int64_t words_per_layer = 2 * ceil_div((int64_t)(d.nx + 2) * (d.ny + 2), 32);
+    if ((int64_t)chunk * words_per_layer >= ((int64_t)1 << 27)) {
+        int64_t c = (((int64_t)1 << 27) - 1) / words_per_layer;
+        c -= c % S;
+        require(c >= S, "grid too large for one slab per chunk");
+        chunk = (int)c;
+    }
+    p.chunk = chunk;
+    double scale = 1.0;
+    for (int k = 0; k < 3; ++k)
+        scale = std::max({scale, fabs((double)L->bbox_lo[k]), fabs((double)L->bbox_hi[k])});
+    scale = std::max({scale, fabs(d.x0), fabs(d.y0), fabs(d.x0 + d.nx * d.pixel),
+                      fabs(d.y0 + d.ny * d.pixel), fabs(d.z0),
+                      fabs(d.z0 + (double)std::max(d.n_layers - 1, 0) * d.dz)});
+    p.margin = (float)(L->R + 8e-6 * scale + 1e-6);
+    return p;
+}
+
+ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const Plan& p, int first,
+                     int n) {
+    ChunkGeom g;
+    g.nx = d.nx;
+    g.ny = d.ny;
+    g.ntx = p.ntx;
+    g.nty = p.nty;
+    g.x0 = d.x0;
+    g.y0 = d.y0;
+    g.px = d.pixel;
+    g.z0 = d.z0;
+    g.dz = d.dz;
+    g.first_layer = first;
+    g.n_layers = n;
+    g.S = p.S;
+    g.n_slabs = (int)ceil_div(n, p.S);
+    g.R = L->R;
+    g.margin_xy = p.margin;
+    g.margin_z = p.margin;
+    return g;
+}
+
+__global__ void k_add_i64(int64_t* a, int64_t n, int64_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += v;
+}
+
+void validate_desc(const csl_slice_desc* d) {
+    require(d != nullptr, "desc is NULL");
+    require(d->n_layers >= 0, "n_layers < 0");
+    require(d->nx >= 1 && d->ny >= 1 && d->nx <= 32000 && d->ny <= 32000,
+            "nx, ny must be in [1, 32000]");
+    require(isfinite(d->pixel) && d->pixel > 0, "pixel must be > 0");
+    require(isfinite(d->x0) && isfinite(d->y0) && isfinite(d->z0), "non-finite origin");
+    require(d->n_layers <= 1 || (isfinite(d->dz) && d->dz > 0), "dz must be > 0");
+}
+
+struct HostContours {
+    std::vector<int64_t> layer_loop_off{0};
+    std::vector<int64_t> loop_off{0};
+    std::vector<float> xy;
+    std::vector<int32_t> eid;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* csl_last_error(void) { return last_error_cstr(); }
+const char* csl_version(void) { return "cslice 0.1 (sm_103a)"; }
+
+csl_status csl_last_stats(csl_stats* out) {
+    return guard([&] {
+        require(out != nullptr, "out is NULL");
+        *out = t_stats;
+    });
+}
+
+csl_status csl_lattice_upload(const float* nodes_xyz, int64_t n_nodes, const int32_t* edges_ij,
+                              const float* radius, int64_t n_edges, const csl_params* params,
+                              void* stream, csl_lattice** out) {
+    return guard([&] {
+        require(out != nullptr, "out is NULL");
+        *out = nullptr;
+        require(n_nodes >= 0 && n_edges >= 0, "negative size");
+        require(n_edges <= 0x7fffffffLL && n_nodes <= 0x7fffffffLL, "more than 2^31 - 1 items");
+        require(n_nodes == 0 || nodes_xyz != nullptr, "nodes_xyz is NULL");
+        require(n_edges == 0 || (edges_ij != nullptr && radius != nullptr),
+                "edges_ij or radius is NULL");
+        csl_params p = {0.0, 1.0, CSL_MODE_PHYSICAL, 0};
+        if (params) p = *params;
+        if (p.C == 0.0) p.C = 1.0;
+        require(isfinite(p.C) && p.C > 0, "C must be > 0");
+        require(p.mode == CSL_MODE_PHYSICAL || p.mode == CSL_MODE_RAW, "unknown mode");
+        require(isfinite(p.R), "R must be finite");
+        cudaStream_t s = (cudaStream_t)stream;
+        csl_lattice* L = new csl_lattice();
+        try {
+            L->n_nodes = n_nodes;
+            L->n_edges = n_edges;
+            L->R = p.R;
+            L->C = p.C;
+            L->mode = p.mode;
+            bool dev = p.input_on_device != 0;
+            copy_in(L->nodes, nodes_xyz, (size_t)n_nodes * 12, dev, s);
+            copy_in(L->edges, edges_ij, (size_t)n_edges * 8, dev, s);
+            copy_in(L->radius, radius, (size_t)n_edges * 4, dev, s);
+            prepare_lattice(L, true, s);
+            CSL_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            delete L;
+            throw;
+        }
+        *out = L;
+    });
+}
+
+csl_status csl_lattice_update(csl_lattice* L, const float* nodes_xyz, const float* radius,
+                              void* stream) {
+    return guard([&] {
+        require(L != nullptr, "lattice is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (nodes_xyz && L->n_nodes > 0)
+            CSL_CUDA(cudaMemcpyAsync(L->nodes.get(), nodes_xyz, (size_t)L->n_nodes * 12,
+                                     cudaMemcpyDeviceToDevice, s));
+        if (radius && L->n_edges > 0)
+            CSL_CUDA(cudaMemcpyAsync(L->radius.get(), radius, (size_t)L->n_edges * 4,
+                                     cudaMemcpyDeviceToDevice, s));
+        prepare_lattice(L, false, s);
+        CSL_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+csl_status csl_lattice_get_info(const csl_lattice* L, csl_lattice_info* out) {
+    return guard([&] {
+        require(L != nullptr && out != nullptr, "NULL argument");
+        memset(out, 0, sizeof(*out));
+        out->n_nodes = L->n_nodes;
+        out->n_edges = L->n_edges;
+        out->R = L->R;
+        out->C = L->C;
+        out->mode = L->mode;
+        for (int k = 0; k < 3; ++k) { out->bbox_lo[k] = L->bbox_lo[k]; out->bbox_hi[k] = L->bbox_hi[k]; }
+        out->max_dz = L->max_dz;
+        out->max_radius = L->max_radius;
+    });
+}
+
+void csl_lattice_free(csl_lattice* L) { delete L; }
+
+void csl_contours_free(csl_contours* c) {
+    if (!c) return;
+    if (c->on_device) {
+        cudaFree(c->layer_loop_off);
+        cudaFree(c->loop_vert_off);
+        cudaFree(c->xy);
+        cudaFree(c->edge_id);
+    } else {
+        free(c->layer_loop_off);
+        free(c->loop_vert_off);
+        free(c->xy);
+        free(c->edge_id);
+    }
+    delete c;
+}
+
+csl_status csl_contours_copy(const csl_contours* c, int64_t* layer_loop_off,
+                             int64_t* loop_vert_off, float* xy, int32_t* edge_id,
+                             int32_t dst_on_device, void* stream) {
+    return guard([&] {
+        require(c != nullptr, "contours is NULL");
+        require(!edge_id || c->edge_id, "these contours carry no edge ids");
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaMemcpyKind kind = c->on_device ? (dst_on_device ? cudaMemcpyDeviceToDevice
+                                                            : cudaMemcpyDeviceToHost)
+                                           : (dst_on_device ? cudaMemcpyHostToDevice
+                                                            : cudaMemcpyHostToHost);
+        auto cp = [&](void* dst, const void* src, size_t bytes) {
+            if (dst && bytes) CSL_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+        };
+        cp(layer_loop_off, c->layer_loop_off, (size_t)(c->n_layers + 1) * 8);
+        cp(loop_vert_off, c->loop_vert_off, (size_t)(c->n_loops + 1) * 8);
+        cp(xy, c->xy, (size_t)c->n_verts * 8);
+        cp(edge_id, c->edge_id, (size_t)c->n_verts * 4);
+        CSL_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* stream,
+                            csl_contours** out) {
+    return guard([&] {
+        require(L != nullptr, "lattice is NULL");
+        validate_desc(desc);
+        const csl_slice_desc d = *desc;
+        const bool want_contours = !(d.flags & CSL_SLICE_NO_CONTOURS);
+        require(!want_contours || out != nullptr, "out is NULL");
+        if (out) *out = nullptr;
+        const bool on_dev = (d.flags & CSL_SLICE_CONTOURS_ON_DEVICE) != 0;
+        const bool want_eid = (d.flags & CSL_SLICE_EDGE_IDS) != 0;
+        cudaStream_t s = (cudaStream_t)stream;
+        Plan p = make_plan(L, d);
+        device_bytes_peak_and_reset();
+        launches_and_reset();
+        csl_stats st = {};
+        const bool time_kernels = (d.flags & CSL_SLICE_TIME_KERNELS) != 0;
+        const bool count_pairs = (d.flags & CSL_SLICE_COUNT_PAIRS) != 0;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (time_kernels) {
+            CSL_CUDA(cudaEventCreate(&ev0));
+            CSL_CUDA(cudaEventCreate(&ev1));
+        }
+        DevBuf pair_count;
+        if (count_pairs) {
+            pair_count.alloc(8, s);
+            CSL_CUDA(cudaMemsetAsync(pair_count.get(), 0, 8, s));
+        }
+
+        const int64_t plane = (int64_t)d.nx * d.ny;
+        DevBuf sigma_ws;
+        if (!d.sigma_out && d.n_layers > 0)
+            sigma_ws.alloc((size_t)std::min(p.chunk, d.n_layers) * plane * 4, s);
+
+        HostContours hc;
+        std::vector<ChunkContours> dev_chunks;
+        for (int first = 0; first < d.n_layers; first += p.chunk) {
+            const int n = std::min(p.chunk, d.n_layers - first);
+            ChunkGeom g = chunk_geom(L, d, p, first, n);
+            float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane : sigma_ws.as<float>();
+            {
+                SlabBins bins;
+                bin_chunk(L, g, bins, s);
+                st.candidate_pairs += bins.n_pairs;
+                if (time_kernels) CSL_CUDA(cudaEventRecord(ev0, s));
+                field_chunk(L, g, bins, sigma,
+                            count_pairs ? pair_count.as<unsigned long long>() : nullptr, s);
+                ++st.field_launches;
+                if (time_kernels) {
+                    CSL_CUDA(cudaEventRecord(ev1, s));
+                    CSL_CUDA(cudaEventSynchronize(ev1));
+                    float ms = 0.0f;
+                    CSL_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+                    st.field_ms += ms;
+                }
+            }
+            ++st.chunks;
+            if (!want_contours) continue;
+            ChunkContours cc;
+            contours_chunk(g, L->C, sigma, want_eid, cc, s);
+            st.crossings += cc.n_verts;
+            st.loops += cc.n_loops;
+            if (on_dev) {
+                dev_chunks.push_back(std::move(cc));
+                continue;
+            }
+            // append to the host result (offsets rebased on the host)
+            std::vector<int64_t> ll(n + 1), lo(cc.n_loops + 1);
+            read_to_host(ll.data(), cc.layer_loops.get(), (n + 1) * 8, s);
+            read_to_host(lo.data(), cc.loop_off.get(), (cc.n_loops + 1) * 8, s);
+            int64_t loop_base = hc.loop_off.size() - 1, vert_base = hc.xy.size() / 2;
+            for (int l = 1; l <= n; ++l) hc.layer_loop_off.push_back(loop_base + ll[l]);
+            for (int64_t i = 1; i <= cc.n_loops; ++i) hc.loop_off.push_back(vert_base + lo[i]);
+            size_t old = hc.xy.size();
+            hc.xy.resize(old + 2 * cc.n_verts);
+            if (cc.n_verts)
+                read_to_host(hc.xy.data() + old, cc.xy.get(), cc.n_verts * 8, s);
+            if (want_eid) {
+                size_t oe = hc.eid.size();
+                hc.eid.resize(oe + cc.n_verts);
+                if (cc.n_verts)
+                    read_to_host(hc.eid.data() + oe, cc.eid.get(), cc.n_verts * 4, s);
+            }
+        }
+        if (want_contours && d.n_layers == 0 && !on_dev) {
+            // no layers: a single zero offset for layers and loops
+        }
+        CSL_CUDA(cudaStreamSynchronize(s));
+        if (time_kernels) {
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+        }
+        if (count_pairs) st.contributing_pairs = read_i64(pair_count.as<int64_t>(), s);
+        st.device_bytes_peak = device_bytes_peak_and_reset();
+        st.kernel_launches = launches_and_reset();
+        t_stats = st;
+        if (!want_contours) return;
+
+        csl_contours* c = new csl_contours();
+        memset(c, 0, sizeof(*c));
+        c->n_layers = d.n_layers;
+        c->on_device = on_dev ? 1 : 0;
+        if (!on_dev) {
+            c->n_loops = (int64_t)hc.loop_off.size() - 1;
+            c->n_verts = (int64_t)hc.xy.size() / 2;
+            c->layer_loop_off = (int64_t*)malloc(hc.layer_loop_off.size() * 8);
+            c->loop_vert_off = (int64_t*)malloc(hc.loop_off.size() * 8);
+            c->xy = (float*)malloc(std::max<size_t>(hc.xy.size(), 1) * 4);
+            if (want_eid) c->edge_id = (int32_t*)malloc(std::max<size_t>(hc.eid.size(), 1) * 4);
+            if (!c->layer_loop_off || !c->loop_vert_off || !c->xy || (want_eid && !c->edge_id)) {
+                csl_contours_free(c);
+                fail(CSL_ERR_OOM, "host allocation of the contours failed");
+            }
+            memcpy(c->layer_loop_off, hc.layer_loop_off.data(), hc.layer_loop_off.size() * 8);
+            memcpy(c->loop_vert_off, hc.loop_off.data(), hc.loop_off.size() * 8);
+            if (!hc.xy.empty()) memcpy(c->xy, hc.xy.data(), hc.xy.size() * 4);
+            if (want_eid && !hc.eid.empty()) memcpy(c->edge_id, hc.eid.data(), hc.eid.size() * 4);
+            *out = c;
+            return;
+        }
+        // device result: concatenate the chunks, rebasing their offsets
+        int64_t n_loops = 0, n_verts = 0;
+        for (auto& cc : dev_chunks) { n_loops += cc.n_loops; n_verts += cc.n_verts; }
+        c->n_loops = n_loops;
+        c->n_verts = n_verts;
+        auto dmalloc = [&](void** p, size_t b) {
+            cudaError_t e = cudaMalloc(p, b ? b : 16);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                csl_contours_free(c);
+                fail(CSL_ERR_OOM, "device allocation of the contours failed");
+            }
+        };
+        dmalloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8);
+        dmalloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
+        dmalloc((void**)&c->xy, (size_t)n_verts * 8);
+        if (want_eid) dmalloc((void**)&c->edge_id, (size_t)n_verts * 4);
+        int64_t lb = 0, vb = 0;
+        int layer = 0;
+        CSL_CUDA(cudaMemsetAsync(c->layer_loop_off, 0, 8, s));
+        CSL_CUDA(cudaMemsetAsync(c->loop_vert_off, 0, 8, s));
+        for (auto& cc : dev_chunks) {
+            const int n = std::min(p.chunk, d.n_layers - layer);
+            CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off + layer + 1, cc.layer_loops.as<int64_t>() + 1,
+                                     n * 8, cudaMemcpyDeviceToDevice, s));
+            k_add_i64<<<grid_for(n, 256), 256, 0, s>>>(c->layer_loop_off + layer + 1, n, lb);
+            CSL_LAUNCH_CHECK("rebase layer offsets");
+            if (cc.n_loops) {
+                CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off + lb + 1, cc.loop_off.as<int64_t>() + 1,
+                                         cc.n_loops * 8, cudaMemcpyDeviceToDevice, s));
+                k_add_i64<<<grid_for(cc.n_loops, 256), 256, 0, s>>>(c->loop_vert_off + lb + 1,
+                                                                   cc.n_loops, vb);
+                CSL_LAUNCH_CHECK("rebase loop offsets");
+            }
+            if (cc.n_verts) {
+                CSL_CUDA(cudaMemcpyAsync(c->xy + 2 * vb, cc.xy.get(), cc.n_verts * 8,
+                                         cudaMemcpyDeviceToDevice, s));
+                if (want_eid)
+                    CSL_CUDA(cudaMemcpyAsync(c->edge_id + vb, cc.eid.get(), cc.n_verts * 4,
+                                             cudaMemcpyDeviceToDevice, s));
+            }
+            lb += cc.n_loops;
+            vb += cc.n_verts;
+            layer += n;
+        }
+        CSL_CUDA(cudaStreamSynchronize(s));
+        *out = c;
+    });
+}
+
+csl_status csl_debug_slab_bins(csl_lattice* L, const csl_slice_desc* desc, int32_t first_layer,
+                               int32_t n_slab_layers, int64_t* tile_off, int32_t* ids,
+                               int64_t capacity, int64_t* n_ids, void* stream) {
+    return guard([&] {
+        require(L != nullptr && tile_off != nullptr && n_ids != nullptr, "NULL argument");
+        validate_desc(desc);
+        require(n_slab_layers >= 1 && first_layer >= 0, "bad slab");
+        cudaStream_t s = (cudaStream_t)stream;
+        csl_slice_desc d = *desc;
+        if (d.n_layers < first_layer + n_slab_layers) d.n_layers = first_layer + n_slab_layers;
+        Plan p = make_plan(L, d);
+        ChunkGeom g = chunk_geom(L, d, p, first_layer, n_slab_layers);
+        g.S = n_slab_layers;
+        g.n_slabs = 1;
+        SlabBins bins;
+        bin_chunk(L, g, bins, s);
+        const int n_tiles = g.ntx * g.nty;
+        std::vector<uint32_t> ts(n_tiles), te(n_tiles), vals(bins.n_pairs), sid(L->n_edges);
+        read_to_host(ts.data(), bins.tile_start.get(), n_tiles * 4, s);
+        read_to_host(te.data(), bins.tile_end.get(), n_tiles * 4, s);
+        if (bins.n_pairs) read_to_host(vals.data(), bins.vals.get(), bins.n_pairs * 4, s);
+        if (L->n_edges) read_to_host(sid.data(), L->sid.get(), L->n_edges * 4, s);
+        *n_ids = bins.n_pairs;
+        tile_off[0] = 0;
+        int64_t pos = 0;
+        for (int t = 0; t < n_tiles; ++t) {
+            std::vector<int32_t> list;
+            for (uint32_t i = ts[t]; i < te[t]; ++i) list.push_back((int32_t)(sid[vals[i]] & 0x7fffffffu));
+            std::sort(list.begin(), list.end());
+            if (ids && pos + (int64_t)list.size() <= capacity)
+                memcpy(ids + pos, list.data(), list.size() * 4);
+            pos += (int64_t)list.size();
+            tile_off[t + 1] = pos;
+        }
+        if (pos > capacity) fail(CSL_ERR_CAPACITY, "ids capacity too small");
+    });
+}
+
+}  // extern "C"

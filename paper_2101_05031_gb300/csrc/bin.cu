@@ -1,0 +1,233 @@
+// Slab / tile binner. The active-edge set of Eq. 8 is widened from one plane
+// to a slab of S layers, then split over 2D tiles of 16 x 16 pixels:
+//   1. per slab, a window of the v_s^z-sorted records (binary search);
+//   2. per (slab, record): the FP32 bin predicate below -> a rectangle of tiles,
+//      counted, prefix-summed and emitted as (slab * n_tiles + tile, record);
+//   3. a stable radix sort by that key, so every (slab, tile) list is
+//      contiguous and in record order (deterministic);
+//   4. list boundaries per key.
+//
+// Bin predicate (all FP32, round-to-nearest, no fused operations), for a slab
+// whose first and last layer planes are zf <= zl and an edge with exact
+// endpoints (ax, ay, zlo) -> (bx, by, zhi), zlo <= zhi:
+//   reject unless (zlo - mz) <= zl and (zhi + mz) >= zf;
+//   t0 = 0, t1 = 1; if zhi - zlo > 0:
+//       t0 = max(((zf - mz) - zlo) / (zhi - zlo), 0), t1 = min(((zl + mz) - zlo) / (zhi - zlo), 1)
+//   x(t) = ax + t (bx - ax), y(t) likewise;
+//   box = [min(x(t0), x(t1)) - mxy, max(...) + mxy] x [same in y];
+//   tile range = floor((box - origin) * inv_tile), clipped to the grid.
+// mz and mxy are R plus a slack for FP32 rounding, so every pixel centre of
+// the tile within distance R of the edge at some layer of the slab is inside.
+#include <math.h>
+
+#include "slice.cuh"
+
+namespace csl {
+namespace {
+
+struct BinConst {
+    float fx0, fy0, inv_tile, mxy, mz;
+    int32_t ntx, nty, n_tiles;
+};
+
+struct SlabInfo {
+    int64_t kb, ke;      // record window
+    int64_t cand_off;    // first candidate of this slab
+    float zf, zl;        // first / last layer plane of the slab
+};
+
+__device__ __forceinline__ bool bin_rect(const float4 e, float zlo, float zhi, float zf, float zl,
+                                         const BinConst& c, int& tx0, int& tx1, int& ty0,
+                                         int& ty1) {
+    if (__fsub_rn(zlo, c.mz) > zl) return false;
+    if (__fadd_rn(zhi, c.mz) < zf) return false;
+    float t0 = 0.0f, t1 = 1.0f;
+    float dzs = __fsub_rn(zhi, zlo);
+    if (dzs > 0.0f) {
+        t0 = fmaxf(__fdiv_rn(__fsub_rn(__fsub_rn(zf, c.mz), zlo), dzs), 0.0f);
+        t1 = fminf(__fdiv_rn(__fsub_rn(__fadd_rn(zl, c.mz), zlo), dzs), 1.0f);
+    }
+    float ex = __fsub_rn(e.z, e.x), ey = __fsub_rn(e.w, e.y);
+    float xa = __fadd_rn(e.x, __fmul_rn(t0, ex)), xb = __fadd_rn(e.x, __fmul_rn(t1, ex));
+    float ya = __fadd_rn(e.y, __fmul_rn(t0, ey)), yb = __fadd_rn(e.y, __fmul_rn(t1, ey));
+    float xmin = __fsub_rn(fminf(xa, xb), c.mxy), xmax = __fadd_rn(fmaxf(xa, xb), c.mxy);
+    float ymin = __fsub_rn(fminf(ya, yb), c.mxy), ymax = __fadd_rn(fmaxf(ya, yb), c.mxy);
+    float fx0 = floorf(__fmul_rn(__fsub_rn(xmin, c.fx0), c.inv_tile));
+    float fx1 = floorf(__fmul_rn(__fsub_rn(xmax, c.fx0), c.inv_tile));
+    float fy0 = floorf(__fmul_rn(__fsub_rn(ymin, c.fy0), c.inv_tile));
+    float fy1 = floorf(__fmul_rn(__fsub_rn(ymax, c.fy0), c.inv_tile));
+    if (fx1 < 0.0f || fy1 < 0.0f || fx0 >= (float)c.ntx || fy0 >= (float)c.nty) return false;
+    tx0 = (int)fmaxf(fx0, 0.0f);
+    ty0 = (int)fmaxf(fy0, 0.0f);
+    tx1 = (int)fminf(fx1, (float)(c.ntx - 1));
+    ty1 = (int)fminf(fy1, (float)(c.nty - 1));
+    return true;
+}
+
+// Window of records for each slab: zlo in [zf - mz - max_dz - slack, zl + mz + slack].
+__global__ void k_slab_windows(const float* __restrict__ zlo, int64_t n, SlabInfo* slabs,
+                               int n_slabs, float mz, float max_dz) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slabs) return;
+    float zf = slabs[s].zf, zl = slabs[s].zl;
+    double lo_key = (double)zf - mz - max_dz - 1e-3 * (1.0 + fabs((double)zf));
+    double hi_key = (double)zl + mz + 1e-3 * (1.0 + fabs((double)zl));
+    int64_t a = 0, b = n;   // first k with zlo[k] >= lo_key
+    while (a < b) {
+        int64_t m = (a + b) >> 1;
+        if ((double)zlo[m] < lo_key) a = m + 1; else b = m;
+    }
+    int64_t kb = a;
+    a = kb;
+    b = n;                  // first k with zlo[k] > hi_key
+    while (a < b) {
+        int64_t m = (a + b) >> 1;
+        if ((double)zlo[m] <= hi_key) a = m + 1; else b = m;
+    }
+    slabs[s].kb = kb;
+    slabs[s].ke = a;
+}
+
+__global__ void k_cand_offsets(SlabInfo* slabs, int n_slabs, int64_t* total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int s = 0; s < n_slabs; ++s) {
+        slabs[s].cand_off = acc;
+        acc += slabs[s].ke - slabs[s].kb;
+    }
+    *total = acc;
+}
+
+__global__ void k_bin_count(const float4* __restrict__ bxy, const float* __restrict__ zlo,
+                            const float* __restrict__ zhi, const SlabInfo* __restrict__ slabs,
+                            BinConst c, uint32_t* __restrict__ count) {
+    const SlabInfo sl = slabs[blockIdx.y];
+    int64_t n = sl.ke - sl.kb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = sl.kb + i;
+        int tx0, tx1, ty0, ty1;
+        uint32_t cnt = 0;
+        if (bin_rect(bxy[k], zlo[k], zhi[k], sl.zf, sl.zl, c, tx0, tx1, ty0, ty1))
+            cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        count[sl.cand_off + i] = cnt;
+    }
+}
+
+__global__ void k_bin_emit(const float4* __restrict__ bxy, const float* __restrict__ zlo,
+                           const float* __restrict__ zhi, const SlabInfo* __restrict__ slabs,
+                           BinConst c, const int64_t* __restrict__ pair_off,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int s = blockIdx.y;
+    const SlabInfo sl = slabs[s];
+    int64_t n = sl.ke - sl.kb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = sl.kb + i;
+        int tx0, tx1, ty0, ty1;
+        if (!bin_rect(bxy[k], zlo[k], zhi[k], sl.zf, sl.zl, c, tx0, tx1, ty0, ty1)) continue;
+        int64_t p = pair_off[sl.cand_off + i];
+        uint32_t kbase = (uint32_t)s * (uint32_t)c.n_tiles;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                keys[p] = kbase + (uint32_t)(ty * c.ntx + tx);
+                vals[p] = (uint32_t)k;
+                ++p;
+            }
+    }
+}
+
+__global__ void k_list_bounds(const uint32_t* __restrict__ keys, int64_t n,
+                              uint32_t* __restrict__ start, uint32_t* __restrict__ end) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        if (i == 0 || keys[i - 1] != k) start[k] = (uint32_t)i;
+        if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+    }
+}
+
+int bits_for(int64_t n) {
+    int b = 0;
+    while (b < 32 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+}  // namespace
+
+void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s) {
+    const int n_tiles = g.ntx * g.nty;
+    const int64_t n_keys = (int64_t)g.n_slabs * n_tiles;
+    if (n_keys > 0xffffffffLL) fail(CSL_ERR_CAPACITY, "too many (slab, tile) bins in one chunk");
+    BinConst c;
+    c.fx0 = (float)g.x0;
+    c.fy0 = (float)g.y0;
+    c.inv_tile = (float)(1.0 / ((double)kTile * g.px));
+    c.mxy = g.margin_xy;
+    c.mz = g.margin_z;
+    c.ntx = g.ntx;
+    c.nty = g.nty;
+    c.n_tiles = n_tiles;
+
+    std::vector<SlabInfo> hs(g.n_slabs);
+    for (int sl = 0; sl < g.n_slabs; ++sl) {
+        int l0 = g.first_layer + sl * g.S;
+        int l1 = l0 + g.S - 1;
+        int last = g.first_layer + g.n_layers - 1;
+        if (l1 > last) l1 = last;
+        hs[sl].zf = (float)(g.z0 + (double)l0 * g.dz);
+        hs[sl].zl = (float)(g.z0 + (double)l1 * g.dz);
+        hs[sl].kb = hs[sl].ke = hs[sl].cand_off = 0;
+    }
+    DevBuf slabs(sizeof(SlabInfo) * g.n_slabs, s);
+    DevBuf total(sizeof(int64_t), s);
+    CSL_CUDA(cudaMemcpyAsync(slabs.get(), hs.data(), sizeof(SlabInfo) * g.n_slabs,
+                             cudaMemcpyHostToDevice, s));
+    k_slab_windows<<<(unsigned)ceil_div(g.n_slabs, 128), 128, 0, s>>>(
+        L->zlo.as<float>(), L->n_edges, slabs.as<SlabInfo>(), g.n_slabs, c.mz, L->max_dz);
+    CSL_LAUNCH_CHECK("slab windows");
+    k_cand_offsets<<<1, 32, 0, s>>>(slabs.as<SlabInfo>(), g.n_slabs, total.as<int64_t>());
+    CSL_LAUNCH_CHECK("candidate offsets");
+    int64_t n_cand = read_i64(total.as<int64_t>(), s);
+    read_to_host(hs.data(), slabs.get(), sizeof(SlabInfo) * g.n_slabs, s);
+    int64_t max_window = 0;
+    for (auto& x : hs) max_window = std::max<int64_t>(max_window, x.ke - x.kb);
+
+    out.tile_start.ensure((size_t)n_keys * 4, s);
+    out.tile_end.ensure((size_t)n_keys * 4, s);
+    CSL_CUDA(cudaMemsetAsync(out.tile_start.get(), 0, (size_t)n_keys * 4, s));
+    CSL_CUDA(cudaMemsetAsync(out.tile_end.get(), 0, (size_t)n_keys * 4, s));
+    out.n_pairs = 0;
+    if (n_cand == 0) return;
+
+    DevBuf count((size_t)n_cand * 4, s), pair_off((size_t)n_cand * 8, s);
+    dim3 grid(grid_for(max_window, 256, 4096), (unsigned)g.n_slabs);
+    k_bin_count<<<grid, 256, 0, s>>>(L->bxy.as<float4>(), L->zlo.as<float>(), L->zhi.as<float>(),
+                                     slabs.as<SlabInfo>(), c, count.as<uint32_t>());
+    CSL_LAUNCH_CHECK("bin count");
+    exclusive_scan_u32_to_i64(count.as<uint32_t>(), pair_off.as<int64_t>(), n_cand,
+                              total.as<int64_t>(), s);
+    int64_t n_pairs = read_i64(total.as<int64_t>(), s);
+    if (n_pairs > 0xffffffffLL) fail(CSL_ERR_CAPACITY, "more than 2^32 bin entries in one chunk");
+    out.n_pairs = n_pairs;
+    if (n_pairs == 0) return;
+    out.keys.ensure((size_t)n_pairs * 4, s);
+    out.vals.ensure((size_t)n_pairs * 4, s);
+    k_bin_emit<<<grid, 256, 0, s>>>(L->bxy.as<float4>(), L->zlo.as<float>(), L->zhi.as<float>(),
+                                    slabs.as<SlabInfo>(), c, pair_off.as<int64_t>(),
+                                    out.keys.as<uint32_t>(), out.vals.as<uint32_t>());
+    CSL_LAUNCH_CHECK("bin emit");
+    count.release();
+    pair_off.release();
+    {
+        DevBuf tk((size_t)n_pairs * 4, s), tv((size_t)n_pairs * 4, s);
+        radix_sort_pairs(out.keys.as<uint32_t>(), out.vals.as<uint32_t>(), tk.as<uint32_t>(),
+                         tv.as<uint32_t>(), n_pairs, bits_for(n_keys), s);
+    }
+    k_list_bounds<<<grid_for(n_pairs, 256), 256, 0, s>>>(out.keys.as<uint32_t>(), n_pairs,
+                                                        out.tile_start.as<uint32_t>(),
+                                                        out.tile_end.as<uint32_t>());
+    CSL_LAUNCH_CHECK("list bounds");
+}
+
+}  // namespace csl

@@ -1,0 +1,110 @@
+// Internal helpers shared by the translation units of libcslice.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/cslice.h"
+
+namespace csl {
+
+// A failure inside the library; converted to a csl_status at the ABI.
+struct Error : std::runtime_error {
+    csl_status code;
+    Error(csl_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void fail(csl_status code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+#define CSL_CUDA(call) ::csl::check_cuda((call), #call)
+// Placed after every kernel launch: checks it and counts it.
+#define CSL_LAUNCH_CHECK(what) ::csl::launched(what)
+void launched(const char* what);
+int64_t launches_and_reset();
+
+// Stream-ordered device allocation that frees itself (cudaFreeAsync).
+class DevBuf {
+  public:
+    DevBuf() = default;
+    DevBuf(size_t bytes, cudaStream_t s) { alloc(bytes, s); }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept
+        : p_(o.p_), n_(o.n_), s_(o.s_), persistent_(o.persistent_) { o.p_ = nullptr; o.n_ = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p_ = o.p_; n_ = o.n_; s_ = o.s_; persistent_ = o.persistent_;
+            o.p_ = nullptr; o.n_ = 0;
+        }
+        return *this;
+    }
+    // stream-ordered (cudaMallocAsync / cudaFreeAsync on the same stream)
+    void alloc(size_t bytes, cudaStream_t s);
+    void ensure(size_t bytes, cudaStream_t s) { if (bytes > n_) alloc(bytes, s); }
+    // outlives any stream (cudaMalloc / cudaFree): for objects handed to the caller
+    void alloc_persistent(size_t bytes);
+    void ensure_persistent(size_t bytes) { if (bytes > n_) alloc_persistent(bytes); }
+    void release();
+    template <class T> T* as() const { return reinterpret_cast<T*>(p_); }
+    size_t size() const { return n_; }
+    void* get() const { return p_; }
+
+  private:
+    void* p_ = nullptr;
+    size_t n_ = 0;
+    cudaStream_t s_ = nullptr;
+    bool persistent_ = false;
+};
+
+// Workspace accounting for csl_last_stats.
+void note_device_bytes(int64_t delta);
+int64_t device_bytes_peak_and_reset();
+
+void set_last_error(const std::string& m);
+const char* last_error_cstr();
+
+int64_t read_i64(const int64_t* dev, cudaStream_t s);   // synchronising
+void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s);  // synchronising
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline unsigned grid_for(int64_t n, int block, int64_t cap = 152 * 64) {
+    int64_t g = ceil_div(n, block);
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ---- scan (scan.cu) ----
+// Exclusive prefix sums; `out` may alias `in`. The total is written to
+// *total_dev when it is non-null.
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+                        cudaStream_t s);
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                        cudaStream_t s);
+// Exclusive scan of uint32 counts into int64 offsets.
+void exclusive_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                               cudaStream_t s);
+
+// ---- stable LSD radix sort (radix_sort.cu) ----
+// Sorts (keys, vals) by the low `key_bits` bits of keys, stably. The result
+// ends in keys/vals; tmp_keys/tmp_vals are scratch of the same size.
+void radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* tmp_keys, uint32_t* tmp_vals,
+                      int64_t n, int key_bits, cudaStream_t s);
+
+// Status word written by kernels (bit flags).
+enum : uint32_t {
+    ST_BAD_INDEX = 1u,
+    ST_NONFINITE = 2u,
+    ST_BAD_RADIUS = 4u,
+    ST_CAPACITY = 8u,
+    ST_TIMEOUT = 16u,
+};
+
+}  // namespace csl

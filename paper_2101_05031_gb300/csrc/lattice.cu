@@ -1,0 +1,173 @@
+// Lattice preparation (Sec. 4): validate the input, order each edge so that
+// v_s^z <= v_e^z (Eq. 8), sort the edges by v_s^z and build 32-byte records.
+#include <math.h>
+
+#include "lattice.cuh"
+
+namespace csl {
+namespace {
+
+__device__ __forceinline__ uint32_t ord_enc(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float ord_dec(uint32_t u) {
+    uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
+struct ScanOut {
+    uint32_t status;
+    uint32_t lo[3], hi[3];
+    uint32_t max_r;
+    uint32_t max_dz;
+};
+
+__global__ void k_scan_inputs(const float* __restrict__ nodes, int64_t n_nodes,
+                              const int32_t* __restrict__ edges, const float* __restrict__ radius,
+                              int64_t n_edges, ScanOut* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t st = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += stride) {
+        for (int k = 0; k < 3; ++k) {
+            float v = nodes[3 * i + k];
+            if (!isfinite(v)) { st |= ST_NONFINITE; continue; }
+            atomicMin(&out->lo[k], ord_enc(v));
+            atomicMax(&out->hi[k], ord_enc(v));
+        }
+    }
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_edges; j += stride) {
+        int32_t a = edges[2 * j], b = edges[2 * j + 1];
+        if (a < 0 || b < 0 || a >= n_nodes || b >= n_nodes) st |= ST_BAD_INDEX;
+        float r = radius[j];
+        if (!isfinite(r)) st |= ST_NONFINITE;
+        else if (!(r > 0.0f)) st |= ST_BAD_RADIUS;
+        else atomicMax(&out->max_r, ord_enc(r));
+    }
+    if (st) atomicOr(&out->status, st);
+}
+
+__global__ void k_prep_keys(const float* __restrict__ nodes, const int32_t* __restrict__ edges,
+                            int64_t n_edges, uint32_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_edges; j += stride) {
+        float za = nodes[3 * (int64_t)edges[2 * j] + 2];
+        float zb = nodes[3 * (int64_t)edges[2 * j + 1] + 2];
+        keys[j] = ord_enc(zb < za ? zb : za);
+        vals[j] = (uint32_t)j;
+    }
+}
+
+__global__ void k_build_records(const float* __restrict__ nodes, const int32_t* __restrict__ edges,
+                                const float* __restrict__ radius, const uint32_t* __restrict__ order,
+                                int64_t n_edges, double R, double C, int mode,
+                                csl_rec* __restrict__ rec, float4* __restrict__ bxy,
+                                float* __restrict__ zlo,
+                                float* __restrict__ zhi, uint32_t* __restrict__ sid,
+                                ScanOut* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t local_max_dz = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_edges; k += stride) {
+        uint32_t j = order[k];
+        const float* pa = nodes + 3 * (int64_t)edges[2 * (int64_t)j];
+        const float* pb = nodes + 3 * (int64_t)edges[2 * (int64_t)j + 1];
+        bool swap = pb[2] < pa[2];
+        const float* lo = swap ? pb : pa;
+        const float* hi = swap ? pa : pb;
+        double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
+        double L = sqrt(dx * dx + dy * dy + dz * dz);
+        double inv = L > 0.0 ? 1.0 / L : 0.0;
+        double rho = radius[j];
+        double w;
+        if (mode == CSL_MODE_RAW) {
+            w = rho;
+        } else {
+            double q = R * R - rho * rho;
+            w = C * 15.0 * (R * R) * (R * R) / (16.0 * q * q * sqrt(q));
+        }
+        csl_rec r;
+        r.ax = lo[0];
+        r.ay = lo[1];
+        r.az = lo[2];
+        r.ux = (float)(dx * inv);
+        r.uy = (float)(dy * inv);
+        r.uz = (float)(dz * inv);
+        r.len = (float)L;
+        r.w = (float)w;
+        rec[k] = r;
+        bxy[k] = make_float4(lo[0], lo[1], hi[0], hi[1]);
+        zlo[k] = lo[2];
+        zhi[k] = hi[2];
+        sid[k] = j | (swap ? 0x80000000u : 0u);
+        uint32_t e = ord_enc(__double2float_ru(dz));
+        local_max_dz = e > local_max_dz ? e : local_max_dz;
+    }
+    if (local_max_dz) atomicMax(&out->max_dz, local_max_dz);
+}
+
+}  // namespace
+
+void prepare_lattice(csl_lattice* L, bool recompute_R, cudaStream_t s) {
+    const int64_t ne = L->n_edges, nn = L->n_nodes;
+    DevBuf scan_out(sizeof(ScanOut), s);
+    ScanOut init;
+    init.status = 0;
+    for (int k = 0; k < 3; ++k) { init.lo[k] = 0xffffffffu; init.hi[k] = 0u; }
+    init.max_r = 0;
+    init.max_dz = 0;
+    CSL_CUDA(cudaMemcpyAsync(scan_out.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    int64_t nmax = nn > ne ? nn : ne;
+    if (nmax > 0) {
+        k_scan_inputs<<<grid_for(nmax, 256), 256, 0, s>>>(
+            L->nodes.as<float>(), nn, L->edges.as<int32_t>(), L->radius.as<float>(), ne,
+            scan_out.as<ScanOut>());
+        CSL_LAUNCH_CHECK("scan inputs");
+    }
+    ScanOut h;
+    read_to_host(&h, scan_out.get(), sizeof(h), s);
+    if (h.status & ST_BAD_INDEX) fail(CSL_ERR_INVALID_ARG, "edge index outside [0, n_nodes)");
+    if (h.status & ST_NONFINITE) fail(CSL_ERR_INVALID_ARG, "non-finite node coordinate or radius");
+    if (h.status & ST_BAD_RADIUS) fail(CSL_ERR_INVALID_ARG, "radius must be > 0");
+    if (nn > 0)
+        for (int k = 0; k < 3; ++k) { L->bbox_lo[k] = ord_dec(h.lo[k]); L->bbox_hi[k] = ord_dec(h.hi[k]); }
+    L->max_radius = ne > 0 ? ord_dec(h.max_r) : 0.0f;
+    if (recompute_R) {
+        if (!(L->R > 0.0)) L->R = 1.5 * (double)L->max_radius;
+        if (!(L->R > 0.0)) L->R = 1.0;   // empty lattice: any positive support
+    }
+    if (L->mode == CSL_MODE_PHYSICAL && ne > 0 && !((double)L->max_radius < L->R))
+        fail(CSL_ERR_INVALID_ARG, "PHYSICAL mode needs every radius < R");
+
+    L->rec.ensure_persistent((size_t)(ne > 0 ? ne : 1) * sizeof(csl_rec));
+    L->bxy.ensure_persistent((size_t)(ne > 0 ? ne : 1) * sizeof(float4));
+    L->zlo.ensure_persistent((size_t)(ne > 0 ? ne : 1) * sizeof(float));
+    L->zhi.ensure_persistent((size_t)(ne > 0 ? ne : 1) * sizeof(float));
+    L->sid.ensure_persistent((size_t)(ne > 0 ? ne : 1) * sizeof(uint32_t));
+    L->max_dz = 0;
+    if (ne == 0) return;
+    DevBuf keys(ne * 4, s), vals(ne * 4, s), tk(ne * 4, s), tv(ne * 4, s);
+    k_prep_keys<<<grid_for(ne, 256), 256, 0, s>>>(L->nodes.as<float>(), L->edges.as<int32_t>(), ne,
+                                                 keys.as<uint32_t>(), vals.as<uint32_t>());
+    CSL_LAUNCH_CHECK("prep keys");
+    radix_sort_pairs(keys.as<uint32_t>(), vals.as<uint32_t>(), tk.as<uint32_t>(),
+                     tv.as<uint32_t>(), ne, 32, s);
+    k_build_records<<<grid_for(ne, 256), 256, 0, s>>>(
+        L->nodes.as<float>(), L->edges.as<int32_t>(), L->radius.as<float>(), vals.as<uint32_t>(),
+        ne, L->R, L->C, L->mode, L->rec.as<csl_rec>(), L->bxy.as<float4>(), L->zlo.as<float>(),
+        L->zhi.as<float>(),
+        L->sid.as<uint32_t>(), scan_out.as<ScanOut>());
+    CSL_LAUNCH_CHECK("build records");
+    read_to_host(&h, scan_out.get(), sizeof(h), s);
+    L->max_dz = h.max_dz ? ord_dec(h.max_dz) : 0.0f;
+    L->node_csr_off.release();
+    L->node_csr.release();
+}
+
+}  // namespace csl

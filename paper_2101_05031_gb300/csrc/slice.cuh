@@ -1,0 +1,51 @@
+// Internal interfaces of the slicing pipeline (binner, field, contours).
+#pragma once
+
+#include "lattice.cuh"
+
+namespace csl {
+
+constexpr int kTile = 16;        // pixels per tile side
+constexpr int kFieldThreads = 256;
+
+// Geometry of one streamed chunk of layers.
+struct ChunkGeom {
+    // grid
+    int32_t nx, ny, ntx, nty;
+    double x0, y0, px, z0, dz;
+    // chunk: layers [first_layer, first_layer + n_layers), slabs of S layers
+    int32_t first_layer, n_layers, S, n_slabs;
+    // lattice
+    double R;
+    float margin_xy;   // xy expansion of a clipped edge's box (R plus rounding slack)
+    float margin_z;    // z expansion (R plus rounding slack)
+};
+
+// Per-slab binning results (device).
+struct SlabBins {
+    DevBuf keys, vals;          // sorted pairs: key = slab * n_tiles + tile, val = record position
+    DevBuf tile_start, tile_end;// uint32 [n_slabs * n_tiles]
+    int64_t n_pairs = 0;
+};
+
+// Bins the lattice's records into (slab, tile) lists for one chunk.
+void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s);
+
+// Sigma for every pixel of the chunk's layers: sigma[layer][ny][nx].
+// count_pairs (device, may be null): adds the number of (pixel, layer, edge)
+// terms that are nonzero.
+void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float* sigma,
+                 unsigned long long* count_pairs, cudaStream_t s);
+
+// Contours of the chunk's layers (device arrays, layer-local edge ids).
+struct ChunkContours {
+    int64_t n_verts = 0, n_loops = 0;
+    DevBuf layer_loops;   // int64 [n_layers + 1] loop offsets per layer (chunk-local)
+    DevBuf loop_off;      // int64 [n_loops + 1] vertex offsets (chunk-local)
+    DevBuf xy;            // float2 [n_verts]
+    DevBuf eid;           // int32 [n_verts]
+};
+void contours_chunk(const ChunkGeom& g, double C, const float* sigma, bool want_eid,
+                    ChunkContours& out, cudaStream_t s);
+
+}  // namespace csl

@@ -1,0 +1,250 @@
+"""Python face of libcslice: lattices, slicing and contours.
+
+Only argument marshalling happens here; every step of the method runs in the
+CUDA library. Inputs may be numpy arrays (host) or torch tensors (host or
+CUDA); outputs are numpy arrays (host contours) or stay in device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+
+try:  # torch is plumbing only: device buffers and streams
+    import torch
+except Exception:  # pragma: no cover - the CPU test image has torch
+    torch = None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        if torch is not None and torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_buffer(x, dtype, width):
+    """Returns (pointer, n_rows, on_device, keepalive)."""
+    if torch is not None and isinstance(x, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        t = x.detach().to(tdt).contiguous()
+        n = t.numel() // width
+        return ctypes.c_void_p(t.data_ptr()), n, t.is_cuda, t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    n = a.size // width
+    return a.ctypes.data_as(ctypes.c_void_p), n, False, a
+
+
+@dataclass
+class ContourSet:
+    """Closed loops of every layer (host arrays).
+
+    layer_loop_off[n_layers + 1], loop_vert_off[n_loops + 1], xy[n_verts, 2]
+    (mm), edge_id[n_verts] (or None)."""
+    layer_loop_off: np.ndarray
+    loop_vert_off: np.ndarray
+    xy: np.ndarray
+    edge_id: np.ndarray | None
+
+    @property
+    def n_layers(self):
+        return len(self.layer_loop_off) - 1
+
+    def layer(self, k):
+        """Loops of layer k as a list of (edge_id or None, xy) arrays."""
+        out = []
+        for li in range(self.layer_loop_off[k], self.layer_loop_off[k + 1]):
+            a, b = self.loop_vert_off[li], self.loop_vert_off[li + 1]
+            out.append((None if self.edge_id is None else self.edge_id[a:b], self.xy[a:b]))
+        return out
+
+
+class DeviceContours:
+    """Contours left in device memory (CSL_SLICE_CONTOURS_ON_DEVICE)."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        c = ptr.contents
+        self.n_layers, self.n_loops, self.n_verts = c.n_layers, c.n_loops, c.n_verts
+        self.has_edge_ids = bool(c.edge_id)
+
+    def to_host(self) -> ContourSet:
+        lo = np.empty(self.n_layers + 1, np.int64)
+        vo = np.empty(self.n_loops + 1, np.int64)
+        xy = np.empty((self.n_verts, 2), np.float32)
+        eid = np.empty(self.n_verts, np.int32) if self.has_edge_ids else None
+        _lib.check(_lib.load().csl_contours_copy(
+            self._ptr, lo.ctypes.data_as(ctypes.c_void_p), vo.ctypes.data_as(ctypes.c_void_p),
+            xy.ctypes.data_as(ctypes.c_void_p),
+            eid.ctypes.data_as(ctypes.c_void_p) if eid is not None else None, 0, _stream_ptr(None)))
+        return ContourSet(lo, vo, xy, eid)
+
+    def free(self):
+        if self._ptr is not None:
+            _lib.load().csl_contours_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _host_contours(ptr) -> ContourSet:
+    c = ptr.contents
+    nl, nloops, nv = c.n_layers, c.n_loops, c.n_verts
+
+    np_type = {ctypes.c_int64: np.int64, ctypes.c_float: np.float32, ctypes.c_int32: np.int32}
+
+    def arr(p, n, ct, shape=None):
+        if n == 0:
+            return np.zeros(shape or (0,), dtype=np_type[ct])
+        a = np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ct)), shape=(n,)).copy()
+        return a.reshape(shape) if shape else a
+
+    lo = arr(c.layer_loop_off, nl + 1, ctypes.c_int64)
+    vo = arr(c.loop_vert_off, nloops + 1, ctypes.c_int64)
+    xy = arr(c.xy, 2 * nv, ctypes.c_float, (nv, 2))
+    eid = arr(c.edge_id, nv, ctypes.c_int32) if c.edge_id else None
+    return ContourSet(lo, vo, xy, eid)
+
+
+class Lattice:
+    """A lattice uploaded to the GPU (csl_lattice_upload).
+
+    nodes float[Nn, 3] (mm), edges int32[Ne, 2], radius float[Ne] (PHYSICAL:
+    strut radius; RAW: the paper's r_i weight). R None -> 1.5 x max radius."""
+
+    def __init__(self, nodes, edges, radius, R=None, C=1.0, mode="physical", stream=None):
+        lib = _lib.load()
+        pn, nn, dn, kn = _as_buffer(nodes, np.float32, 3)
+        pe, ne, de, ke = _as_buffer(edges, np.int32, 2)
+        pr, nr, dr, kr = _as_buffer(radius, np.float32, 1)
+        if nr != ne:
+            raise ValueError("radius needs one value per edge")
+        if not (dn == de == dr):
+            raise ValueError("nodes, edges and radius must all be host or all device")
+        params = _lib.Params(float(R) if R else 0.0, float(C),
+                             _lib.MODE_RAW if mode == "raw" else _lib.MODE_PHYSICAL, int(dn))
+        h = ctypes.c_void_p()
+        _lib.check(lib.csl_lattice_upload(pn, nn, pe, pr, ne, ctypes.byref(params),
+                                          _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        del kn, ke, kr
+        info = self.info()
+        self.R, self.C = info.R, info.C
+        self.n_nodes, self.n_edges = info.n_nodes, info.n_edges
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> _lib.LatticeInfo:
+        out = _lib.LatticeInfo()
+        _lib.check(_lib.load().csl_lattice_get_info(self._h, ctypes.byref(out)))
+        return out
+
+    def update(self, nodes=None, radius=None, stream=None):
+        """Replace node positions / radii with CUDA tensors (same edges)."""
+        keep = []
+        pn = pr = None
+        if nodes is not None:
+            t = nodes.detach().to(torch.float32).contiguous()
+            keep.append(t)
+            pn = ctypes.c_void_p(t.data_ptr())
+        if radius is not None:
+            t = radius.detach().to(torch.float32).contiguous()
+            keep.append(t)
+            pr = ctypes.c_void_p(t.data_ptr())
+        _lib.check(_lib.load().csl_lattice_update(self._h, pn, pr, _stream_ptr(stream)))
+
+    def _desc(self, z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab, chunk_layers):
+        d = _lib.SliceDesc()
+        d.z0, d.dz, d.n_layers = float(z0), float(dz), int(n_layers)
+        d.nx, d.ny, d.flags = int(nx), int(ny), int(flags)
+        d.x0, d.y0, d.pixel = float(x0), float(y0), float(pixel)
+        d.sigma_out = ctypes.c_void_p(sigma_out.data_ptr()) if sigma_out is not None else None
+        d.tile, d.slab, d.chunk_layers = 0, int(slab), int(chunk_layers)
+        return d
+
+    def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None,
+              contours=True, on_device=False, edge_ids=False, slab=0, chunk_layers=0,
+              time_kernels=False, count_pairs=False, stream=None):
+        """csl_slice_layers. sigma_out: optional CUDA float32 tensor
+        [n_layers, ny, nx] that receives Sigma. Returns a ContourSet (host),
+        a DeviceContours (on_device=True) or None (contours=False)."""
+        if sigma_out is not None:
+            if not (sigma_out.is_cuda and sigma_out.dtype == torch.float32
+                    and sigma_out.is_contiguous()
+                    and sigma_out.numel() >= int(n_layers) * int(ny) * int(nx)):
+                raise ValueError("sigma_out must be a contiguous CUDA float32 tensor "
+                                 "of n_layers * ny * nx elements")
+        flags = 0
+        if not contours:
+            flags |= _lib.SLICE_NO_CONTOURS
+        if on_device:
+            flags |= _lib.SLICE_CONTOURS_ON_DEVICE
+        if edge_ids:
+            flags |= _lib.SLICE_EDGE_IDS
+        if time_kernels:
+            flags |= _lib.SLICE_TIME_KERNELS
+        if count_pairs:
+            flags |= _lib.SLICE_COUNT_PAIRS
+        d = self._desc(z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab,
+                       chunk_layers)
+        out = ctypes.POINTER(_lib.Contours)()
+        _lib.check(_lib.load().csl_slice_layers(self._h, ctypes.byref(d), _stream_ptr(stream),
+                                                ctypes.byref(out)))
+        if not contours:
+            return None
+        if on_device:
+            return DeviceContours(out)
+        try:
+            return _host_contours(out)
+        finally:
+            _lib.load().csl_contours_free(out)
+
+    def slab_bins(self, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny, pixel,
+                  stream=None):
+        """Binner output for one slab: (tile_off[n_tiles+1], edge ids sorted per tile)."""
+        d = self._desc(z0, dz, first_layer + n_slab_layers, x0, y0, nx, ny, pixel, 0, None,
+                       0, 0)
+        n_tiles = ((int(nx) + 15) // 16) * ((int(ny) + 15) // 16)
+        off = np.zeros(n_tiles + 1, np.int64)
+        n = ctypes.c_int64()
+        lib = _lib.load()
+        st = lib.csl_debug_slab_bins(self._h, ctypes.byref(d), int(first_layer),
+                                     int(n_slab_layers), off.ctypes.data_as(ctypes.c_void_p),
+                                     None, 0, ctypes.byref(n), _stream_ptr(stream))
+        if st not in (_lib.CSL_OK, 5):
+            _lib.check(st)
+        ids = np.zeros(max(1, n.value), np.int32)
+        _lib.check(lib.csl_debug_slab_bins(self._h, ctypes.byref(d), int(first_layer),
+                                           int(n_slab_layers), off.ctypes.data_as(ctypes.c_void_p),
+                                           ids.ctypes.data_as(ctypes.c_void_p), ids.size,
+                                           ctypes.byref(n), _stream_ptr(stream)))
+        return off, ids[:n.value]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().csl_lattice_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def last_stats() -> _lib.Stats:
+    s = _lib.Stats()
+    _lib.check(_lib.load().csl_last_stats(ctypes.byref(s)))
+    return s

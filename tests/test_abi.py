@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(csl_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("csl_lattice_upload", "csl_slice_layers", "csl_last_error", "csl_contours_free"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2101_05031_gb300 import _lib
+    lib = _lib.load()
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+    # the binding declares a signature for each one
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    assert declared_functions() <= bound
+
+
+def test_structs_match_header_layout(tmp_path):
+    """ctypes mirrors of the ABI structs have the header's size and offsets."""
+    from paper_2101_05031_gb300 import _lib
+    mirrors = {"csl_params": _lib.Params, "csl_lattice_info": _lib.LatticeInfo,
+               "csl_slice_desc": _lib.SliceDesc, "csl_contours": _lib.Contours,
+               "csl_stats": _lib.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for cname, py in mirrors.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_errors_cross_the_abi_as_codes():
+    """Host-side validation runs before any device work."""
+    from paper_2101_05031_gb300 import _lib
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    st = lib.csl_lattice_upload(None, -1, None, None, 0, None, None, ctypes.byref(out))
+    assert st == 1 and b"negative" in lib.csl_last_error()
+    st = lib.csl_lattice_upload(None, 0, None, None, 0, None, None, None)
+    assert st == 1
+    d = _lib.SliceDesc()
+    d.nx = d.ny = 10
+    d.pixel = 0.1
+    d.n_layers = 1
+    st = lib.csl_slice_layers(None, ctypes.byref(d), None, None)
+    assert st == 1 and b"NULL" in lib.csl_last_error()
+
+
+def test_no_gpu_reports_not_ready():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2101_05031_gb300 as cs
+    with pytest.raises(cs.CslError) as e:
+        cs.Lattice(np.zeros((2, 3), np.float32), np.array([[0, 1]], np.int32),
+                   np.array([0.1], np.float32))
+    assert e.value.code in (3, 6)
+
+
+def test_product_path_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2101_05031_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "cslice_oracle" not in src and "liboracle" not in src, f
