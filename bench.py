@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-count", action="store_true",
+                    help="skip the untimed pass that counts nonzero terms (profiling runs)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -234,16 +236,19 @@ def main():
 
     for _ in range(args.warmup):
         step()
-    # exact count of nonzero terms, once, outside the timed region
-    lat.slice(**kw, contours=False, count_pairs=True)
-    pairs = cs.last_stats().contributing_pairs
-    cand = cs.last_stats().candidate_pairs
+    # exact count of nonzero and of evaluated terms, once, outside the timed region
+    pairs = evaluated = cand = 0
+    if not args.no_count:
+        lat.slice(**kw, contours=False, count_pairs=True)
+        pairs = cs.last_stats().contributing_pairs
+        evaluated = cs.last_stats().evaluated_terms
+        cand = cs.last_stats().candidate_pairs
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    field_ms = 0.0
+    field_ms = bin_ms = contour_ms = output_ms = 0.0
     field_launches = 0
     launches = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -254,6 +259,9 @@ def main():
         for _ in range(args.steps):
             st, (n_loops, n_verts) = step(flags_time=True)
             field_ms += st.field_ms
+            bin_ms += st.bin_ms
+            contour_ms += st.contour_ms
+            output_ms += st.output_ms
             field_launches += st.field_launches
             launches += st.kernel_launches
         e1.record(stream)
@@ -278,7 +286,8 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "kernel": "k_field", "flops_per_term": F_PAIR,
-            "nonzero_terms_per_step": pairs, "candidate_entries_per_step": cand,
+            "nonzero_terms_per_step": pairs, "evaluated_terms_per_step": evaluated,
+            "candidate_entries_per_step": cand,
             "field_share_of_step": field_ms / ms if ms > 0 else None,
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)"}
     if clocks.get("sm_mhz"):
@@ -294,6 +303,9 @@ def main():
                        "parallelism": f"{world} GPU(s), layers offset per rank"},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
             "contours_per_step": {"loops": n_loops, "vertices": n_verts},
+            "phase_ms_per_step": {"bin": bin_ms / args.steps, "field": field_ms / args.steps,
+                                  "contours": contour_ms / args.steps,
+                                  "gather": output_ms / args.steps},
             "setup_s": {"generate": t_gen, "upload_and_sort": t_up}}
 
     if not args.no_e2e:

@@ -199,6 +199,10 @@ typedef struct csl_stats {
     int64_t field_launches;   /* launches of the field kernel                       */
     double field_ms;          /* their summed CUDA-event time (CSL_SLICE_TIME_KERNELS) */
     int64_t contributing_pairs; /* pairs with a nonzero term (CSL_SLICE_COUNT_PAIRS) */
+    double bin_ms;            /* CUDA-event time of the binner (CSL_SLICE_TIME_KERNELS) */
+    double contour_ms;        /* ... of marching squares and loop assembly            */
+    double output_ms;         /* ... of gathering the chunks into the result          */
+    int64_t evaluated_terms;  /* terms the field kernel evaluated (CSL_SLICE_COUNT_PAIRS) */
 } csl_stats;
 csl_status csl_last_stats(csl_stats* out);
 

@@ -51,7 +51,9 @@ class Contours(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("candidate_pairs", c_i64), ("crossings", c_i64), ("loops", c_i64),
                 ("chunks", c_i64), ("device_bytes_peak", c_i64), ("kernel_launches", c_i64),
-                ("field_launches", c_i64), ("field_ms", c_f64), ("contributing_pairs", c_i64)]
+                ("field_launches", c_i64), ("field_ms", c_f64), ("contributing_pairs", c_i64),
+                ("bin_ms", c_f64), ("contour_ms", c_f64), ("output_ms", c_f64),
+                ("evaluated_terms", c_i64)]
 
 
 class CellsDesc(ctypes.Structure):

@@ -74,7 +74,7 @@ Plan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
     require(chunk > 0 && (chunk % S == 0 || chunk >= d.n_layers),
             "chunk_layers must be a positive multiple of the slab depth");
     // marching squares needs < 2^27 edge words per chunk
-    const int64_t words_per_layer = 2 * ceil_div((int64_t)(d.nx + 2) * (d.ny + 2), 32);
+    const int64_t words_per_layer = 2 * mask_words_per_layer(d.nx, d.ny);
     if ((int64_t)chunk * words_per_layer >= ((int64_t)1 << 27)) {
         int64_t c = (((int64_t)1 << 27) - 1) / words_per_layer;
         c -= c % S;
@@ -129,13 +129,6 @@ void validate_desc(const csl_slice_desc* d) {
     require(isfinite(d->x0) && isfinite(d->y0) && isfinite(d->z0), "non-finite origin");
     require(d->n_layers <= 1 || (isfinite(d->dz) && d->dz > 0), "dz must be > 0");
 }
-
-struct HostContours {
-    std::vector<int64_t> layer_loop_off{0};
-    std::vector<int64_t> loop_off{0};
-    std::vector<float> xy;
-    std::vector<int32_t> eid;
-};
 
 }  // namespace
 
@@ -284,18 +277,40 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             CSL_CUDA(cudaEventCreate(&ev0));
             CSL_CUDA(cudaEventCreate(&ev1));
         }
+        // times the enqueued work of f() with events on the stream (when asked)
+        auto timed = [&](double& acc, const std::function<void()>& f) {
+            if (!time_kernels) { f(); return; }
+            CSL_CUDA(cudaEventRecord(ev0, s));
+            f();
+            CSL_CUDA(cudaEventRecord(ev1, s));
+            CSL_CUDA(cudaEventSynchronize(ev1));
+            float ms = 0.0f;
+            CSL_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+            acc += ms;
+        };
         DevBuf pair_count;
         if (count_pairs) {
-            pair_count.alloc(8, s);
-            CSL_CUDA(cudaMemsetAsync(pair_count.get(), 0, 8, s));
+            pair_count.alloc(16, s);
+            CSL_CUDA(cudaMemsetAsync(pair_count.get(), 0, 16, s));
         }
+        auto finish_stats = [&] {
+            if (time_kernels) {
+                cudaEventDestroy(ev0);
+                cudaEventDestroy(ev1);
+            }
+            st.device_bytes_peak = device_bytes_peak_and_reset();
+            st.kernel_launches = launches_and_reset();
+            t_stats = st;
+        };
 
         const int64_t plane = (int64_t)d.nx * d.ny;
-        DevBuf sigma_ws;
-        if (!d.sigma_out && d.n_layers > 0)
-            sigma_ws.alloc((size_t)std::min(p.chunk, d.n_layers) * plane * 4, s);
+        DevBuf sigma_ws, mask_ws;
+        const int chunk_alloc = std::min(p.chunk, std::max(d.n_layers, 1));
+        if (!d.sigma_out && d.n_layers > 0) sigma_ws.alloc((size_t)chunk_alloc * plane * 4, s);
+        const int64_t mask_layer = mask_words_per_layer(d.nx, d.ny);
+        if (want_contours && d.n_layers > 0)
+            mask_ws.alloc((size_t)chunk_alloc * mask_layer * 4, s);
 
-        HostContours hc;
         std::vector<ChunkContours> dev_chunks;
         for (int first = 0; first < d.n_layers; first += p.chunk) {
             const int n = std::min(p.chunk, d.n_layers - first);
@@ -303,130 +318,110 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane : sigma_ws.as<float>();
             {
                 SlabBins bins;
-                bin_chunk(L, g, bins, s);
+                timed(st.bin_ms, [&] { bin_chunk(L, g, bins, s); });
                 st.candidate_pairs += bins.n_pairs;
-                if (time_kernels) CSL_CUDA(cudaEventRecord(ev0, s));
-                field_chunk(L, g, bins, sigma,
-                            count_pairs ? pair_count.as<unsigned long long>() : nullptr, s);
+                uint32_t* mask = want_contours ? mask_ws.as<uint32_t>() : nullptr;
+                if (mask)
+                    CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, s));
+                timed(st.field_ms, [&] {
+                    field_chunk(L, g, bins, (float)L->C, sigma, mask,
+                                count_pairs ? pair_count.as<unsigned long long>() : nullptr, s);
+                });
                 ++st.field_launches;
-                if (time_kernels) {
-                    CSL_CUDA(cudaEventRecord(ev1, s));
-                    CSL_CUDA(cudaEventSynchronize(ev1));
-                    float ms = 0.0f;
-                    CSL_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-                    st.field_ms += ms;
-                }
             }
             ++st.chunks;
             if (!want_contours) continue;
             ChunkContours cc;
-            contours_chunk(g, L->C, sigma, want_eid, cc, s);
+            timed(st.contour_ms, [&] {
+                contours_chunk(g, L->C, sigma, mask_ws.as<uint32_t>(), want_eid, cc, s);
+            });
             st.crossings += cc.n_verts;
             st.loops += cc.n_loops;
-            if (on_dev) {
-                dev_chunks.push_back(std::move(cc));
-                continue;
-            }
-            // append to the host result (offsets rebased on the host)
-            std::vector<int64_t> ll(n + 1), lo(cc.n_loops + 1);
-            read_to_host(ll.data(), cc.layer_loops.get(), (n + 1) * 8, s);
-            read_to_host(lo.data(), cc.loop_off.get(), (cc.n_loops + 1) * 8, s);
-            int64_t loop_base = hc.loop_off.size() - 1, vert_base = hc.xy.size() / 2;
-            for (int l = 1; l <= n; ++l) hc.layer_loop_off.push_back(loop_base + ll[l]);
-            for (int64_t i = 1; i <= cc.n_loops; ++i) hc.loop_off.push_back(vert_base + lo[i]);
-            size_t old = hc.xy.size();
-            hc.xy.resize(old + 2 * cc.n_verts);
-            if (cc.n_verts)
-                read_to_host(hc.xy.data() + old, cc.xy.get(), cc.n_verts * 8, s);
-            if (want_eid) {
-                size_t oe = hc.eid.size();
-                hc.eid.resize(oe + cc.n_verts);
-                if (cc.n_verts)
-                    read_to_host(hc.eid.data() + oe, cc.eid.get(), cc.n_verts * 4, s);
-            }
-        }
-        if (want_contours && d.n_layers == 0 && !on_dev) {
-            // no layers: a single zero offset for layers and loops
+            dev_chunks.push_back(std::move(cc));
         }
         CSL_CUDA(cudaStreamSynchronize(s));
-        if (time_kernels) {
-            cudaEventDestroy(ev0);
-            cudaEventDestroy(ev1);
+        if (count_pairs) {
+            int64_t pc[2];
+            read_to_host(pc, pair_count.get(), 16, s);
+            st.contributing_pairs = pc[0];
+            st.evaluated_terms = pc[1];
         }
-        if (count_pairs) st.contributing_pairs = read_i64(pair_count.as<int64_t>(), s);
-        st.device_bytes_peak = device_bytes_peak_and_reset();
-        st.kernel_launches = launches_and_reset();
-        t_stats = st;
-        if (!want_contours) return;
+        if (!want_contours) {
+            finish_stats();
+            return;
+        }
 
+        // Gather the chunks into the result: offsets are rebased on the device,
+        // then every array is copied straight to its place (device or host).
         csl_contours* c = new csl_contours();
         memset(c, 0, sizeof(*c));
         c->n_layers = d.n_layers;
         c->on_device = on_dev ? 1 : 0;
-        if (!on_dev) {
-            c->n_loops = (int64_t)hc.loop_off.size() - 1;
-            c->n_verts = (int64_t)hc.xy.size() / 2;
-            c->layer_loop_off = (int64_t*)malloc(hc.layer_loop_off.size() * 8);
-            c->loop_vert_off = (int64_t*)malloc(hc.loop_off.size() * 8);
-            c->xy = (float*)malloc(std::max<size_t>(hc.xy.size(), 1) * 4);
-            if (want_eid) c->edge_id = (int32_t*)malloc(std::max<size_t>(hc.eid.size(), 1) * 4);
-            if (!c->layer_loop_off || !c->loop_vert_off || !c->xy || (want_eid && !c->edge_id)) {
-                csl_contours_free(c);
-                fail(CSL_ERR_OOM, "host allocation of the contours failed");
-            }
-            memcpy(c->layer_loop_off, hc.layer_loop_off.data(), hc.layer_loop_off.size() * 8);
-            memcpy(c->loop_vert_off, hc.loop_off.data(), hc.loop_off.size() * 8);
-            if (!hc.xy.empty()) memcpy(c->xy, hc.xy.data(), hc.xy.size() * 4);
-            if (want_eid && !hc.eid.empty()) memcpy(c->edge_id, hc.eid.data(), hc.eid.size() * 4);
-            *out = c;
-            return;
-        }
-        // device result: concatenate the chunks, rebasing their offsets
         int64_t n_loops = 0, n_verts = 0;
         for (auto& cc : dev_chunks) { n_loops += cc.n_loops; n_verts += cc.n_verts; }
         c->n_loops = n_loops;
         c->n_verts = n_verts;
-        auto dmalloc = [&](void** p, size_t b) {
-            cudaError_t e = cudaMalloc(p, b ? b : 16);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                csl_contours_free(c);
-                fail(CSL_ERR_OOM, "device allocation of the contours failed");
+        auto give_up = [&](const char* what) {
+            csl_contours_free(c);
+            fail(CSL_ERR_OOM, what);
+        };
+        auto dst_alloc = [&](void** p, size_t b) {
+            if (on_dev) {
+                if (cudaMalloc(p, b ? b : 16) != cudaSuccess) {
+                    cudaGetLastError();
+                    give_up("device allocation of the contours failed");
+                }
+            } else {
+                *p = malloc(b ? b : 16);
+                if (!*p) give_up("host allocation of the contours failed");
             }
         };
-        dmalloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8);
-        dmalloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
-        dmalloc((void**)&c->xy, (size_t)n_verts * 8);
-        if (want_eid) dmalloc((void**)&c->edge_id, (size_t)n_verts * 4);
-        int64_t lb = 0, vb = 0;
-        int layer = 0;
-        CSL_CUDA(cudaMemsetAsync(c->layer_loop_off, 0, 8, s));
-        CSL_CUDA(cudaMemsetAsync(c->loop_vert_off, 0, 8, s));
-        for (auto& cc : dev_chunks) {
-            const int n = std::min(p.chunk, d.n_layers - layer);
-            CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off + layer + 1, cc.layer_loops.as<int64_t>() + 1,
-                                     n * 8, cudaMemcpyDeviceToDevice, s));
-            k_add_i64<<<grid_for(n, 256), 256, 0, s>>>(c->layer_loop_off + layer + 1, n, lb);
-            CSL_LAUNCH_CHECK("rebase layer offsets");
-            if (cc.n_loops) {
-                CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off + lb + 1, cc.loop_off.as<int64_t>() + 1,
-                                         cc.n_loops * 8, cudaMemcpyDeviceToDevice, s));
-                k_add_i64<<<grid_for(cc.n_loops, 256), 256, 0, s>>>(c->loop_vert_off + lb + 1,
-                                                                   cc.n_loops, vb);
-                CSL_LAUNCH_CHECK("rebase loop offsets");
+        dst_alloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8);
+        dst_alloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
+        dst_alloc((void**)&c->xy, (size_t)n_verts * 8);
+        if (want_eid) dst_alloc((void**)&c->edge_id, (size_t)n_verts * 4);
+        const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        timed(st.output_ms, [&] {
+            int64_t lb = 0, vb = 0;
+            int layer = 0;
+            for (auto& cc : dev_chunks) {
+                const int n = std::min(p.chunk, d.n_layers - layer);
+                if (lb) {
+                    k_add_i64<<<grid_for(n + 1, 256), 256, 0, s>>>(cc.layer_loops.as<int64_t>(),
+                                                                   n + 1, lb);
+                    CSL_LAUNCH_CHECK("rebase layer offsets");
+                }
+                if (vb) {
+                    k_add_i64<<<grid_for(cc.n_loops + 1, 256), 256, 0, s>>>(
+                        cc.loop_off.as<int64_t>(), cc.n_loops + 1, vb);
+                    CSL_LAUNCH_CHECK("rebase loop offsets");
+                }
+                // entry 0 of each chunk duplicates the previous chunk's last entry
+                CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off + layer, cc.layer_loops.get(),
+                                         (size_t)(n + 1) * 8, kind, s));
+                CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off + lb, cc.loop_off.get(),
+                                         (size_t)(cc.n_loops + 1) * 8, kind, s));
+                if (cc.n_verts) {
+                    CSL_CUDA(cudaMemcpyAsync(c->xy + 2 * vb, cc.xy.get(), cc.n_verts * 8, kind, s));
+                    if (want_eid)
+                        CSL_CUDA(cudaMemcpyAsync(c->edge_id + vb, cc.eid.get(), cc.n_verts * 4,
+                                                 kind, s));
+                }
+                lb += cc.n_loops;
+                vb += cc.n_verts;
+                layer += n;
             }
-            if (cc.n_verts) {
-                CSL_CUDA(cudaMemcpyAsync(c->xy + 2 * vb, cc.xy.get(), cc.n_verts * 8,
-                                         cudaMemcpyDeviceToDevice, s));
-                if (want_eid)
-                    CSL_CUDA(cudaMemcpyAsync(c->edge_id + vb, cc.eid.get(), cc.n_verts * 4,
-                                             cudaMemcpyDeviceToDevice, s));
+            if (d.n_layers == 0) {
+                const int64_t zero = 0;
+                CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off, &zero, 8,
+                                         on_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+                CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off, &zero, 8,
+                                         on_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
             }
-            lb += cc.n_loops;
-            vb += cc.n_verts;
-            layer += n;
-        }
-        CSL_CUDA(cudaStreamSynchronize(s));
+            CSL_CUDA(cudaStreamSynchronize(s));
+        });
+        dev_chunks.clear();
+        finish_stats();
         *out = c;
     });
 }

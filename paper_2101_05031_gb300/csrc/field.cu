@@ -37,16 +37,28 @@ struct FieldConst {
     int32_t first_layer;   // global index of the chunk's first layer
     double x0, y0, px, z0, dz;
     float R2, inv_R4, fpx, fdz, cull;
+    float cull_line2;   // (cull + half-diagonal of a warp's pixel block)^2
+    float C;            // iso-value (inside mask)
+    int32_t mwr;        // mask words per row
+    int64_t mask_wpl;   // mask words per layer
 };
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <int S, bool COUNT>
-__global__ void __launch_bounds__(kFieldThreads, 2)
+__global__ void __launch_bounds__(kFieldThreads, 3)
 k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
         const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
-        float* __restrict__ sigma, unsigned long long* __restrict__ n_pairs) {
+        float* __restrict__ sigma, uint32_t* __restrict__ mask,
+        unsigned long long* __restrict__ n_pairs) {
     __shared__ float4 s_a[kFieldThreads];   // ax, ay, az (tile-local), ux
     __shared__ float4 s_b[kFieldThreads];   // uy, uz, len, w / R^4
     __shared__ uint64_t s_mask[kFieldThreads];   // bit warp*8 + layer
+    __shared__ float s_org[6];
 
     const int tile = blockIdx.x, slab = blockIdx.y;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
@@ -61,15 +73,24 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
     float acc[S];
 #pragma unroll
     for (int l = 0; l < S; ++l) acc[l] = 0.0f;
-    uint32_t n_nonzero = 0;
+    uint32_t n_nonzero = 0, n_eval = 0;
 
     if (end > beg) {
-        const double ox = c.x0 + (double)(tx * kTile) * c.px;
-        const double oy = c.y0 + (double)(ty * kTile) * c.px;
-        const double oz = c.z0 + (double)(c.first_layer + l0) * c.dz;
-        const float oxh = (float)ox, oxl = (float)(ox - (double)oxh);
-        const float oyh = (float)oy, oyl = (float)(oy - (double)oyh);
-        const float ozh = (float)oz, ozl = (float)(oz - (double)ozh);
+        if (threadIdx.x == 0) {   // the tile's corner, as a float pair per axis
+            const double ox = c.x0 + (double)(tx * kTile) * c.px;
+            const double oy = c.y0 + (double)(ty * kTile) * c.px;
+            const double oz = c.z0 + (double)(c.first_layer + l0) * c.dz;
+            const float oxh = (float)ox, oyh = (float)oy, ozh = (float)oz;
+            s_org[0] = oxh;
+            s_org[1] = (float)(ox - (double)oxh);
+            s_org[2] = oyh;
+            s_org[3] = (float)(oy - (double)oyh);
+            s_org[4] = ozh;
+            s_org[5] = (float)(oz - (double)ozh);
+        }
+        __syncthreads();
+        const float oxh = s_org[0], oxl = s_org[1], oyh = s_org[2], oyl = s_org[3];
+        const float ozh = s_org[4], ozl = s_org[5];
         const float pxl = ((float)il + 0.5f) * c.fpx;
         const float pyl = ((float)jl + 0.5f) * c.fpx;
         float zloc[S];
@@ -89,14 +110,14 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                 s_b[threadIdx.x] = make_float4(uy, uz, len, r1.w * c.inv_R4);
                 uint64_t m = 0;
                 const float inv_uz = uz > 1e-12f ? 1.0f / uz : 0.0f;
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    if (l >= nl) break;
+#pragma unroll 1
+                for (int l = 0; l < nl; ++l) {
+                    const float zl = (float)l * c.fdz;
                     float t_lo = 0.0f, t_hi = len;
                     if (uz > 1e-12f) {
-                        t_lo = fmaxf((zloc[l] - c.cull - az) * inv_uz, 0.0f);
-                        t_hi = fminf((zloc[l] + c.cull - az) * inv_uz, len);
-                    } else if (fabsf(az - zloc[l]) > c.cull) {
+                        t_lo = fmaxf((zl - c.cull - az) * inv_uz, 0.0f);
+                        t_hi = fminf((zl + c.cull - az) * inv_uz, len);
+                    } else if (fabsf(az - zl) > c.cull) {
                         t_lo = 1.0f;
                         t_hi = 0.0f;
                     }
@@ -105,13 +126,20 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                         float ya = fmaf(t_lo, uy, ay), yb = fmaf(t_hi, uy, ay);
                         float xmin = fminf(xa, xb) - c.cull, xmax = fmaxf(xa, xb) + c.cull;
                         float ymin = fminf(ya, yb) - c.cull, ymax = fmaxf(ya, yb) + c.cull;
+                        const float qz = zl - az;
 #pragma unroll
                         for (int w = 0; w < kFieldThreads / 32; ++w) {
                             float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
                             float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
                             float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
                             float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
-                            if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1)
+                            // and the block's centre within cull + half-diagonal of the line
+                            float qx = 0.5f * (rx0 + rx1) - ax, qy = 0.5f * (ry0 + ry1) - ay;
+                            float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
+                            float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy), ez = fmaf(-t, uz, qz);
+                            float dl2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                            if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1 &&
+                                dl2 <= c.cull_line2)
                                 m |= 1ull << (w * 8 + l);
                         }
                     }
@@ -140,7 +168,7 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                             const float ez = fmaf(-t0, B.y, dz);
                             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                             const float h2 = fmaxf(c.R2 - d2, 0.0f);
-                            const float w = h2 * rsqrtf(fmaxf(h2, 1e-30f));
+                            const float w = sqrt_approx(h2);
                             const float tau1 = fmaxf(-t0, -w);
                             const float tau2 = fminf(B.z - t0, w);
                             const float d = fmaxf(tau2 - tau1, 0.0f);   // 2 h
@@ -152,7 +180,10 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                             const float I = d * fmaf(5.0f / 9.0f, fmaf(Av, Av, B2),
                                                      (4.0f / 9.0f) * cc * cc);
                             acc[l] = fmaf(B.w, I, acc[l]);
-                            if (COUNT) n_nonzero += I > 0.0f;
+                            if (COUNT) {
+                                n_nonzero += I > 0.0f;
+                                ++n_eval;
+                            }
                         }
                     }
                 }
@@ -160,25 +191,54 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
             __syncthreads();
         }
     }
-    if (COUNT) {
-        unsigned long long t = n_nonzero;
+    if (COUNT) {   // n_pairs[0]: nonzero terms, n_pairs[1]: evaluated terms
+        unsigned long long t = n_nonzero, e = n_eval;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            t += __shfl_down_sync(0xffffffffu, t, o);
+            e += __shfl_down_sync(0xffffffffu, e, o);
+        }
         if (lane == 0 && t) atomicAdd(n_pairs, t);
+        if (lane == 0 && e) atomicAdd(n_pairs + 1, e);
     }
     const int gi = tx * kTile + il, gj = ty * kTile + jl;
-    if (gi < c.nx && gj < c.ny) {
+    const bool in_grid = gi < c.nx && gj < c.ny;
+    if (in_grid) {
 #pragma unroll
         for (int l = 0; l < S; ++l)
             if (l < nl) sigma[((int64_t)(l0 + l) * c.ny + gj) * c.nx + gi] = acc[l];
+    }
+    if (mask) {
+        // inside bits of the warp's 8 x 4 block: one byte per pixel row, OR-ed
+        // into the padded row (pixel i is padded sample i + 1)
+        const int I0 = tx * kTile + wx * 8 + 1;
+        const int sh = I0 & 31;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            if (l >= nl) break;
+            const uint32_t ball = __ballot_sync(0xffffffffu, in_grid && acc[l] >= c.C);
+            if (lane < 4) {
+                const uint32_t byte = (ball >> (8 * lane)) & 0xffu;
+                if (byte) {
+                    const int J = ty * kTile + wy * 4 + lane + 1;
+                    uint32_t* row = mask + (int64_t)(l0 + l) * c.mask_wpl + (int64_t)J * c.mwr;
+                    atomicOr(row + (I0 >> 5), byte << sh);
+                    const uint32_t hi = sh > 24 ? byte >> (32 - sh) : 0u;
+                    if (hi) atomicOr(row + (I0 >> 5) + 1, hi);
+                }
+            }
+        }
     }
 }
 
 }  // namespace
 
-void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float* sigma,
-                 unsigned long long* count_pairs, cudaStream_t s) {
+void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
+                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s) {
     FieldConst c;
+    c.C = C;
+    c.mwr = (int32_t)mask_words_per_row(g.nx);
+    c.mask_wpl = mask_words_per_layer(g.nx, g.ny);
     c.nx = g.nx;
     c.ny = g.ny;
     c.ntx = g.ntx;
@@ -195,6 +255,12 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     c.fpx = (float)g.px;
     c.fdz = (float)g.dz;
     c.cull = (float)(g.R * (1.0 + 1e-5) + 1e-6);
+    {
+        // pixel centres of a warp's 8 x 4 block lie within 3.5 x 1.5 pixels of its centre
+        double hd = g.px * sqrt(3.5 * 3.5 + 1.5 * 1.5) * (1.0 + 1e-5);
+        double r = (double)c.cull + hd;
+        c.cull_line2 = (float)(r * r);
+    }
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
     const csl_rec* rec = L->rec.as<csl_rec>();
     const uint32_t* vals = bins.vals.as<uint32_t>();
@@ -203,11 +269,11 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
 #define CSL_FIELD_CASE(SV)                                                                    \
     case SV:                                                                                  \
         if (count_pairs)                                                                      \
-            k_field<SV, true><<<grid, kFieldThreads, 0, s>>>(rec, vals, ts, te, c, sigma,      \
+            k_field<SV, true><<<grid, kFieldThreads, 0, s>>>(rec, vals, ts, te, c, sigma, mask,\
                                                              count_pairs);                    \
         else                                                                                  \
             k_field<SV, false><<<grid, kFieldThreads, 0, s>>>(rec, vals, ts, te, c, sigma,     \
-                                                              nullptr);                       \
+                                                              mask, nullptr);                 \
         break;
     switch (g.S) {
         CSL_FIELD_CASE(1)

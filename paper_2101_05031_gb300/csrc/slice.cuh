@@ -31,11 +31,20 @@ struct SlabBins {
 // Bins the lattice's records into (slab, tile) lists for one chunk.
 void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s);
 
-// Sigma for every pixel of the chunk's layers: sigma[layer][ny][nx].
-// count_pairs (device, may be null): adds the number of (pixel, layer, edge)
-// terms that are nonzero.
-void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float* sigma,
-                 unsigned long long* count_pairs, cudaStream_t s);
+// Inside mask of a chunk (the binary image of Sec. 4): bit I % 32 of word
+// [layer][J][I / 32] is set when padded sample (I, J), i.e. pixel (I-1, J-1),
+// has Sigma >= C. Rows J in [0, ny + 2); the padding ring stays 0.
+inline int64_t mask_words_per_row(int nx) { return ceil_div((int64_t)nx + 2, 32); }
+inline int64_t mask_words_per_layer(int nx, int ny) {
+    return mask_words_per_row(nx) * ((int64_t)ny + 2);
+}
+
+// Sigma for every pixel of the chunk's layers: sigma[layer][ny][nx], and the
+// inside mask (OR-ed into `mask`, which must be zero on entry; may be null).
+// count_pairs (device, may be null): [0] += the number of (pixel, layer, edge)
+// terms that are nonzero, [1] += the number of terms evaluated.
+void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
+                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s);
 
 // Contours of the chunk's layers (device arrays, layer-local edge ids).
 struct ChunkContours {
@@ -45,7 +54,7 @@ struct ChunkContours {
     DevBuf xy;            // float2 [n_verts]
     DevBuf eid;           // int32 [n_verts]
 };
-void contours_chunk(const ChunkGeom& g, double C, const float* sigma, bool want_eid,
-                    ChunkContours& out, cudaStream_t s);
+void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
+                    bool want_eid, ChunkContours& out, cudaStream_t s);
 
 }  // namespace csl

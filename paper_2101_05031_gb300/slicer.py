@@ -97,22 +97,36 @@ class DeviceContours:
             pass
 
 
+class _ContoursOwner:
+    """Frees a library-owned csl_contours when the last array viewing it dies."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        try:
+            _lib.load().csl_contours_free(self.ptr)
+        except Exception:
+            pass
+
+
 def _host_contours(ptr) -> ContourSet:
+    """Wraps the library's host arrays without copying them."""
     c = ptr.contents
+    owner = _ContoursOwner(ptr)
     nl, nloops, nv = c.n_layers, c.n_loops, c.n_verts
 
-    np_type = {ctypes.c_int64: np.int64, ctypes.c_float: np.float32, ctypes.c_int32: np.int32}
-
-    def arr(p, n, ct, shape=None):
+    def view(addr, n, ct, dtype):
         if n == 0:
-            return np.zeros(shape or (0,), dtype=np_type[ct])
-        a = np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ct)), shape=(n,)).copy()
-        return a.reshape(shape) if shape else a
+            return np.zeros(0, dtype=dtype)
+        buf = (ct * n).from_address(addr)
+        buf._owner = owner
+        return np.frombuffer(buf, dtype=dtype)
 
-    lo = arr(c.layer_loop_off, nl + 1, ctypes.c_int64)
-    vo = arr(c.loop_vert_off, nloops + 1, ctypes.c_int64)
-    xy = arr(c.xy, 2 * nv, ctypes.c_float, (nv, 2))
-    eid = arr(c.edge_id, nv, ctypes.c_int32) if c.edge_id else None
+    lo = view(c.layer_loop_off, nl + 1, ctypes.c_int64, np.int64)
+    vo = view(c.loop_vert_off, nloops + 1, ctypes.c_int64, np.int64)
+    xy = view(c.xy, 2 * nv, ctypes.c_float, np.float32).reshape(nv, 2)
+    eid = view(c.edge_id, nv, ctypes.c_int32, np.int32) if c.edge_id else None
     return ContourSet(lo, vo, xy, eid)
 
 
@@ -206,10 +220,7 @@ class Lattice:
             return None
         if on_device:
             return DeviceContours(out)
-        try:
-            return _host_contours(out)
-        finally:
-            _lib.load().csl_contours_free(out)
+        return _host_contours(out)
 
     def slab_bins(self, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny, pixel,
                   stream=None):
