@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--slab", type=int, default=0, help="layers per slab (0: library default)")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
     args = ap.parse_args()
@@ -221,6 +222,7 @@ def main():
     cfg = workload(args.workload)
     t_gen = time.perf_counter() - t_gen
     kw = slice_kwargs(cfg, rank, world)
+    kw["slab"] = args.slab
     stream = torch.cuda.current_stream()
 
     t_up = time.perf_counter()

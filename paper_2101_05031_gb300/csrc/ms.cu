@@ -29,6 +29,8 @@
 // is one load.
 #include <math.h>
 
+#include <algorithm>
+
 #include "slice.cuh"
 
 namespace csl {
@@ -208,12 +210,18 @@ __global__ void k_candidates(const Xing* __restrict__ rec, const uint32_t* __res
     }
 }
 
+// Walk kernels: loops have very uneven lengths, so every lane takes its next
+// candidate from a shared counter as soon as its walk ends (a persistent grid
+// of one wave), instead of a fixed share that waits for the longest loop.
+__device__ __forceinline__ int64_t next_item(uint32_t* counter) {
+    return (int64_t)atomicAdd(counter, 1u);
+}
+
 __global__ void k_heads(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, int64_t n,
-                        int64_t* __restrict__ packed, uint32_t* status) {
+                        const uint32_t* __restrict__ n_cand, uint32_t* __restrict__ counter,
+                        int64_t n, int64_t* __restrict__ packed, uint32_t* status) {
     const int64_t nc = *n_cand;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = next_item(counter); t < nc; t = next_item(counter)) {
         const uint32_t q = cand[t];
         uint32_t j = rec[q].succ;
         int64_t len = 1;
@@ -233,13 +241,12 @@ __global__ void k_heads(const Xing* __restrict__ rec, const uint32_t* __restrict
 }
 
 __global__ void k_write(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, const int64_t* __restrict__ packed,
-                        const int64_t* __restrict__ scan, int64_t n,
-                        int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
+                        const uint32_t* __restrict__ n_cand, uint32_t* __restrict__ counter,
+                        const int64_t* __restrict__ packed, const int64_t* __restrict__ scan,
+                        int64_t n, int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
                         int32_t* __restrict__ oeid) {
     const int64_t nc = *n_cand;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = next_item(counter); t < nc; t = next_item(counter)) {
         const uint32_t q = cand[t];
         const int64_t p = packed[q];
         if (p == 0) continue;
@@ -255,6 +262,14 @@ __global__ void k_write(const Xing* __restrict__ rec, const uint32_t* __restrict
             j = x.succ;
         }
     }
+}
+
+int persistent_blocks(const void* kernel, int block) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CSL_CUDA(cudaGetDevice(&dev));
+    CSL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CSL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0));
+    return std::max(1, sms * std::max(1, per_sm));
 }
 
 // layer_loops[l] = loops whose head lies before the first crossing of layer l
@@ -324,10 +339,10 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     }
     DevBuf pred((size_t)n_cross * 4, s), cand((size_t)n_cross * 4, s);
     DevBuf packed((size_t)n_cross * 8, s), scan((size_t)n_cross * 8, s);
-    DevBuf small(8, s);   // [0] status, [1] candidate count
+    DevBuf small(16, s);   // [0] status, [1] candidate count, [2], [3] work counters
     uint32_t* status = small.as<uint32_t>();
     uint32_t* n_cand = small.as<uint32_t>() + 1;
-    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8, s));
+    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 16, s));
     CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
@@ -335,8 +350,11 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     k_candidates<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
                                     cand.as<uint32_t>(), n_cand, packed.as<int64_t>());
     CSL_LAUNCH_CHECK("ms candidates");
-    k_heads<<<gx, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand, n_cross,
-                               packed.as<int64_t>(), status);
+    static int heads_blocks = persistent_blocks((const void*)k_heads, 256);
+    static int write_blocks = persistent_blocks((const void*)k_write, 256);
+    k_heads<<<heads_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand,
+                                         small.as<uint32_t>() + 2, n_cross, packed.as<int64_t>(),
+                                         status);
     CSL_LAUNCH_CHECK("ms heads");
     DevBuf tot(8, s);
     exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), n_cross, tot.as<int64_t>(), s);
@@ -351,9 +369,11 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
     out.xy.ensure((size_t)n_cross * 8, s);
     if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
-    k_write<<<gx, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand, packed.as<int64_t>(),
-                               scan.as<int64_t>(), n_cross, out.loop_off.as<int64_t>(),
-                               out.xy.as<float2>(), want_eid ? out.eid.as<int32_t>() : nullptr);
+    k_write<<<write_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand,
+                                         small.as<uint32_t>() + 3, packed.as<int64_t>(),
+                                         scan.as<int64_t>(), n_cross, out.loop_off.as<int64_t>(),
+                                         out.xy.as<float2>(),
+                                         want_eid ? out.eid.as<int32_t>() : nullptr);
     CSL_LAUNCH_CHECK("ms write");
     k_layer_loops<<<(unsigned)ceil_div(g.n_layers + 1, 128), 128, 0, s>>>(
         prefix.as<uint32_t>(), c.edge_wpl, g.n_layers, scan.as<int64_t>(), n_cross, n_loops,
