@@ -26,6 +26,8 @@
 // per-pixel evaluation is branch-free.
 #include <math.h>
 
+#include <vector>
+
 #include "slice.cuh"
 
 namespace csl {
@@ -39,6 +41,9 @@ struct FieldConst {
     float R2, inv_R4, fpx, fdz, cull;
     float cull_line2;   // (cull + half-diagonal of a warp's pixel block)^2
     float C;            // iso-value (inside mask)
+    const float2* org_x;   // per tile column: x of its first pixel edge, (hi, lo)
+    const float2* org_y;   // per tile row
+    const float2* org_z;   // per slab: z of its first layer
     int32_t mwr;        // mask words per row
     int64_t mask_wpl;   // mask words per layer
 };
@@ -58,7 +63,6 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
     __shared__ float4 s_a[kFieldThreads];   // ax, ay, az (tile-local), ux
     __shared__ float4 s_b[kFieldThreads];   // uy, uz, len, w / R^4
     __shared__ uint64_t s_mask[kFieldThreads];   // bit warp*8 + layer
-    __shared__ float s_org[6];
 
     const int tile = blockIdx.x, slab = blockIdx.y;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
@@ -76,21 +80,9 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
     uint32_t n_nonzero = 0, n_eval = 0;
 
     if (end > beg) {
-        if (threadIdx.x == 0) {   // the tile's corner, as a float pair per axis
-            const double ox = c.x0 + (double)(tx * kTile) * c.px;
-            const double oy = c.y0 + (double)(ty * kTile) * c.px;
-            const double oz = c.z0 + (double)(c.first_layer + l0) * c.dz;
-            const float oxh = (float)ox, oyh = (float)oy, ozh = (float)oz;
-            s_org[0] = oxh;
-            s_org[1] = (float)(ox - (double)oxh);
-            s_org[2] = oyh;
-            s_org[3] = (float)(oy - (double)oyh);
-            s_org[4] = ozh;
-            s_org[5] = (float)(oz - (double)ozh);
-        }
-        __syncthreads();
-        const float oxh = s_org[0], oxl = s_org[1], oyh = s_org[2], oyl = s_org[3];
-        const float ozh = s_org[4], ozl = s_org[5];
+        // the tile's corner and the slab's first plane, each a (hi, lo) float pair
+        const float2 ox = c.org_x[tx], oy = c.org_y[ty], oz = c.org_z[slab];
+        const float oxh = ox.x, oxl = ox.y, oyh = oy.x, oyl = oy.y, ozh = oz.x, ozl = oz.y;
         const float pxl = ((float)il + 0.5f) * c.fpx;
         const float pyl = ((float)jl + 0.5f) * c.fpx;
         float zloc[S];
@@ -129,18 +121,20 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                         const float qz = zl - az;
 #pragma unroll
                         for (int w = 0; w < kFieldThreads / 32; ++w) {
-                            float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
-                            float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
-                            float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
-                            float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
-                            // and the block's centre within cull + half-diagonal of the line
-                            float qx = 0.5f * (rx0 + rx1) - ax, qy = 0.5f * (ry0 + ry1) - ay;
-                            float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
-                            float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy), ez = fmaf(-t, uz, qz);
-                            float dl2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                            if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1 &&
-                                dl2 <= c.cull_line2)
-                                m |= 1ull << (w * 8 + l);
+                            const float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
+                            const float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
+                            const float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
+                            const float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
+                            if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1) {
+                                // and the block's centre within cull + half-diagonal of the line
+                                const float qx = 0.5f * (rx0 + rx1) - ax;
+                                const float qy = 0.5f * (ry0 + ry1) - ay;
+                                const float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
+                                const float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy);
+                                const float ez = fmaf(-t, uz, qz);
+                                if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= c.cull_line2)
+                                    m |= 1ull << (w * 8 + l);
+                            }
                         }
                     }
                 }
@@ -188,7 +182,7 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                     }
                 }
             }
-            __syncthreads();
+            if (c0 + kFieldThreads < end) __syncthreads();   // the next chunk reuses smem
         }
     }
     if (COUNT) {   // n_pairs[0]: nonzero terms, n_pairs[1]: evaluated terms
@@ -237,6 +231,22 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
                  float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s) {
     FieldConst c;
     c.C = C;
+    // tile and slab origins in double, each split into a (hi, lo) float pair
+    std::vector<float2> org((size_t)g.ntx + g.nty + g.n_slabs);
+    auto split = [](double v) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    for (int i = 0; i < g.ntx; ++i) org[i] = split(g.x0 + (double)(i * kTile) * g.px);
+    for (int j = 0; j < g.nty; ++j) org[g.ntx + j] = split(g.y0 + (double)(j * kTile) * g.px);
+    for (int k = 0; k < g.n_slabs; ++k)
+        org[g.ntx + g.nty + k] = split(g.z0 + (double)(g.first_layer + k * g.S) * g.dz);
+    DevBuf org_d(org.size() * sizeof(float2), s);
+    CSL_CUDA(cudaMemcpyAsync(org_d.get(), org.data(), org.size() * sizeof(float2),
+                             cudaMemcpyHostToDevice, s));
+    c.org_x = org_d.as<float2>();
+    c.org_y = c.org_x + g.ntx;
+    c.org_z = c.org_y + g.nty;
     c.mwr = (int32_t)mask_words_per_row(g.nx);
     c.mask_wpl = mask_words_per_layer(g.nx, g.ny);
     c.nx = g.nx;

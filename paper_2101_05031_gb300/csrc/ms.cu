@@ -210,18 +210,29 @@ __global__ void k_candidates(const Xing* __restrict__ rec, const uint32_t* __res
     }
 }
 
-// Walk kernels: loops have very uneven lengths, so every lane takes its next
-// candidate from a shared counter as soon as its walk ends (a persistent grid
-// of one wave), instead of a fixed share that waits for the longest loop.
-__device__ __forceinline__ int64_t next_item(uint32_t* counter) {
-    return (int64_t)atomicAdd(counter, 1u);
+// Walk kernels: loops have very uneven lengths. A persistent grid (one wave)
+// splits the candidate list into one contiguous range per block; inside the
+// block, each lane takes its next candidate from a shared-memory counter as
+// soon as its walk ends, so no lane waits for another's long loop.
+struct WorkRange {
+    int64_t begin, end;
+};
+
+__device__ __forceinline__ WorkRange block_range(int64_t nc) {
+    const int64_t per = (nc + gridDim.x - 1) / gridDim.x;
+    const int64_t b = (int64_t)blockIdx.x * per;
+    return {b < nc ? b : nc, b + per < nc ? b + per : nc};
 }
 
 __global__ void k_heads(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, uint32_t* __restrict__ counter,
-                        int64_t n, int64_t* __restrict__ packed, uint32_t* status) {
-    const int64_t nc = *n_cand;
-    for (int64_t t = next_item(counter); t < nc; t = next_item(counter)) {
+                        const uint32_t* __restrict__ n_cand, int64_t n,
+                        int64_t* __restrict__ packed, uint32_t* status) {
+    __shared__ uint32_t s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const WorkRange r = block_range(*n_cand);
+    for (int64_t t = r.begin + atomicAdd(&s_next, 1u); t < r.end;
+         t = r.begin + atomicAdd(&s_next, 1u)) {
         const uint32_t q = cand[t];
         uint32_t j = rec[q].succ;
         int64_t len = 1;
@@ -241,12 +252,16 @@ __global__ void k_heads(const Xing* __restrict__ rec, const uint32_t* __restrict
 }
 
 __global__ void k_write(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, uint32_t* __restrict__ counter,
-                        const int64_t* __restrict__ packed, const int64_t* __restrict__ scan,
-                        int64_t n, int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
+                        const uint32_t* __restrict__ n_cand, const int64_t* __restrict__ packed,
+                        const int64_t* __restrict__ scan, int64_t n,
+                        int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
                         int32_t* __restrict__ oeid) {
-    const int64_t nc = *n_cand;
-    for (int64_t t = next_item(counter); t < nc; t = next_item(counter)) {
+    __shared__ uint32_t s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const WorkRange r = block_range(*n_cand);
+    for (int64_t t = r.begin + atomicAdd(&s_next, 1u); t < r.end;
+         t = r.begin + atomicAdd(&s_next, 1u)) {
         const uint32_t q = cand[t];
         const int64_t p = packed[q];
         if (p == 0) continue;
@@ -255,10 +270,10 @@ __global__ void k_write(const Xing* __restrict__ rec, const uint32_t* __restrict
         const int64_t voff = scan[q] & 0xffffffffLL;
         loop_off[loop] = voff;
         uint32_t j = q;
-        for (int64_t r = 0; r < len && (int64_t)j < n; ++r) {
+        for (int64_t k = 0; k < len && (int64_t)j < n; ++k) {
             const Xing x = rec[j];
-            oxy[voff + r] = make_float2(x.x, x.y);
-            if (oeid) oeid[voff + r] = x.eid;
+            oxy[voff + k] = make_float2(x.x, x.y);
+            if (oeid) oeid[voff + k] = x.eid;
             j = x.succ;
         }
     }
@@ -339,10 +354,10 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     }
     DevBuf pred((size_t)n_cross * 4, s), cand((size_t)n_cross * 4, s);
     DevBuf packed((size_t)n_cross * 8, s), scan((size_t)n_cross * 8, s);
-    DevBuf small(16, s);   // [0] status, [1] candidate count, [2], [3] work counters
+    DevBuf small(8, s);   // [0] status, [1] candidate count
     uint32_t* status = small.as<uint32_t>();
     uint32_t* n_cand = small.as<uint32_t>() + 1;
-    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 16, s));
+    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8, s));
     CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
@@ -352,9 +367,8 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     CSL_LAUNCH_CHECK("ms candidates");
     static int heads_blocks = persistent_blocks((const void*)k_heads, 256);
     static int write_blocks = persistent_blocks((const void*)k_write, 256);
-    k_heads<<<heads_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand,
-                                         small.as<uint32_t>() + 2, n_cross, packed.as<int64_t>(),
-                                         status);
+    k_heads<<<heads_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand, n_cross,
+                                         packed.as<int64_t>(), status);
     CSL_LAUNCH_CHECK("ms heads");
     DevBuf tot(8, s);
     exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), n_cross, tot.as<int64_t>(), s);
@@ -370,7 +384,7 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     out.xy.ensure((size_t)n_cross * 8, s);
     if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
     k_write<<<write_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand,
-                                         small.as<uint32_t>() + 3, packed.as<int64_t>(),
+                                         packed.as<int64_t>(),
                                          scan.as<int64_t>(), n_cross, out.loop_off.as<int64_t>(),
                                          out.xy.as<float2>(),
                                          want_eid ? out.eid.as<int32_t>() : nullptr);
