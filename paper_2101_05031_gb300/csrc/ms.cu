@@ -19,12 +19,16 @@
 //      saddle (two inside corners on a diagonal) joins its inside corners when
 //      the mean of the 4 corner values is >= C, i.e. each entry turns to the
 //      next side, else to the previous one. Inside lies on the left.
-//   4. the head of a loop is its smallest id. Only local minima
-//      (pred > id < succ) can be heads; they are compacted into a list and
-//      each walks its loop until it meets a smaller id (not the head) or
-//      returns (the head, which then knows the loop length);
-//   5. a prefix sum over (is head, length) gives each head its loop index and
-//      first vertex; each head walks its loop again and writes its vertices.
+//   4. the head of a loop is its smallest id, which is a local minimum
+//      (pred > id < succ). Splitters = all local minima plus a hashed 1-in-32
+//      sample of crossings; each splitter walks its segment to the next
+//      splitter, so no thread walks a whole long loop;
+//   5. on the graph of splitters (one cycle per loop), pointer jumping gives
+//      every splitter its cycle's minimum (the head), and, with the cycles
+//      cut before their heads, weighted list ranking gives every segment its
+//      distance from the head;
+//   6. a prefix sum over the heads (loop length) numbers the loops in head
+//      order and places them; every splitter writes its segment there.
 // Crossings are 16-byte records {x, y, successor, edge id}, so one walk step
 // is one load.
 #include <math.h>
@@ -188,113 +192,155 @@ __global__ void k_pred(const Xing* __restrict__ rec, int64_t n, uint32_t* __rest
     }
 }
 
-// Local minima (pred > i < succ) into a compact list; packed[] cleared.
-__global__ void k_candidates(const Xing* __restrict__ rec, const uint32_t* __restrict__ pred,
-                             int64_t n, uint32_t* __restrict__ cand, uint32_t* __restrict__ n_cand,
-                             int64_t* __restrict__ packed) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        bool is_min = false;
-        if (i < n) {
-            const uint32_t q = (uint32_t)i;
-            is_min = pred[q] > q && rec[q].succ > q;
-            packed[i] = 0;
-        }
-        const uint32_t ball = __ballot_sync(0xffffffffu, is_min);
-        uint32_t pos = 0;
-        if (lane == 0 && ball) pos = atomicAdd(n_cand, (uint32_t)__popc(ball));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (is_min) cand[pos + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+// Splitters cut every loop into short segments: every local minimum
+// (pred > id < succ; the loop's smallest id is one) and a hashed 1-in-32
+// sample, so that a smooth loop with a single local minimum is cut too.
+__device__ __forceinline__ bool is_splitter(uint32_t i, uint32_t pred_i, uint32_t succ_i) {
+    return (pred_i > i && succ_i > i) || ((i * 2654435761u) >> 27) == 0u;
+}
+
+__global__ void k_split_flags(const Xing* __restrict__ rec, const uint32_t* __restrict__ pred,
+                              int64_t n, uint32_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t q = (uint32_t)i;
+        flag[i] = is_splitter(q, pred[q], rec[q].succ) ? 1u : 0u;
     }
 }
 
-// Walk kernels: loops have very uneven lengths. A persistent grid (one wave)
-// splits the candidate list into one contiguous range per block; inside the
-// block, each lane takes its next candidate from a shared-memory counter as
-// soon as its walk ends, so no lane waits for another's long loop.
-struct WorkRange {
-    int64_t begin, end;
-};
-
-__device__ __forceinline__ WorkRange block_range(int64_t nc) {
-    const int64_t per = (nc + gridDim.x - 1) / gridDim.x;
-    const int64_t b = (int64_t)blockIdx.x * per;
-    return {b < nc ? b : nc, b + per < nc ? b + per : nc};
+// spos: exclusive scan of flag. split_id[spos[i]] = i for splitters.
+__global__ void k_split_list(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ spos,
+                             int64_t n, uint32_t* __restrict__ split_id) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) split_id[spos[i]] = (uint32_t)i;
 }
 
-__global__ void k_heads(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, int64_t n,
-                        int64_t* __restrict__ packed, uint32_t* status) {
-    __shared__ uint32_t s_next;
-    if (threadIdx.x == 0) s_next = 0;
-    __syncthreads();
-    const WorkRange r = block_range(*n_cand);
-    for (int64_t t = r.begin + atomicAdd(&s_next, 1u); t < r.end;
-         t = r.begin + atomicAdd(&s_next, 1u)) {
-        const uint32_t q = cand[t];
-        uint32_t j = rec[q].succ;
+// Each splitter walks its segment up to the next splitter.
+__global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ flag,
+                           const uint32_t* __restrict__ spos, const uint32_t* __restrict__ split_id,
+                           int64_t ns, int64_t n, uint32_t* __restrict__ seg_next,
+                           uint32_t* __restrict__ seg_len, uint32_t* status) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t j = rec[split_id[t]].succ;
         int64_t len = 1;
-        bool head = true;
-        while (j != q) {
-            if (j < q) { head = false; break; }
-            if ((int64_t)j >= n || len > n) {   // corrupt links: report, never loop forever
-                atomicOr(status, ST_CAPACITY);
-                head = false;
-                break;
-            }
+        while ((int64_t)j < n && !flag[j] && len <= n) {
             j = rec[j].succ;
             ++len;
         }
-        if (head) packed[q] = ((int64_t)1 << 32) | len;
+        if ((int64_t)j >= n || len > n) {   // corrupt links: report, never loop forever
+            atomicOr(status, ST_CAPACITY);
+            seg_next[t] = (uint32_t)t;
+            seg_len[t] = 1;
+            continue;
+        }
+        seg_next[t] = spos[j];
+        seg_len[t] = (uint32_t)len;
     }
 }
 
-__global__ void k_write(const Xing* __restrict__ rec, const uint32_t* __restrict__ cand,
-                        const uint32_t* __restrict__ n_cand, const int64_t* __restrict__ packed,
-                        const int64_t* __restrict__ scan, int64_t n,
-                        int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
-                        int32_t* __restrict__ oeid) {
-    __shared__ uint32_t s_next;
-    if (threadIdx.x == 0) s_next = 0;
-    __syncthreads();
-    const WorkRange r = block_range(*n_cand);
-    for (int64_t t = r.begin + atomicAdd(&s_next, 1u); t < r.end;
-         t = r.begin + atomicAdd(&s_next, 1u)) {
-        const uint32_t q = cand[t];
-        const int64_t p = packed[q];
-        if (p == 0) continue;
-        const int64_t len = p & 0xffffffffLL;
-        const int64_t loop = scan[q] >> 32;
-        const int64_t voff = scan[q] & 0xffffffffLL;
-        loop_off[loop] = voff;
-        uint32_t j = q;
-        for (int64_t k = 0; k < len && (int64_t)j < n; ++k) {
+// One doubling step of the cycle minimum over the splitter graph:
+// (cm, nx) -> (min(cm, cm[nx]), nx[nx]). Runs only while the previous step
+// changed something (done[it - 1] != 0); sets done[it] when it changes cm.
+__global__ void k_jump_min(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ nx,
+                           uint32_t* __restrict__ cm2, uint32_t* __restrict__ nx2, int64_t ns,
+                           uint32_t* done, int it) {
+    if (it > 0 && done[it - 1] == 0) return;
+    bool changed = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = cm[t], nt = nx[t];
+        const uint32_t b = cm[nt];
+        const uint32_t m = b < a ? b : a;
+        changed |= m != a;
+        cm2[t] = m;
+        nx2[t] = nx[nt];
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0) done[it] = 1u;
+}
+
+// Break each cycle before its head (the splitter whose id is the cycle
+// minimum): nx = NIL there. dist = segment length.
+__global__ void k_break(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
+                        const uint32_t* __restrict__ seg_next, const uint32_t* __restrict__ seg_len,
+                        int64_t ns, uint32_t* __restrict__ nx, uint32_t* __restrict__ dist) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t nt = seg_next[t];
+        nx[t] = cm[nt] == split_id[nt] ? 0xffffffffu : nt;
+        dist[t] = seg_len[t];
+    }
+}
+
+// One doubling step of weighted list ranking: dist += dist[nx], nx = nx[nx].
+__global__ void k_jump_rank(const uint32_t* __restrict__ dist, const uint32_t* __restrict__ nx,
+                            uint32_t* __restrict__ dist2, uint32_t* __restrict__ nx2, int64_t ns,
+                            uint32_t* done, int it) {
+    if (it > 0 && done[it - 1] == 0) return;
+    bool live = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t nt = nx[t];
+        if (nt == 0xffffffffu) {
+            dist2[t] = dist[t];
+            nx2[t] = nt;
+        } else {
+            dist2[t] = dist[t] + dist[nt];
+            const uint32_t nn = nx[nt];
+            nx2[t] = nn;
+            live |= nn != 0xffffffffu;
+        }
+    }
+    if (__syncthreads_or(live) && threadIdx.x == 0) done[it] = 1u;
+}
+
+// packed[t] = (1 << 32) | loop length for heads, else 0 (splitter order).
+__global__ void k_head_flags(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
+                             const uint32_t* __restrict__ dist, int64_t ns,
+                             int64_t* __restrict__ packed) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x)
+        packed[t] = cm[t] == split_id[t] ? (((int64_t)1 << 32) | dist[t]) : 0;
+}
+
+// Each splitter writes its segment at loop offset + (loop length - dist).
+__global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ cm,
+                                 const uint32_t* __restrict__ spos,
+                                 const uint32_t* __restrict__ split_id,
+                                 const uint32_t* __restrict__ seg_len,
+                                 const uint32_t* __restrict__ dist,
+                                 const int64_t* __restrict__ scan, int64_t ns, int64_t n,
+                                 int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
+                                 int32_t* __restrict__ oeid) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t h = spos[cm[t]];               // the head splitter of this loop
+        const int64_t voff = scan[h] & 0xffffffffLL;
+        if (h == (uint32_t)t) loop_off[scan[h] >> 32] = voff;
+        const int64_t base = voff + (int64_t)dist[h] - (int64_t)dist[t];
+        uint32_t j = split_id[t];
+        const int64_t len = seg_len[t];
+        if (base < 0 || base + len > n) continue;   // only if the links were inconsistent
+        for (int64_t r = 0; r < len && (int64_t)j < n; ++r) {
             const Xing x = rec[j];
-            oxy[voff + k] = make_float2(x.x, x.y);
-            if (oeid) oeid[voff + k] = x.eid;
+            oxy[base + r] = make_float2(x.x, x.y);
+            if (oeid) oeid[base + r] = x.eid;
             j = x.succ;
         }
     }
 }
 
-int persistent_blocks(const void* kernel, int block) {
-    int dev = 0, sms = 0, per_sm = 0;
-    CSL_CUDA(cudaGetDevice(&dev));
-    CSL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CSL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0));
-    return std::max(1, sms * std::max(1, per_sm));
-}
-
 // layer_loops[l] = loops whose head lies before the first crossing of layer l
 __global__ void k_layer_loops(const uint32_t* __restrict__ prefix, int64_t edge_wpl, int n_layers,
-                              const int64_t* __restrict__ scan, int64_t n_cross, int64_t n_loops,
+                              const uint32_t* __restrict__ spos, const int64_t* __restrict__ scan,
+                              int64_t n_cross, int64_t ns, int64_t n_loops,
                               int64_t* __restrict__ layer_loops, int64_t* __restrict__ loop_off) {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l > n_layers) return;
-    int64_t first = l < n_layers ? (int64_t)prefix[(int64_t)l * edge_wpl] : n_cross;
-    layer_loops[l] = first < n_cross ? (scan[first] >> 32) : n_loops;
+    const int64_t first = l < n_layers ? (int64_t)prefix[(int64_t)l * edge_wpl] : n_cross;
+    const int64_t sp = first < n_cross ? (int64_t)spos[first] : ns;
+    layer_loops[l] = sp < ns ? (scan[sp] >> 32) : n_loops;
     if (l == 0) loop_off[n_loops] = n_cross;
 }
 
@@ -352,26 +398,87 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         k_emit<<<grid, 256, 0, s>>>(sigma, mask, c, D, rec.as<Xing>());
         CSL_LAUNCH_CHECK("ms emit");
     }
-    DevBuf pred((size_t)n_cross * 4, s), cand((size_t)n_cross * 4, s);
-    DevBuf packed((size_t)n_cross * 8, s), scan((size_t)n_cross * 8, s);
-    DevBuf small(8, s);   // [0] status, [1] candidate count
+    // ---- loops: splitters, segments, pointer jumping on the splitter graph
+    DevBuf pred((size_t)n_cross * 4, s), flag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
+    DevBuf small(8 + 4 * 128, s);   // [0] status, [1] splitter count, then done flags
     uint32_t* status = small.as<uint32_t>();
-    uint32_t* n_cand = small.as<uint32_t>() + 1;
-    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8, s));
+    uint32_t* done = small.as<uint32_t>() + 2;
+    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8 + 4 * 128, s));
     CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms pred");
-    k_candidates<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
-                                    cand.as<uint32_t>(), n_cand, packed.as<int64_t>());
-    CSL_LAUNCH_CHECK("ms candidates");
-    static int heads_blocks = persistent_blocks((const void*)k_heads, 256);
-    static int write_blocks = persistent_blocks((const void*)k_write, 256);
-    k_heads<<<heads_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand, n_cross,
-                                         packed.as<int64_t>(), status);
+    k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
+                                     flag.as<uint32_t>());
+    CSL_LAUNCH_CHECK("ms splitter flags");
+    exclusive_scan_u32(flag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, small.as<uint32_t>() + 1,
+                       s);
+    uint32_t head2[2];
+    read_to_host(head2, small.get(), 8, s);
+    if (head2[0]) fail(CSL_ERR_CUDA, "marching squares: a crossing has no successor");
+    const int64_t ns = head2[1];
+    pred.release();
+    DevBuf split_id((size_t)ns * 4, s), seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
+    DevBuf cmA((size_t)ns * 4, s), cmB((size_t)ns * 4, s), nxA((size_t)ns * 4, s),
+        nxB((size_t)ns * 4, s);
+    const unsigned gs = grid_for(ns, 256);
+    k_split_list<<<gx, 256, 0, s>>>(flag.as<uint32_t>(), spos.as<uint32_t>(), n_cross,
+                                    split_id.as<uint32_t>());
+    CSL_LAUNCH_CHECK("ms splitter list");
+    k_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), flag.as<uint32_t>(), spos.as<uint32_t>(),
+                                  split_id.as<uint32_t>(), ns, n_cross, seg_next.as<uint32_t>(),
+                                  seg_len.as<uint32_t>(), status);
+    CSL_LAUNCH_CHECK("ms segments");
+    flag.release();
+    // cycle minimum by doubling; a step that changes nothing ends it (no host sync)
+    int max_it = 1;
+    while (((int64_t)1 << max_it) < ns + 1) ++max_it;
+    max_it += 1;
+    if (max_it > 60) fail(CSL_ERR_CAPACITY, "marching squares: too many splitters");
+    CSL_CUDA(cudaMemcpyAsync(cmA.get(), split_id.get(), (size_t)ns * 4, cudaMemcpyDeviceToDevice, s));
+    CSL_CUDA(cudaMemcpyAsync(nxA.get(), seg_next.get(), (size_t)ns * 4, cudaMemcpyDeviceToDevice, s));
+    uint32_t *cm = cmA.as<uint32_t>(), *nx = nxA.as<uint32_t>();
+    uint32_t *cm2 = cmB.as<uint32_t>(), *nx2 = nxB.as<uint32_t>();
+    for (int it = 0; it < max_it; ++it) {
+        k_jump_min<<<gs, 256, 0, s>>>(cm, nx, cm2, nx2, ns, done, it);
+        CSL_LAUNCH_CHECK("ms cycle minimum");
+        std::swap(cm, cm2);
+        std::swap(nx, nx2);
+    }
+    // Steps after the first one that changed nothing return at once, so the
+    // result is in the buffer written by the last step that ran.
+    uint32_t done_h[64];
+    read_to_host(done_h, done, 4 * max_it, s);
+    {
+        int ran = 1;   // step 0 always runs
+        while (ran < max_it && done_h[ran - 1]) ++ran;
+        // step k writes buffer B when k is even, A when odd; after `ran` steps
+        // the result is in B if ran is odd, else A
+        cm = (ran & 1) ? cmB.as<uint32_t>() : cmA.as<uint32_t>();
+    }
+    DevBuf dA((size_t)ns * 4, s), dB((size_t)ns * 4, s);
+    uint32_t *nxr = nxA.as<uint32_t>(), *nxr2 = nxB.as<uint32_t>();   // free again
+    k_break<<<gs, 256, 0, s>>>(cm, split_id.as<uint32_t>(), seg_next.as<uint32_t>(),
+                               seg_len.as<uint32_t>(), ns, nxr, dA.as<uint32_t>());
+    CSL_LAUNCH_CHECK("ms break cycles");
+    CSL_CUDA(cudaMemsetAsync(done, 0, 4 * 64, s));
+    uint32_t *dist = dA.as<uint32_t>(), *dist2 = dB.as<uint32_t>();
+    for (int it = 0; it < max_it; ++it) {
+        k_jump_rank<<<gs, 256, 0, s>>>(dist, nxr, dist2, nxr2, ns, done, it);
+        CSL_LAUNCH_CHECK("ms list ranking");
+        std::swap(dist, dist2);
+        std::swap(nxr, nxr2);
+    }
+    read_to_host(done_h, done, 4 * max_it, s);
+    {
+        int ran = 1;
+        while (ran < max_it && done_h[ran - 1]) ++ran;
+        dist = (ran & 1) ? dB.as<uint32_t>() : dA.as<uint32_t>();
+    }
+    DevBuf packed((size_t)ns * 8, s), scan((size_t)ns * 8, s), tot(8, s);
+    k_head_flags<<<gs, 256, 0, s>>>(cm, split_id.as<uint32_t>(), dist, ns, packed.as<int64_t>());
     CSL_LAUNCH_CHECK("ms heads");
-    DevBuf tot(8, s);
-    exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), n_cross, tot.as<int64_t>(), s);
+    exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), ns, tot.as<int64_t>(), s);
     const int64_t packed_total = read_i64(tot.as<int64_t>(), s);
     uint32_t st = 0;
     read_to_host(&st, status, 4, s);
@@ -383,15 +490,15 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
     out.xy.ensure((size_t)n_cross * 8, s);
     if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
-    k_write<<<write_blocks, 256, 0, s>>>(rec.as<Xing>(), cand.as<uint32_t>(), n_cand,
-                                         packed.as<int64_t>(),
-                                         scan.as<int64_t>(), n_cross, out.loop_off.as<int64_t>(),
-                                         out.xy.as<float2>(),
-                                         want_eid ? out.eid.as<int32_t>() : nullptr);
+    k_write_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), cm, spos.as<uint32_t>(),
+                                        split_id.as<uint32_t>(), seg_len.as<uint32_t>(), dist,
+                                        scan.as<int64_t>(), ns, n_cross,
+                                        out.loop_off.as<int64_t>(), out.xy.as<float2>(),
+                                        want_eid ? out.eid.as<int32_t>() : nullptr);
     CSL_LAUNCH_CHECK("ms write");
     k_layer_loops<<<(unsigned)ceil_div(g.n_layers + 1, 128), 128, 0, s>>>(
-        prefix.as<uint32_t>(), c.edge_wpl, g.n_layers, scan.as<int64_t>(), n_cross, n_loops,
-        out.layer_loops.as<int64_t>(), out.loop_off.as<int64_t>());
+        prefix.as<uint32_t>(), c.edge_wpl, g.n_layers, spos.as<uint32_t>(), scan.as<int64_t>(),
+        n_cross, ns, n_loops, out.layer_loops.as<int64_t>(), out.loop_off.as<int64_t>());
     CSL_LAUNCH_CHECK("ms layer loops");
 }
 
