@@ -188,6 +188,41 @@ csl_status csl_debug_slab_bins(csl_lattice* lat, const csl_slice_desc* desc, int
                                int32_t n_slab_layers, int64_t* tile_off, int32_t* ids,
                                int64_t capacity, int64_t* n_ids, void* stream);
 
+/*
+ * csl_field_layers_static -- Sigma on the layers of desc for a lattice given
+ * as raw device arrays, WITHOUT allocating any memory. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory, e.g. an application that plans all of its device memory up front (a
+ * fixed budget or its own allocator that forbids outside allocations), or one
+ * that must not take the implicit device synchronisation of cudaMalloc and
+ * cudaFree. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   nodes_xyz, edges_ij, radius  device arrays as in csl_lattice_upload
+ *   R                            support radius, > 0 (no default here)
+ *   C, mode                      as csl_params (C = 0 means 1)
+ *   desc                         z0, dz, n_layers (<= 65535), x0, y0, nx, ny,
+ *                                pixel are used; everything else is ignored
+ *   sigma_out                    device float[n_layers][ny][nx] (caller-owned)
+ * Its only scratch is a fixed static device array that every GPU which loads
+ * this library keeps until the process exits: 256 bytes plus 32 bytes per
+ * edge for at most CSL_STATIC_MAX_EDGES edges (8 MiB + 256 bytes); larger
+ * inputs are rejected with CSL_ERR_CAPACITY. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Every call reuses the array (its status word is
+ * cleared, its records rewritten): calls whose GPU work overlaps, on other
+ * streams or host threads, race on it and must be serialised by the caller.
+ * Edges are summed in edge order (not z order), so values agree with
+ * csl_slice_layers within FP32 rounding, not bit for bit.
+ * Errors: INVALID_ARG for the csl_lattice_upload and csl_slice_layers input
+ * errors (bad index, non-finite value, radius <= 0 or >= R in PHYSICAL mode),
+ * reported after the GPU work, in which case sigma_out is unspecified.
+ * Synchronises the stream.
+ */
+#define CSL_STATIC_MAX_EDGES 262144
+csl_status csl_field_layers_static(const float* nodes_xyz, int64_t n_nodes, const int32_t* edges_ij,
+                                   const float* radius, int64_t n_edges, double R, double C,
+                                   int32_t mode, const csl_slice_desc* desc, float* sigma_out,
+                                   void* stream);
+
 /* Statistics of the last csl_slice_layers call on this thread. */
 typedef struct csl_stats {
     int64_t candidate_pairs;  /* (slab, tile, edge) entries produced by the binner */

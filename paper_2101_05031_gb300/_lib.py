@@ -23,6 +23,7 @@ SLICE_EDGE_IDS = 2
 SLICE_NO_CONTOURS = 4
 SLICE_TIME_KERNELS = 8
 SLICE_COUNT_PAIRS = 16
+STATIC_MAX_EDGES = 262144
 
 
 class Params(ctypes.Structure):
@@ -85,6 +86,8 @@ SIGNATURES = [
     ("csl_contours_copy", c_i32, [ctypes.POINTER(Contours), c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
     ("csl_debug_slab_bins", c_i32, [c_vp, ctypes.POINTER(SliceDesc), c_i32, c_i32, c_vp, c_vp,
                                     c_i64, ctypes.POINTER(c_i64), c_vp]),
+    ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
+                                        ctypes.POINTER(SliceDesc), c_vp, c_vp]),
 ]
 
 
