@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixel-evals/s and layers/s at 10M and 100M struts; backward/forward time ratio"
 F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the field kernel
+# DRAM bytes (read + write) per pixel-layer of one field-kernel launch, from an
+# ncu capture of the current field kernel on the 12.96M-strut graded lattice
+# (1.12 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
+FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.1226e9 / (64 * 2000 * 2000)
 N_SM = 152
 FP32_LANES = 128
 MAX_SM_MHZ = 2070.0
@@ -285,8 +289,13 @@ def main():
     flops_per_launch = pairs * F_PAIR / max(field_launches // args.steps, 1)
     achieved = flops_per_launch / t_field / 1e12 if t_field > 0 else 0.0
     peak = N_SM * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    px_layers_per_launch = cfg["nx"] * cfg["ny"] * cfg["n_layers"] / max(
+        field_launches // args.steps, 1)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak,
+            "traffic": FIELD_DRAM_BYTES_PER_PIXEL_LAYER * px_layers_per_launch,
+            "traffic_basis": "ncu dram bytes of one field launch on the 12.96M-strut graded "
+                             "lattice, scaled by pixel-layers per launch",
             "kernel": "k_field", "flops_per_term": F_PAIR,
             "nonzero_terms_per_step": pairs, "evaluated_terms_per_step": evaluated,
             "candidate_entries_per_step": cand,
