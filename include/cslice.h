@@ -189,6 +189,51 @@ csl_status csl_debug_slab_bins(csl_lattice* lat, const csl_slice_desc* desc, int
                                int64_t capacity, int64_t* n_ids, void* stream);
 
 /*
+ * Density cells (Eq. 9): cell (ix, iy, iz), 0 <= i* < dims[*], is the cube
+ * origin + h [i, i+1)^3; it is sampled at the m^3 points
+ * origin + h (i + (k + 1/2) / m), k in [0, m) per axis.
+ */
+typedef struct csl_cells {
+    double origin[3];
+    double h;                 /* cell edge (mm), > 0                                    */
+    int32_t dims[3];          /* cells per axis; dims[0] m, dims[1] m <= 32000          */
+    int32_t m;                /* samples per cell axis: 1, 2, 4 or 8                    */
+    double temperature;       /* T > 0 of the sigmoid (absolute; e.g. 0.01 C)           */
+} csl_cells;
+
+/*
+ * csl_volume_fraction -- smoothed volume fraction of the solid in every cell:
+ *   vf[iz][iy][ix] = (1/m^3) sum over the cell's samples p of
+ *                    1 / (1 + exp(-(Sigma(p) - C) / T)),
+ * the density of Eq. 9 with the Monte-Carlo hit count replaced by stratified
+ * samples and a sigmoid, so that it is differentiable (radius tuning, Sec.
+ * 5.4). vf_out: device float[dims[2]][dims[1]][dims[0]] (caller-owned).
+ * Errors: INVALID_ARG for bad cells (see csl_cells) or NULL pointers.
+ * Synchronises the stream.
+ */
+csl_status csl_volume_fraction(csl_lattice* lat, const csl_cells* cells, float* vf_out,
+                               void* stream);
+
+/*
+ * csl_volume_fraction_backward -- gradient of a scalar loss L with respect to
+ * every radius and node position, given grad_vf = dL/dvf (device, the layout
+ * of vf_out). Sigma is recomputed (nothing is kept from the forward call).
+ *   dL/drho_j = sum_c grad_vf_c (1/m^3) sum_p s(1-s)/T * I_j(p) * dw_j/drho_j
+ *   dL/dv_i   = sum over the edges at node i of the same factor times
+ *               w_j dI_j/d(endpoint)
+ * with s the sigmoid at p, I_j the segment integral of Eq. 7 and w_j the
+ * weight (PHYSICAL: dw/drho = w 5 rho / (R^2 - rho^2); RAW: 1). R and C are
+ * held fixed.
+ *   grad_radius  device float[n_edges]   (overwritten)
+ *   grad_nodes   device float[n_nodes][3] (overwritten)
+ * The sums run in a fixed order: results are deterministic.
+ * Synchronises the stream.
+ */
+csl_status csl_volume_fraction_backward(csl_lattice* lat, const csl_cells* cells,
+                                        const float* grad_vf, float* grad_radius,
+                                        float* grad_nodes, void* stream);
+
+/*
  * csl_field_layers_static -- Sigma on the layers of desc for a lattice given
  * as raw device arrays, WITHOUT allocating any memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device

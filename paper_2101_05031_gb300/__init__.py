@@ -6,4 +6,13 @@ include/cslice.h). This package only marshals arguments to it.
 from ._lib import CslError, load  # noqa: F401
 from .slicer import ContourSet, DeviceContours, Lattice, last_stats  # noqa: F401
 
-__all__ = ["Lattice", "ContourSet", "DeviceContours", "CslError", "load", "last_stats"]
+__all__ = ["Lattice", "ContourSet", "DeviceContours", "CslError", "load", "last_stats",
+           "volume_fraction", "volume_fraction_backward", "VolumeFraction"]
+
+
+def __getattr__(name):
+    # the volume-fraction layer needs torch; import it on first use
+    if name in ("volume_fraction", "volume_fraction_backward", "VolumeFraction", "cells_desc"):
+        from . import vf
+        return getattr(vf, name)
+    raise AttributeError(name)

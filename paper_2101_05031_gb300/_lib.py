@@ -86,6 +86,9 @@ SIGNATURES = [
     ("csl_contours_copy", c_i32, [ctypes.POINTER(Contours), c_vp, c_vp, c_vp, c_vp, c_i32, c_vp]),
     ("csl_debug_slab_bins", c_i32, [c_vp, ctypes.POINTER(SliceDesc), c_i32, c_i32, c_vp, c_vp,
                                     c_i64, ctypes.POINTER(c_i64), c_vp]),
+    ("csl_volume_fraction", c_i32, [c_vp, ctypes.POINTER(CellsDesc), c_vp, c_vp]),
+    ("csl_volume_fraction_backward", c_i32, [c_vp, ctypes.POINTER(CellsDesc), c_vp, c_vp, c_vp,
+                                             c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),
 ]

@@ -426,6 +426,39 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
     });
 }
 
+csl_status csl_volume_fraction(csl_lattice* L, const csl_cells* cells, float* vf_out,
+                               void* stream) {
+    return guard([&] {
+        require(L != nullptr, "lattice is NULL");
+        validate_cells_or_fail(cells);
+        require(vf_out != nullptr, "vf_out is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        launches_and_reset();
+        vf_forward(L, *cells, vf_out, s);
+        CSL_CUDA(cudaStreamSynchronize(s));
+        t_stats = csl_stats{};
+        t_stats.kernel_launches = launches_and_reset();
+    });
+}
+
+csl_status csl_volume_fraction_backward(csl_lattice* L, const csl_cells* cells,
+                                        const float* grad_vf, float* grad_radius,
+                                        float* grad_nodes, void* stream) {
+    return guard([&] {
+        require(L != nullptr, "lattice is NULL");
+        validate_cells_or_fail(cells);
+        require(grad_vf != nullptr, "grad_vf is NULL");
+        require(L->n_edges == 0 || grad_radius != nullptr, "grad_radius is NULL");
+        require(L->n_nodes == 0 || grad_nodes != nullptr, "grad_nodes is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        launches_and_reset();
+        vf_backward(L, *cells, grad_vf, grad_radius, grad_nodes, s);
+        CSL_CUDA(cudaStreamSynchronize(s));
+        t_stats = csl_stats{};
+        t_stats.kernel_launches = launches_and_reset();
+    });
+}
+
 csl_status csl_debug_slab_bins(csl_lattice* L, const csl_slice_desc* desc, int32_t first_layer,
                                int32_t n_slab_layers, int64_t* tile_off, int32_t* ids,
                                int64_t capacity, int64_t* n_ids, void* stream) {

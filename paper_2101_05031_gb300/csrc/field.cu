@@ -28,6 +28,7 @@
 
 #include <vector>
 
+#include "field_tile.cuh"
 #include "slice.cuh"
 
 namespace csl {
@@ -40,6 +41,7 @@ struct FieldConst {
     double x0, y0, px, z0, dz;
     float R2, inv_R4, fpx, fdz, cull;
     float cull_line2;   // (cull + half-diagonal of a warp's pixel block)^2
+    TileCull tc;        // the same values for stage_record
     float C;            // iso-value (inside mask)
     const float2* org_x;   // per tile column: x of its first pixel edge, (hi, lo)
     const float2* org_y;   // per tile row
@@ -47,12 +49,6 @@ struct FieldConst {
     int32_t mwr;        // mask words per row
     int64_t mask_wpl;   // mask words per layer
 };
-
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
 template <int S, bool COUNT>
 __global__ void __launch_bounds__(kFieldThreads, 3)
@@ -88,57 +84,16 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
         float zloc[S];
 #pragma unroll
         for (int l = 0; l < S; ++l) zloc[l] = (float)l * c.fdz;
+        const TileCull cull = c.tc;
 
         for (uint32_t c0 = beg; c0 < end; c0 += kFieldThreads) {
             const int cnt = (int)min((uint32_t)kFieldThreads, end - c0);
             if ((int)threadIdx.x < cnt) {
-                const float4* rp = reinterpret_cast<const float4*>(rec + vals[c0 + threadIdx.x]);
-                float4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-                float ax = (r0.x - oxh) - oxl;
-                float ay = (r0.y - oyh) - oyl;
-                float az = (r0.z - ozh) - ozl;
-                float ux = r0.w, uy = r1.x, uz = r1.y, len = r1.z;
-                s_a[threadIdx.x] = make_float4(ax, ay, az, ux);
-                s_b[threadIdx.x] = make_float4(uy, uz, len, r1.w * c.inv_R4);
-                uint64_t m = 0;
-                const float inv_uz = uz > 1e-12f ? 1.0f / uz : 0.0f;
-#pragma unroll 1
-                for (int l = 0; l < nl; ++l) {
-                    const float zl = (float)l * c.fdz;
-                    float t_lo = 0.0f, t_hi = len;
-                    if (uz > 1e-12f) {
-                        t_lo = fmaxf((zl - c.cull - az) * inv_uz, 0.0f);
-                        t_hi = fminf((zl + c.cull - az) * inv_uz, len);
-                    } else if (fabsf(az - zl) > c.cull) {
-                        t_lo = 1.0f;
-                        t_hi = 0.0f;
-                    }
-                    if (t_lo <= t_hi) {
-                        float xa = fmaf(t_lo, ux, ax), xb = fmaf(t_hi, ux, ax);
-                        float ya = fmaf(t_lo, uy, ay), yb = fmaf(t_hi, uy, ay);
-                        float xmin = fminf(xa, xb) - c.cull, xmax = fmaxf(xa, xb) + c.cull;
-                        float ymin = fminf(ya, yb) - c.cull, ymax = fmaxf(ya, yb) + c.cull;
-                        const float qz = zl - az;
-#pragma unroll
-                        for (int w = 0; w < kFieldThreads / 32; ++w) {
-                            const float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
-                            const float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
-                            const float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
-                            const float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
-                            if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1) {
-                                // and the block's centre within cull + half-diagonal of the line
-                                const float qx = 0.5f * (rx0 + rx1) - ax;
-                                const float qy = 0.5f * (ry0 + ry1) - ay;
-                                const float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
-                                const float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy);
-                                const float ez = fmaf(-t, uz, qz);
-                                if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= c.cull_line2)
-                                    m |= 1ull << (w * 8 + l);
-                            }
-                        }
-                    }
-                }
-                s_mask[threadIdx.x] = m;
+                float4 A, B;
+                s_mask[threadIdx.x] = stage_record(rec + vals[c0 + threadIdx.x], oxh, oxl, oyh,
+                                                   oyl, ozh, ozl, nl, cull, A, B);
+                s_a[threadIdx.x] = A;
+                s_b[threadIdx.x] = B;
             }
             __syncthreads();
             for (int i0 = 0; i0 < cnt; i0 += 32) {
@@ -162,17 +117,7 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                             const float ez = fmaf(-t0, B.y, dz);
                             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                             const float h2 = fmaxf(c.R2 - d2, 0.0f);
-                            const float w = sqrt_approx(h2);
-                            const float tau1 = fmaxf(-t0, -w);
-                            const float tau2 = fminf(B.z - t0, w);
-                            const float d = fmaxf(tau2 - tau1, 0.0f);   // 2 h
-                            const float s = tau2 + tau1;                 // 2 m
-                            const float cc = fmaf(-0.25f * s, s, h2);    // w^2 - m^2
-                            const float dd = 0.15f * d * d;              // 0.6 h^2
-                            const float Av = cc - dd;
-                            const float B2 = dd * s * s;                 // (2 m h sqrt(0.6))^2
-                            const float I = d * fmaf(5.0f / 9.0f, fmaf(Av, Av, B2),
-                                                     (4.0f / 9.0f) * cc * cc);
+                            const float I = segment_term_R4(t0, h2, B.z);
                             acc[l] = fmaf(B.w, I, acc[l]);
                             if (COUNT) {
                                 n_nonzero += I > 0.0f;
@@ -271,6 +216,11 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
         double r = (double)c.cull + hd;
         c.cull_line2 = (float)(r * r);
     }
+    c.tc.fpx = c.fpx;
+    c.tc.fdz = c.fdz;
+    c.tc.cull = c.cull;
+    c.tc.cull_line2 = c.cull_line2;
+    c.tc.inv_R4 = c.inv_R4;
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
     const csl_rec* rec = L->rec.as<csl_rec>();
     const uint32_t* vals = bins.vals.as<uint32_t>();

@@ -1,0 +1,104 @@
+// Device helpers shared by the field kernel and the volume-fraction adjoint:
+// staging one edge record for a (16x16-pixel tile, slab) CTA, the per-warp
+// cull mask, and the closed-form segment integral (Eq. 7) by 3-point
+// Gauss-Legendre on the clipped interval.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace csl {
+
+constexpr int kTileWarps = 8;   // a CTA = 8 warps, each an 8 x 4 pixel block
+
+struct TileCull {
+    float fpx, fdz;      // pixel size, layer spacing (float)
+    float cull;          // R plus rounding slack
+    float cull_line2;    // (cull + half-diagonal of a warp's pixel block)^2
+    float inv_R4;
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Loads record rp, converts it to coordinates relative to the tile corner and
+// the slab's first layer plane (each given as a (hi, lo) float pair) and
+// returns its cull mask: bit w * 8 + l is set when the edge's support (radius
+// cull) may reach a pixel centre of warp w's 8 x 4 block at layer l < nl,
+// i.e. when the block meets the xy box of the edge clipped to |z - z_l| <= cull
+// grown by cull, and the block's centre lies within cull + half-diagonal of
+// the edge's line. A = (ax, ay, az, ux), B = (uy, uz, len, w / R^4).
+__device__ __forceinline__ uint64_t stage_record(const csl_rec* rp_rec, float oxh, float oxl,
+                                                 float oyh, float oyl, float ozh, float ozl, int nl,
+                                                 const TileCull& c, float4& A, float4& B) {
+    const float4* rp = reinterpret_cast<const float4*>(rp_rec);
+    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    const float ax = (r0.x - oxh) - oxl;
+    const float ay = (r0.y - oyh) - oyl;
+    const float az = (r0.z - ozh) - ozl;
+    const float ux = r0.w, uy = r1.x, uz = r1.y, len = r1.z;
+    A = make_float4(ax, ay, az, ux);
+    B = make_float4(uy, uz, len, r1.w * c.inv_R4);
+    uint64_t m = 0;
+    const float inv_uz = uz > 1e-12f ? 1.0f / uz : 0.0f;
+#pragma unroll 1
+    for (int l = 0; l < nl; ++l) {
+        const float zl = (float)l * c.fdz;
+        float t_lo = 0.0f, t_hi = len;
+        if (uz > 1e-12f) {
+            t_lo = fmaxf((zl - c.cull - az) * inv_uz, 0.0f);
+            t_hi = fminf((zl + c.cull - az) * inv_uz, len);
+        } else if (fabsf(az - zl) > c.cull) {
+            t_lo = 1.0f;
+            t_hi = 0.0f;
+        }
+        if (t_lo <= t_hi) {
+            const float xa = fmaf(t_lo, ux, ax), xb = fmaf(t_hi, ux, ax);
+            const float ya = fmaf(t_lo, uy, ay), yb = fmaf(t_hi, uy, ay);
+            const float xmin = fminf(xa, xb) - c.cull, xmax = fmaxf(xa, xb) + c.cull;
+            const float ymin = fminf(ya, yb) - c.cull, ymax = fmaxf(ya, yb) + c.cull;
+            const float qz = zl - az;
+#pragma unroll
+            for (int w = 0; w < kTileWarps; ++w) {
+                const float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
+                const float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
+                const float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
+                const float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
+                if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1) {
+                    const float qx = 0.5f * (rx0 + rx1) - ax;
+                    const float qy = 0.5f * (ry0 + ry1) - ay;
+                    const float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
+                    const float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy);
+                    const float ez = fmaf(-t, uz, qz);
+                    if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= c.cull_line2)
+                        m |= 1ull << (w * 8 + l);
+                }
+            }
+        }
+    }
+    return m;
+}
+
+// In the frame of the edge: p - v_s = t0 u + e, h2 = max(R^2 - |e|^2, 0),
+// w = sqrt(h2); the edge covers tau = t - t0 in [tau1, tau2] =
+// [max(-t0, -w), min(L - t0, w)] and the kernel there is (h2 - tau^2)^2 / R^4.
+// Returns R^4 I = integral of (h2 - tau^2)^2 over [tau1, tau2], by 3-point
+// Gauss-Legendre (exact for this degree-4 polynomial, all terms >= 0). With
+// m = (tau1 + tau2)/2, h = (tau2 - tau1)/2, c = h2 - m^2, A = c - 0.6 h^2 and
+// B = 2 m h sqrt(0.6): R^4 I = h [(10/9)(A^2 + B^2) + (8/9) c^2].
+__device__ __forceinline__ float segment_term_R4(float t0, float h2, float len) {
+    const float w = sqrt_approx(h2);
+    const float tau1 = fmaxf(-t0, -w);
+    const float tau2 = fminf(len - t0, w);
+    const float d = fmaxf(tau2 - tau1, 0.0f);   // 2 h
+    const float s = tau2 + tau1;                 // 2 m
+    const float cc = fmaf(-0.25f * s, s, h2);    // h2 - m^2
+    const float dd = 0.15f * d * d;              // 0.6 h^2
+    const float Av = cc - dd;
+    const float B2 = dd * s * s;                 // (2 m h sqrt(0.6))^2
+    return d * fmaf(5.0f / 9.0f, fmaf(Av, Av, B2), (4.0f / 9.0f) * cc * cc);
+}
+
+}  // namespace csl

@@ -57,4 +57,10 @@ struct ChunkContours {
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
                     bool want_eid, ChunkContours& out, cudaStream_t s);
 
+// Volume fraction per density cell and its adjoint (vf.cu).
+void vf_forward(const csl_lattice* L, const csl_cells& cells, float* vf, cudaStream_t s);
+void vf_backward(csl_lattice* L, const csl_cells& cells, const float* grad_vf, float* grad_radius,
+                 float* grad_nodes, cudaStream_t s);
+void validate_cells_or_fail(const csl_cells* c);
+
 }  // namespace csl
