@@ -165,6 +165,64 @@ def oracle_sample(cfg, window=256, layer=None, min_seconds=8.0):
                       f"{sel.size} edges meeting the window given to the oracle"}
 
 
+# --------------------------------------------------------------------------- extra lines
+
+def _event_ms(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_vf(steps, warmup):
+    """Volume fraction and its adjoint on the 1M-strut Freudenthal lattice
+    (64^3 cells x 8^3 samples): ms per forward, per backward, and the ratio."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    import synth
+    from paper_2101_05031_gb300 import volume_fraction, volume_fraction_backward
+    cfg = synth.config(5)
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    cells = cfg["cells"]
+    d = cells["dims"]
+    stream = torch.cuda.current_stream()
+    vf = torch.empty((d[2], d[1], d[0]), device="cuda")
+    g = torch.randn((d[2], d[1], d[0]), device="cuda",
+                    generator=torch.Generator("cuda").manual_seed(0))
+    fwd = _event_ms(lambda: volume_fraction(lat, cells, out=vf), steps, warmup, stream)
+    bwd = _event_ms(lambda: volume_fraction_backward(lat, cells, g), steps, warmup, stream)
+    samples = d[0] * d[1] * d[2] * cells["m"] ** 3
+    return {"workload": cfg["name"], "forward_ms": fwd, "backward_ms": bwd,
+            "backward_forward_ratio": bwd / fwd, "samples_per_s_forward": samples / (fwd / 1e3),
+            "samples_per_s_backward": samples / (bwd / 1e3)}
+
+
+def run_10m(steps, warmup):
+    """Slicing throughput on the 10M-strut graded lattice."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    cfg = workload("graded-10M")
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    kw = slice_kwargs(cfg, 0, 1)
+
+    def step():
+        lat.slice(**kw, on_device=True).free()
+
+    ms = _event_ms(step, steps, warmup, torch.cuda.current_stream())
+    return {"workload": cfg["name"], "struts": int(cfg["edges"].shape[0]),
+            "pixel_evals_per_s": cfg["nx"] * cfg["ny"] * cfg["n_layers"] / (ms / 1e3),
+            "layers_per_s": cfg["n_layers"] / (ms / 1e3), "ms_per_step": ms}
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args, cfg, rank, world):
@@ -200,6 +258,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--slab", type=int, default=0, help="layers per slab (0: library default)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
     args = ap.parse_args()
@@ -349,6 +409,10 @@ def main():
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": e2e_ms}
 
+    if world == 1 and not args.no_extra:
+        del lat
+        line["at_10M"] = run_10m(args.steps, args.warmup)
+        line["volume_fraction"] = run_vf(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:
