@@ -51,14 +51,14 @@ struct FieldConst {
 };
 
 template <int S, bool COUNT>
-__global__ void __launch_bounds__(kFieldThreads, 3)
+__global__ void __launch_bounds__(kFieldThreads, 4)
 k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
         const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
         float* __restrict__ sigma, uint32_t* __restrict__ mask,
         unsigned long long* __restrict__ n_pairs) {
     __shared__ float4 s_a[kFieldThreads];   // ax, ay, az (tile-local), ux
     __shared__ float4 s_b[kFieldThreads];   // uy, uz, len, w / R^4
-    __shared__ uint64_t s_mask[kFieldThreads];   // bit warp*8 + layer
+    __shared__ uint64_t s_mask[kFieldThreads];   // byte l: warps reached at layer l
 
     const int tile = blockIdx.x, slab = blockIdx.y;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
@@ -90,15 +90,24 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
             const int cnt = (int)min((uint32_t)kFieldThreads, end - c0);
             if ((int)threadIdx.x < cnt) {
                 float4 A, B;
-                s_mask[threadIdx.x] = stage_record(rec + vals[c0 + threadIdx.x], oxh, oxl, oyh,
-                                                   oyl, ozh, ozl, nl, cull, A, B);
+                load_record(rec + vals[c0 + threadIdx.x], oxh, oxl, oyh, oyl, ozh, ozl,
+                            cull.inv_R4, A, B);
                 s_a[threadIdx.x] = A;
                 s_b[threadIdx.x] = B;
+                s_mask[threadIdx.x] = 0;
+            }
+            __syncthreads();
+            // cull masks: one (record, layer) item per thread; byte l of s_mask[r]
+            // holds the warps of layer l
+            for (int item = threadIdx.x; item < cnt * nl; item += kFieldThreads) {
+                const int r = item % cnt, l = item / cnt;
+                reinterpret_cast<uint8_t*>(s_mask)[8 * r + l] =
+                    (uint8_t)cull_layer(s_a[r], s_b[r], l, cull);
             }
             __syncthreads();
             for (int i0 = 0; i0 < cnt; i0 += 32) {
                 const int i = i0 + lane;
-                const uint32_t wm = i < cnt ? (uint32_t)(s_mask[i] >> (warp * 8)) & 0xffu : 0u;
+                const uint32_t wm = i < cnt ? warp_layers(s_mask[i], warp) : 0u;
                 uint32_t ball = __ballot_sync(0xffffffffu, wm != 0u);
                 while (ball) {
                     const int b = __ffs(ball) - 1;

@@ -81,6 +81,62 @@ __device__ __forceinline__ uint64_t stage_record(const csl_rec* rp_rec, float ox
     return m;
 }
 
+// Loads record rp into tile-local coordinates (see stage_record).
+__device__ __forceinline__ void load_record(const csl_rec* rp_rec, float oxh, float oxl, float oyh,
+                                            float oyl, float ozh, float ozl, float inv_R4,
+                                            float4& A, float4& B) {
+    const float4* rp = reinterpret_cast<const float4*>(rp_rec);
+    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    A = make_float4((r0.x - oxh) - oxl, (r0.y - oyh) - oyl, (r0.z - ozh) - ozl, r0.w);
+    B = make_float4(r1.x, r1.y, r1.z, r1.w * inv_R4);
+}
+
+// The warps of one layer l whose 8 x 4 block the staged edge (A, B) may reach
+// (the test of stage_record for a single layer): bit w set for warp w.
+__device__ __forceinline__ uint32_t cull_layer(const float4 A, const float4 B, int l,
+                                               const TileCull& c) {
+    const float ax = A.x, ay = A.y, az = A.z, ux = A.w, uy = B.x, uz = B.y, len = B.z;
+    const float zl = (float)l * c.fdz;
+    float t_lo = 0.0f, t_hi = len;
+    if (uz > 1e-12f) {
+        const float inv_uz = 1.0f / uz;
+        t_lo = fmaxf((zl - c.cull - az) * inv_uz, 0.0f);
+        t_hi = fminf((zl + c.cull - az) * inv_uz, len);
+    } else if (fabsf(az - zl) > c.cull) {
+        return 0u;
+    }
+    if (t_lo > t_hi) return 0u;
+    const float xa = fmaf(t_lo, ux, ax), xb = fmaf(t_hi, ux, ax);
+    const float ya = fmaf(t_lo, uy, ay), yb = fmaf(t_hi, uy, ay);
+    const float xmin = fminf(xa, xb) - c.cull, xmax = fmaxf(xa, xb) + c.cull;
+    const float ymin = fminf(ya, yb) - c.cull, ymax = fmaxf(ya, yb) + c.cull;
+    const float qz = zl - az;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < kTileWarps; ++w) {
+        const float rx0 = ((float)((w & 1) * 8) + 0.5f) * c.fpx;
+        const float rx1 = ((float)((w & 1) * 8) + 7.5f) * c.fpx;
+        const float ry0 = ((float)((w >> 1) * 4) + 0.5f) * c.fpx;
+        const float ry1 = ((float)((w >> 1) * 4) + 3.5f) * c.fpx;
+        if (xmax >= rx0 && xmin <= rx1 && ymax >= ry0 && ymin <= ry1) {
+            const float qx = 0.5f * (rx0 + rx1) - ax;
+            const float qy = 0.5f * (ry0 + ry1) - ay;
+            const float t = fmaf(qz, uz, fmaf(qy, uy, qx * ux));
+            const float ex = fmaf(-t, ux, qx), ey = fmaf(-t, uy, qy);
+            const float ez = fmaf(-t, uz, qz);
+            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= c.cull_line2) m |= 1u << w;
+        }
+    }
+    return m;
+}
+
+// Byte l of `bytes` holds the warp bits of layer l; returns warp w's layer
+// bits (bit l = layer l).
+__device__ __forceinline__ uint32_t warp_layers(uint64_t bytes, int w) {
+    const uint64_t b = (bytes >> w) & 0x0101010101010101ull;
+    return (uint32_t)((b * 0x0102040810204080ull) >> 56);
+}
+
 // In the frame of the edge: p - v_s = t0 u + e, h2 = max(R^2 - |e|^2, 0),
 // w = sqrt(h2); the edge covers tau = t - t0 in [tau1, tau2] =
 // [max(-t0, -w), min(L - t0, w)] and the kernel there is (h2 - tau^2)^2 / R^4.
