@@ -126,11 +126,14 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
                             const float ez = fmaf(-t0, B.y, dz);
                             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                             const float h2 = fmaxf(c.R2 - d2, 0.0f);
-                            const float I = segment_term_R4(t0, h2, B.z);
-                            acc[l] = fmaf(B.w, I, acc[l]);
-                            if (COUNT) {
-                                n_nonzero += I > 0.0f;
-                                ++n_eval;
+                            // the rest only when some pixel of the warp is within R
+                            if (__any_sync(0xffffffffu, h2 > 0.0f)) {
+                                const float I = segment_term_R4(t0, h2, B.z);
+                                acc[l] = fmaf(B.w, I, acc[l]);
+                                if (COUNT) {
+                                    n_nonzero += I > 0.0f;
+                                    ++n_eval;
+                                }
                             }
                         }
                     }

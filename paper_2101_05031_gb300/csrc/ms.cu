@@ -23,10 +23,11 @@
 //      (pred > id < succ). Splitters = all local minima plus a hashed 1-in-32
 //      sample of crossings; each splitter walks its segment to the next
 //      splitter, so no thread walks a whole long loop;
-//   5. on the graph of splitters (one cycle per loop), pointer jumping gives
-//      every splitter its cycle's minimum (the head), and, with the cycles
-//      cut before their heads, weighted list ranking gives every segment its
-//      distance from the head;
+//   5. on the graph of splitters (one cycle per loop), a cycle of at most 16
+//      splitters (every small loop) is resolved by walking it; on the rest,
+//      pointer jumping gives every splitter its cycle's minimum (the head)
+//      and, with the cycles cut before their heads, weighted list ranking
+//      gives every segment its distance from the head;
 //   6. a prefix sum over the heads (loop length) numbers the loops in head
 //      order and places them; every splitter writes its segment there.
 // Crossings are 16-byte records {x, y, successor, edge id}, so one walk step
@@ -90,17 +91,13 @@ __global__ void k_popc(const uint32_t* __restrict__ words, int64_t n, uint32_t* 
         cnt[i] = __popc(words[i]);
 }
 
+// Crossing numbering: the crossing on the edge with bit `bit` of edge word w
+// has id prefix[w] + popc(ew[w] & ((1 << bit) - 1)).
 struct Dense {
     const uint32_t* ew;
     const uint32_t* prefix;
     int64_t edge_wpl;
     int32_t ewr;
-    // id of the crossing on edge (I, J, b), b = 0 horizontal, 1 vertical
-    __device__ __forceinline__ uint32_t id(int layer, int I, int J, int b) const {
-        const int64_t w = layer * edge_wpl + (int64_t)J * ewr + (I >> 4);
-        const int bit = 2 * (I & 15) + b;
-        return prefix[w] + __popc(ew[w] & ((1u << bit) - 1u));
-    }
 };
 
 __device__ __forceinline__ float value_at(const float* __restrict__ sg, const MsConst& c, int I,
@@ -128,6 +125,25 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
     const uint32_t vr = (vb >> 1) | ((in1 ^ up1) << 31);           // right side
     const uint32_t ht = up ^ ((up >> 1) | (up1 << 31));            // top side
     uint32_t active = hb | vb | vr | ht;
+    if (!active) return;
+    // edge words (and their prefix sums) of this row's 32 samples, the next
+    // sample, and the row above: every crossing id below comes from registers
+    const int64_t wb = layer * D.edge_wpl + (int64_t)J * D.ewr + 2 * k;
+    const int64_t wu = wb + D.ewr;
+    const uint32_t e0 = D.ew[wb], e1 = D.ew[wb + 1], p0 = D.prefix[wb], p1 = D.prefix[wb + 1];
+    const uint32_t e2 = last ? 0u : D.ew[wb + 2], p2 = last ? 0u : D.prefix[wb + 2];
+    const uint32_t u0 = D.ew[wu], u1 = D.ew[wu + 1], q0 = D.prefix[wu], q1 = D.prefix[wu + 1];
+    // crossing on edge (32 k + si, J, b), si in [0, 32]; and (32 k + si, J + 1, 0)
+    auto id_row = [&](int si, int bb) -> uint32_t {
+        const int wsel = si >> 4, bit = 2 * (si & 15) + bb;
+        const uint32_t e = wsel == 0 ? e0 : (wsel == 1 ? e1 : e2);
+        const uint32_t p = wsel == 0 ? p0 : (wsel == 1 ? p1 : p2);
+        return p + __popc(e & ((1u << bit) - 1u));
+    };
+    auto id_up = [&](int si) -> uint32_t {
+        const uint32_t e = si < 16 ? u0 : u1, p = si < 16 ? q0 : q1;
+        return p + __popc(e & ((1u << (2 * (si & 15))) - 1u));
+    };
     while (active) {
         const int b = __ffs(active) - 1;
         active &= active - 1u;
@@ -141,7 +157,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         const float v3 = value_at(sg, c, I, J + 1);
         const int64_t eb = 2 * ((int64_t)J * c.W + I);
         if ((hb >> b) & 1u) {   // vertex on the bottom edge (I, J) -> (I+1, J)
-            const uint32_t id = D.id(layer, I, J, 0);
+            const uint32_t id = id_row(b, 0);
             const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
             const float t = (sa - c.C) / (sa - sbv);
             const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
@@ -150,7 +166,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
             rec[id].eid = (int32_t)eb;
         }
         if ((vb >> b) & 1u) {   // vertex on the left edge (I, J) -> (I, J+1)
-            const uint32_t id = D.id(layer, I, J, 1);
+            const uint32_t id = id_row(b, 1);
             const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
             const float t = (sa - c.C) / (sa - sbv);
             const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
@@ -163,10 +179,9 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         const uint32_t nxt = ((cs >> 1) | (cs << 3)) & 0xfu;
         const uint32_t enter = cs & ~nxt & 0xfu;   // inside -> outside
         const uint32_t leave = ~cs & nxt & 0xfu;   // outside -> inside
-        auto side = [&](int s) -> uint32_t {   // sides: 0 bottom, 1 right, 2 top, 3 left
-            return s == 0 ? D.id(layer, I, J, 0)
-                          : (s == 1 ? D.id(layer, I + 1, J, 1)
-                                    : (s == 2 ? D.id(layer, I, J + 1, 0) : D.id(layer, I, J, 1)));
+        auto side = [&](int sd) -> uint32_t {   // sides: 0 bottom, 1 right, 2 top, 3 left
+            return sd == 0 ? id_row(b, 0)
+                           : (sd == 1 ? id_row(b + 1, 1) : (sd == 2 ? id_up(b) : id_row(b, 1)));
         };
         if (__popc(enter) == 1) {
             rec[side(__ffs(enter) - 1)].succ = side(__ffs(leave) - 1);
@@ -260,19 +275,6 @@ __global__ void k_jump_min(const uint32_t* __restrict__ cm, const uint32_t* __re
     if (__syncthreads_or(changed) && threadIdx.x == 0) done[it] = 1u;
 }
 
-// Break each cycle before its head (the splitter whose id is the cycle
-// minimum): nx = NIL there. dist = segment length.
-__global__ void k_break(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
-                        const uint32_t* __restrict__ seg_next, const uint32_t* __restrict__ seg_len,
-                        int64_t ns, uint32_t* __restrict__ nx, uint32_t* __restrict__ dist) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t nt = seg_next[t];
-        nx[t] = cm[nt] == split_id[nt] ? 0xffffffffu : nt;
-        dist[t] = seg_len[t];
-    }
-}
-
 // One doubling step of weighted list ranking: dist += dist[nx], nx = nx[nx].
 __global__ void k_jump_rank(const uint32_t* __restrict__ dist, const uint32_t* __restrict__ nx,
                             uint32_t* __restrict__ dist2, uint32_t* __restrict__ nx2, int64_t ns,
@@ -295,21 +297,130 @@ __global__ void k_jump_rank(const uint32_t* __restrict__ dist, const uint32_t* _
     if (__syncthreads_or(live) && threadIdx.x == 0) done[it] = 1u;
 }
 
+// Splitter cycles of at most kShortCycle splitters (all the small loops) are
+// resolved by walking them; the rest go to pointer jumping on a compact list.
+constexpr int kShortCycle = 16;
+constexpr uint32_t kNil = 0xffffffffu;
+
+// cm[t] = the cycle's smallest splitter id when t's cycle closes within
+// kShortCycle steps; otherwise t is appended to the long list.
+__global__ void k_short_cycles(const uint32_t* __restrict__ split_id,
+                               const uint32_t* __restrict__ seg_next, int64_t ns,
+                               uint32_t* __restrict__ cm, uint32_t* __restrict__ long_list,
+                               uint32_t* __restrict__ long_pos, uint32_t* __restrict__ n_long) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ns;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        bool is_long = false;
+        if (t < ns) {
+            uint32_t v = seg_next[t], mn = split_id[t];
+            int n = 1;
+            while (v != (uint32_t)t && n < kShortCycle) {
+                const uint32_t id = split_id[v];
+                mn = id < mn ? id : mn;
+                v = seg_next[v];
+                ++n;
+            }
+            is_long = v != (uint32_t)t;
+            cm[t] = is_long ? kNil : mn;
+            long_pos[t] = kNil;
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, is_long);
+        uint32_t pos = 0;
+        if (lane == 0 && ball) pos = atomicAdd(n_long, (uint32_t)__popc(ball));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (is_long) {
+            const uint32_t q = pos + __popc(ball & ((1u << lane) - 1u));
+            long_list[q] = (uint32_t)t;
+            long_pos[t] = q;
+        }
+    }
+}
+
+// The head of each short cycle walks it: rank_start = crossings of the loop
+// before the segment, loop_len at the head.
+__global__ void k_short_ranks(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
+                              const uint32_t* __restrict__ seg_next,
+                              const uint32_t* __restrict__ seg_len, int64_t ns,
+                              uint32_t* __restrict__ rank_start, uint32_t* __restrict__ loop_len) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (cm[t] == kNil || cm[t] != split_id[t]) continue;   // long, or not a head
+        uint32_t acc = 0, v = (uint32_t)t;
+        int n = 0;
+        do {
+            rank_start[v] = acc;
+            acc += seg_len[v];
+            v = seg_next[v];
+        } while (v != (uint32_t)t && ++n < kShortCycle);
+        loop_len[t] = acc;
+    }
+}
+
+// Compact long-cycle graph: node u = long_list[u]; next in compact indices.
+__global__ void k_long_setup(const uint32_t* __restrict__ long_list,
+                             const uint32_t* __restrict__ long_pos,
+                             const uint32_t* __restrict__ split_id,
+                             const uint32_t* __restrict__ seg_next, int64_t nl,
+                             uint32_t* __restrict__ lcm, uint32_t* __restrict__ lnx) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nl;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = long_list[u];
+        lcm[u] = split_id[t];
+        lnx[u] = long_pos[seg_next[t]];
+    }
+}
+
+// Break each long cycle before its head (nx = NIL there); dist = segment length.
+__global__ void k_long_break(const uint32_t* __restrict__ lcm, const uint32_t* __restrict__ long_list,
+                             const uint32_t* __restrict__ long_pos,
+                             const uint32_t* __restrict__ split_id,
+                             const uint32_t* __restrict__ seg_next,
+                             const uint32_t* __restrict__ seg_len, int64_t nl,
+                             uint32_t* __restrict__ nx, uint32_t* __restrict__ dist) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nl;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = long_list[u];
+        const uint32_t nt = seg_next[t];
+        const uint32_t nu = long_pos[nt];
+        nx[u] = lcm[nu] == split_id[nt] ? kNil : nu;
+        dist[u] = seg_len[t];
+    }
+}
+
+// Back to splitter order: cm, rank_start = loop length - dist, loop_len at heads.
+__global__ void k_long_ranks(const uint32_t* __restrict__ lcm, const uint32_t* __restrict__ dist,
+                             const uint32_t* __restrict__ long_list,
+                             const uint32_t* __restrict__ long_pos,
+                             const uint32_t* __restrict__ spos, int64_t nl,
+                             uint32_t* __restrict__ cm, uint32_t* __restrict__ rank_start,
+                             uint32_t* __restrict__ loop_len) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nl;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = long_list[u];
+        const uint32_t hu = long_pos[spos[lcm[u]]];
+        cm[t] = lcm[u];
+        rank_start[t] = dist[hu] - dist[u];
+        if (hu == (uint32_t)u) loop_len[t] = dist[u];
+    }
+}
+
 // packed[t] = (1 << 32) | loop length for heads, else 0 (splitter order).
 __global__ void k_head_flags(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
-                             const uint32_t* __restrict__ dist, int64_t ns,
+                             const uint32_t* __restrict__ loop_len, int64_t ns,
                              int64_t* __restrict__ packed) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
          t += (int64_t)gridDim.x * blockDim.x)
-        packed[t] = cm[t] == split_id[t] ? (((int64_t)1 << 32) | dist[t]) : 0;
+        packed[t] = cm[t] == split_id[t] ? (((int64_t)1 << 32) | loop_len[t]) : 0;
 }
 
-// Each splitter writes its segment at loop offset + (loop length - dist).
+// Each splitter writes its segment at its loop's offset + rank_start.
 __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ cm,
                                  const uint32_t* __restrict__ spos,
                                  const uint32_t* __restrict__ split_id,
                                  const uint32_t* __restrict__ seg_len,
-                                 const uint32_t* __restrict__ dist,
+                                 const uint32_t* __restrict__ rank_start,
                                  const int64_t* __restrict__ scan, int64_t ns, int64_t n,
                                  int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
                                  int32_t* __restrict__ oeid) {
@@ -318,7 +429,7 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
         const uint32_t h = spos[cm[t]];               // the head splitter of this loop
         const int64_t voff = scan[h] & 0xffffffffLL;
         if (h == (uint32_t)t) loop_off[scan[h] >> 32] = voff;
-        const int64_t base = voff + (int64_t)dist[h] - (int64_t)dist[t];
+        const int64_t base = voff + (int64_t)rank_start[t];
         uint32_t j = split_id[t];
         const int64_t len = seg_len[t];
         if (base < 0 || base + len > n) continue;   // only if the links were inconsistent
@@ -400,7 +511,7 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
     DevBuf pred((size_t)n_cross * 4, s), flag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
-    DevBuf small(8 + 4 * 128, s);   // [0] status, [1] splitter count, then done flags
+    DevBuf small(8 + 4 * 128, s);   // [0] status, [1] splitters, [2..65] done, [66] long count
     uint32_t* status = small.as<uint32_t>();
     uint32_t* done = small.as<uint32_t>() + 2;
     CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8 + 4 * 128, s));
@@ -419,8 +530,6 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     const int64_t ns = head2[1];
     pred.release();
     DevBuf split_id((size_t)ns * 4, s), seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
-    DevBuf cmA((size_t)ns * 4, s), cmB((size_t)ns * 4, s), nxA((size_t)ns * 4, s),
-        nxB((size_t)ns * 4, s);
     const unsigned gs = grid_for(ns, 256);
     k_split_list<<<gx, 256, 0, s>>>(flag.as<uint32_t>(), spos.as<uint32_t>(), n_cross,
                                     split_id.as<uint32_t>());
@@ -430,53 +539,76 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
                                   seg_len.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms segments");
     flag.release();
-    // cycle minimum by doubling; a step that changes nothing ends it (no host sync)
-    int max_it = 1;
-    while (((int64_t)1 << max_it) < ns + 1) ++max_it;
-    max_it += 1;
-    if (max_it > 60) fail(CSL_ERR_CAPACITY, "marching squares: too many splitters");
-    CSL_CUDA(cudaMemcpyAsync(cmA.get(), split_id.get(), (size_t)ns * 4, cudaMemcpyDeviceToDevice, s));
-    CSL_CUDA(cudaMemcpyAsync(nxA.get(), seg_next.get(), (size_t)ns * 4, cudaMemcpyDeviceToDevice, s));
-    uint32_t *cm = cmA.as<uint32_t>(), *nx = nxA.as<uint32_t>();
-    uint32_t *cm2 = cmB.as<uint32_t>(), *nx2 = nxB.as<uint32_t>();
-    for (int it = 0; it < max_it; ++it) {
-        k_jump_min<<<gs, 256, 0, s>>>(cm, nx, cm2, nx2, ns, done, it);
-        CSL_LAUNCH_CHECK("ms cycle minimum");
-        std::swap(cm, cm2);
-        std::swap(nx, nx2);
-    }
-    // Steps after the first one that changed nothing return at once, so the
-    // result is in the buffer written by the last step that ran.
-    uint32_t done_h[64];
-    read_to_host(done_h, done, 4 * max_it, s);
-    {
-        int ran = 1;   // step 0 always runs
-        while (ran < max_it && done_h[ran - 1]) ++ran;
-        // step k writes buffer B when k is even, A when odd; after `ran` steps
-        // the result is in B if ran is odd, else A
-        cm = (ran & 1) ? cmB.as<uint32_t>() : cmA.as<uint32_t>();
-    }
-    DevBuf dA((size_t)ns * 4, s), dB((size_t)ns * 4, s);
-    uint32_t *nxr = nxA.as<uint32_t>(), *nxr2 = nxB.as<uint32_t>();   // free again
-    k_break<<<gs, 256, 0, s>>>(cm, split_id.as<uint32_t>(), seg_next.as<uint32_t>(),
-                               seg_len.as<uint32_t>(), ns, nxr, dA.as<uint32_t>());
-    CSL_LAUNCH_CHECK("ms break cycles");
-    CSL_CUDA(cudaMemsetAsync(done, 0, 4 * 64, s));
-    uint32_t *dist = dA.as<uint32_t>(), *dist2 = dB.as<uint32_t>();
-    for (int it = 0; it < max_it; ++it) {
-        k_jump_rank<<<gs, 256, 0, s>>>(dist, nxr, dist2, nxr2, ns, done, it);
-        CSL_LAUNCH_CHECK("ms list ranking");
-        std::swap(dist, dist2);
-        std::swap(nxr, nxr2);
-    }
-    read_to_host(done_h, done, 4 * max_it, s);
-    {
+    // short splitter cycles by walking them; long ones by pointer jumping
+    DevBuf cm((size_t)ns * 4, s), long_list((size_t)ns * 4, s), long_pos((size_t)ns * 4, s);
+    DevBuf rank_start((size_t)ns * 4, s), loop_len((size_t)ns * 4, s);
+    uint32_t* n_long = done + 64;
+    k_short_cycles<<<gs, 256, 0, s>>>(split_id.as<uint32_t>(), seg_next.as<uint32_t>(), ns,
+                                      cm.as<uint32_t>(), long_list.as<uint32_t>(),
+                                      long_pos.as<uint32_t>(), n_long);
+    CSL_LAUNCH_CHECK("ms short cycles");
+    k_short_ranks<<<gs, 256, 0, s>>>(cm.as<uint32_t>(), split_id.as<uint32_t>(),
+                                     seg_next.as<uint32_t>(), seg_len.as<uint32_t>(), ns,
+                                     rank_start.as<uint32_t>(), loop_len.as<uint32_t>());
+    CSL_LAUNCH_CHECK("ms short ranks");
+    uint32_t nl_u = 0;
+    read_to_host(&nl_u, n_long, 4, s);
+    const int64_t nl = nl_u;
+    if (nl > 0) {
+        // cycle minimum by doubling; a step that changes nothing ends it
+        int max_it = 1;
+        while (((int64_t)1 << max_it) < nl + 1) ++max_it;
+        max_it += 1;
+        if (max_it > 60) fail(CSL_ERR_CAPACITY, "marching squares: too many splitters");
+        DevBuf cmA((size_t)nl * 4, s), cmB((size_t)nl * 4, s), nxA((size_t)nl * 4, s),
+            nxB((size_t)nl * 4, s);
+        const unsigned gl = grid_for(nl, 256);
+        k_long_setup<<<gl, 256, 0, s>>>(long_list.as<uint32_t>(), long_pos.as<uint32_t>(),
+                                        split_id.as<uint32_t>(), seg_next.as<uint32_t>(), nl,
+                                        cmA.as<uint32_t>(), nxA.as<uint32_t>());
+        CSL_LAUNCH_CHECK("ms long setup");
+        uint32_t *a_cm = cmA.as<uint32_t>(), *a_nx = nxA.as<uint32_t>();
+        uint32_t *b_cm = cmB.as<uint32_t>(), *b_nx = nxB.as<uint32_t>();
+        for (int it = 0; it < max_it; ++it) {
+            k_jump_min<<<gl, 256, 0, s>>>(a_cm, a_nx, b_cm, b_nx, nl, done, it);
+            CSL_LAUNCH_CHECK("ms cycle minimum");
+            std::swap(a_cm, b_cm);
+            std::swap(a_nx, b_nx);
+        }
+        // steps after the first one that changed nothing return at once: the
+        // result is in the buffer of the last step that ran (B after an odd count)
+        uint32_t done_h[64];
+        read_to_host(done_h, done, 4 * max_it, s);
         int ran = 1;
         while (ran < max_it && done_h[ran - 1]) ++ran;
+        uint32_t* lcm = (ran & 1) ? cmB.as<uint32_t>() : cmA.as<uint32_t>();
+        DevBuf dA((size_t)nl * 4, s), dB((size_t)nl * 4, s);
+        uint32_t *nxr = nxA.as<uint32_t>(), *nxr2 = nxB.as<uint32_t>();   // free again
+        k_long_break<<<gl, 256, 0, s>>>(lcm, long_list.as<uint32_t>(), long_pos.as<uint32_t>(),
+                                        split_id.as<uint32_t>(), seg_next.as<uint32_t>(),
+                                        seg_len.as<uint32_t>(), nl, nxr, dA.as<uint32_t>());
+        CSL_LAUNCH_CHECK("ms break cycles");
+        CSL_CUDA(cudaMemsetAsync(done, 0, 4 * 64, s));
+        uint32_t *dist = dA.as<uint32_t>(), *dist2 = dB.as<uint32_t>();
+        for (int it = 0; it < max_it; ++it) {
+            k_jump_rank<<<gl, 256, 0, s>>>(dist, nxr, dist2, nxr2, nl, done, it);
+            CSL_LAUNCH_CHECK("ms list ranking");
+            std::swap(dist, dist2);
+            std::swap(nxr, nxr2);
+        }
+        read_to_host(done_h, done, 4 * max_it, s);
+        ran = 1;
+        while (ran < max_it && done_h[ran - 1]) ++ran;
         dist = (ran & 1) ? dB.as<uint32_t>() : dA.as<uint32_t>();
+        k_long_ranks<<<gl, 256, 0, s>>>(lcm, dist, long_list.as<uint32_t>(),
+                                        long_pos.as<uint32_t>(), spos.as<uint32_t>(), nl,
+                                        cm.as<uint32_t>(), rank_start.as<uint32_t>(),
+                                        loop_len.as<uint32_t>());
+        CSL_LAUNCH_CHECK("ms long ranks");
     }
     DevBuf packed((size_t)ns * 8, s), scan((size_t)ns * 8, s), tot(8, s);
-    k_head_flags<<<gs, 256, 0, s>>>(cm, split_id.as<uint32_t>(), dist, ns, packed.as<int64_t>());
+    k_head_flags<<<gs, 256, 0, s>>>(cm.as<uint32_t>(), split_id.as<uint32_t>(),
+                                    loop_len.as<uint32_t>(), ns, packed.as<int64_t>());
     CSL_LAUNCH_CHECK("ms heads");
     exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), ns, tot.as<int64_t>(), s);
     const int64_t packed_total = read_i64(tot.as<int64_t>(), s);
@@ -490,8 +622,9 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
     out.xy.ensure((size_t)n_cross * 8, s);
     if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
-    k_write_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), cm, spos.as<uint32_t>(),
-                                        split_id.as<uint32_t>(), seg_len.as<uint32_t>(), dist,
+    k_write_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), cm.as<uint32_t>(), spos.as<uint32_t>(),
+                                        split_id.as<uint32_t>(), seg_len.as<uint32_t>(),
+                                        rank_start.as<uint32_t>(),
                                         scan.as<int64_t>(), ns, n_cross,
                                         out.loop_off.as<int64_t>(), out.xy.as<float2>(),
                                         want_eid ? out.eid.as<int32_t>() : nullptr);
