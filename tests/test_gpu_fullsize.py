@@ -36,7 +36,7 @@ def _edges_near(cfg, x0, y0, w, z_lo, z_hi):
     return nodes[used], remap[edges[sel]].astype(np.int32), cfg["radius"][sel], sel
 
 
-def _check_windows(cfg, lat, first, n, n_windows, seed):
+def _check_windows(cfg, lat, first, n, n_windows, seed, win=WIN):
     nx, ny, px = cfg["nx"], cfg["ny"], cfg["pixel"]
     sig = torch.empty((n, ny, nx), dtype=torch.float32, device="cuda")
     z0 = cfg["z0"] + first * cfg["dz"]
@@ -48,14 +48,14 @@ def _check_windows(cfg, lat, first, n, n_windows, seed):
     matched = 0
     for _ in range(n_windows):
         k = int(r.integers(0, n))
-        i0 = int(r.integers(0, nx - WIN))
-        j0 = int(r.integers(0, ny - WIN))
+        i0 = int(r.integers(0, nx - win))
+        j0 = int(r.integers(0, ny - win))
         wx0, wy0 = cfg["x0"] + i0 * px, cfg["y0"] + j0 * px
         z = z0 + k * cfg["dz"]
-        sn, se, sr, _ = _edges_near(cfg, wx0, wy0, WIN * px, z, z)
+        sn, se, sr, _ = _edges_near(cfg, wx0, wy0, win * px, z, z)
         ref = oracle.slice_sigma(sn, se, sr, R=cfg["R"], C=cfg["C"], z0=z, dz=1.0, n_layers=1,
-                                 x0=wx0, y0=wy0, nx=WIN, ny=WIN, pixel=px)[0]
-        got = sig[k, j0:j0 + WIN, i0:i0 + WIN].cpu().numpy()
+                                 x0=wx0, y0=wy0, nx=win, ny=win, pixel=px)[0]
+        got = sig[k, j0:j0 + win, i0:i0 + win].cpu().numpy()
         helpers.assert_field(got, ref, cfg["C"])
         # loops inside the window
         off, eid, xy = oracle.marching_squares(ref, x0=wx0, y0=wy0, pixel=px, C=cfg["C"])
@@ -64,10 +64,10 @@ def _check_windows(cfg, lat, first, n, n_windows, seed):
         for li in range(len(off) - 1):
             le, lxy = eid[off[li]:off[li + 1]], xy[off[li]:off[li + 1]]
             s = le // 2
-            I, J = s % (WIN + 2), s // (WIN + 2)
-            if (I <= 1).any() or (J <= 1).any() or (I >= WIN).any() or (J >= WIN).any():
+            I, J = s % (win + 2), s // (win + 2)
+            if (I <= 1).any() or (J <= 1).any() or (I >= win).any() or (J >= win).any():
                 continue   # touches the window's border cells
-            cells = helpers._edge_cells(le, WIN)
+            cells = helpers._edge_cells(le, win)
             if band[cells[:, 1], cells[:, 0]].any():
                 continue
             glob = 2 * ((J + j0) * W + (I + i0)) + (le % 2)
@@ -92,7 +92,8 @@ def test_freudenthal_430k_windows():
     import paper_2101_05031_gb300 as cs
     cfg = synth.config(2)
     lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
-    matched = _check_windows(cfg, lat, first=64, n=64, n_windows=6, seed=32)
+    # the holes of this dense lattice are ~50 px across: wider windows
+    matched = _check_windows(cfg, lat, first=64, n=64, n_windows=4, seed=32, win=200)
     assert matched > 5
 
 
@@ -115,7 +116,6 @@ def test_volume_fraction_1M_sampled_cells():
     o, h, R = cells["origin"], cells["h"], cfg["R"]
     bx0, by0, bz0 = o[0] + cx0 * h, o[1] + cy0 * h, o[2] + cz0 * h
     sn, se, sr, sel = _edges_near(cfg, bx0, by0, 3 * h, bz0, bz0 + 3 * h)
-    # the window test above is 2D; restrict x/y/z all to the block
     ref = oracle.volume_fraction(sn, se, sr, cells, R=R, ids=ids)
     assert np.max(np.abs(vf[ids] - ref)) <= 3e-4
     g = np.zeros(vf.size, np.float32)
