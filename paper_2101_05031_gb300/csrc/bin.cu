@@ -64,6 +64,19 @@ __device__ __forceinline__ bool bin_rect(const float4 e, float zlo, float zhi, f
     return true;
 }
 
+// First / last layer plane of each slab, from double (non-fused, as the
+// binning reference computes them) rounded to float.
+__global__ void k_init_slabs(SlabInfo* slabs, int n_slabs, double z0, double dz, int first_layer,
+                             int S, int last_layer) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= n_slabs) return;
+    const int l0 = first_layer + sl * S;
+    const int l1 = min(l0 + S - 1, last_layer);
+    slabs[sl].zf = (float)__dadd_rn(z0, __dmul_rn((double)l0, dz));
+    slabs[sl].zl = (float)__dadd_rn(z0, __dmul_rn((double)l1, dz));
+    slabs[sl].kb = slabs[sl].ke = slabs[sl].cand_off = 0;
+}
+
 // Window of records for each slab: zlo in [zf - mz - max_dz - slack, zl + mz + slack].
 __global__ void k_slab_windows(const float* __restrict__ zlo, int64_t n, SlabInfo* slabs,
                                int n_slabs, float mz, float max_dz) {
@@ -100,7 +113,8 @@ __global__ void k_cand_offsets(SlabInfo* slabs, int n_slabs, int64_t* total) {
 
 __global__ void k_bin_count(const float4* __restrict__ bxy, const float* __restrict__ zlo,
                             const float* __restrict__ zhi, const SlabInfo* __restrict__ slabs,
-                            BinConst c, uint32_t* __restrict__ count) {
+                            BinConst c, uint32_t* __restrict__ count, int64_t cap_cand,
+                            uint32_t* flag) {
     const SlabInfo sl = slabs[blockIdx.y];
     int64_t n = sl.ke - sl.kb;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -110,14 +124,27 @@ __global__ void k_bin_count(const float4* __restrict__ bxy, const float* __restr
         uint32_t cnt = 0;
         if (bin_rect(bxy[k], zlo[k], zhi[k], sl.zf, sl.zl, c, tx0, tx1, ty0, ty1))
             cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-        count[sl.cand_off + i] = cnt;
+        if (sl.cand_off + i < cap_cand) count[sl.cand_off + i] = cnt;
+        else if (flag) atomicOr(flag, 1u);
     }
+}
+
+// Replay check: the device's totals must equal the planned ones.
+__global__ void k_check_i64(const int64_t* __restrict__ v, int64_t expect, uint32_t* flag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *v != expect) atomicOr(flag, 1u);
+}
+
+__global__ void k_check_windows(const SlabInfo* __restrict__ slabs, int n_slabs,
+                                int64_t max_window, uint32_t* flag) {
+    const int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl < n_slabs && slabs[sl].ke - slabs[sl].kb > max_window) atomicOr(flag, 1u);
 }
 
 __global__ void k_bin_emit(const float4* __restrict__ bxy, const float* __restrict__ zlo,
                            const float* __restrict__ zhi, const SlabInfo* __restrict__ slabs,
-                           BinConst c, const int64_t* __restrict__ pair_off,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                           BinConst c, const int64_t* __restrict__ pair_off, int64_t cap_cand,
+                           int64_t cap_pairs, uint32_t* __restrict__ keys,
+                           uint32_t* __restrict__ vals) {
     const int s = blockIdx.y;
     const SlabInfo sl = slabs[s];
     int64_t n = sl.ke - sl.kb;
@@ -126,7 +153,9 @@ __global__ void k_bin_emit(const float4* __restrict__ bxy, const float* __restri
         int64_t k = sl.kb + i;
         int tx0, tx1, ty0, ty1;
         if (!bin_rect(bxy[k], zlo[k], zhi[k], sl.zf, sl.zl, c, tx0, tx1, ty0, ty1)) continue;
+        if (sl.cand_off + i >= cap_cand) continue;   // a replay whose sizes changed (flagged)
         int64_t p = pair_off[sl.cand_off + i];
+        if (p + (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1) > cap_pairs) continue;
         uint32_t kbase = (uint32_t)s * (uint32_t)c.n_tiles;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
@@ -155,7 +184,10 @@ int bits_for(int64_t n) {
 
 }  // namespace
 
-void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s) {
+void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s,
+               const Replay* rp) {
+    const bool replay = rp && rp->replay;
+    uint32_t* flag = rp ? rp->flag : nullptr;
     const int n_tiles = g.ntx * g.nty;
     const int64_t n_keys = (int64_t)g.n_slabs * n_tiles;
     if (n_keys > 0xffffffffLL) fail(CSL_ERR_CAPACITY, "too many (slab, tile) bins in one chunk");
@@ -170,28 +202,35 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     c.n_tiles = n_tiles;
 
     std::vector<SlabInfo> hs(g.n_slabs);
-    for (int sl = 0; sl < g.n_slabs; ++sl) {
-        int l0 = g.first_layer + sl * g.S;
-        int l1 = l0 + g.S - 1;
-        int last = g.first_layer + g.n_layers - 1;
-        if (l1 > last) l1 = last;
-        hs[sl].zf = (float)(g.z0 + (double)l0 * g.dz);
-        hs[sl].zl = (float)(g.z0 + (double)l1 * g.dz);
-        hs[sl].kb = hs[sl].ke = hs[sl].cand_off = 0;
-    }
     DevBuf slabs(sizeof(SlabInfo) * g.n_slabs, s);
     DevBuf total(sizeof(int64_t), s);
-    CSL_CUDA(cudaMemcpyAsync(slabs.get(), hs.data(), sizeof(SlabInfo) * g.n_slabs,
-                             cudaMemcpyHostToDevice, s));
+    k_init_slabs<<<(unsigned)ceil_div(g.n_slabs, 128), 128, 0, s>>>(
+        slabs.as<SlabInfo>(), g.n_slabs, g.z0, g.dz, g.first_layer, g.S,
+        g.first_layer + g.n_layers - 1);
+    CSL_LAUNCH_CHECK("slab planes");
     k_slab_windows<<<(unsigned)ceil_div(g.n_slabs, 128), 128, 0, s>>>(
         L->zlo.as<float>(), L->n_edges, slabs.as<SlabInfo>(), g.n_slabs, c.mz, L->max_dz);
     CSL_LAUNCH_CHECK("slab windows");
     k_cand_offsets<<<1, 32, 0, s>>>(slabs.as<SlabInfo>(), g.n_slabs, total.as<int64_t>());
     CSL_LAUNCH_CHECK("candidate offsets");
-    int64_t n_cand = read_i64(total.as<int64_t>(), s);
-    read_to_host(hs.data(), slabs.get(), sizeof(SlabInfo) * g.n_slabs, s);
-    int64_t max_window = 0;
-    for (auto& x : hs) max_window = std::max<int64_t>(max_window, x.ke - x.kb);
+    int64_t n_cand, max_window = 0;
+    if (replay) {
+        n_cand = rp->plan->n_cand;
+        max_window = rp->plan->max_window;
+        k_check_i64<<<1, 32, 0, s>>>(total.as<int64_t>(), n_cand, flag);
+        CSL_LAUNCH_CHECK("check candidates");
+        k_check_windows<<<(unsigned)ceil_div(g.n_slabs, 128), 128, 0, s>>>(
+            slabs.as<SlabInfo>(), g.n_slabs, max_window, flag);
+        CSL_LAUNCH_CHECK("check windows");
+    } else {
+        n_cand = read_i64(total.as<int64_t>(), s);
+        read_to_host(hs.data(), slabs.get(), sizeof(SlabInfo) * g.n_slabs, s);
+        for (auto& x : hs) max_window = std::max<int64_t>(max_window, x.ke - x.kb);
+        if (rp) {
+            rp->plan->n_cand = n_cand;
+            rp->plan->max_window = max_window;
+        }
+    }
 
     out.tile_start.ensure((size_t)n_keys * 4, s);
     out.tile_end.ensure((size_t)n_keys * 4, s);
@@ -203,19 +242,27 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     DevBuf count((size_t)n_cand * 4, s), pair_off((size_t)n_cand * 8, s);
     dim3 grid(grid_for(max_window, 256, 4096), (unsigned)g.n_slabs);
     k_bin_count<<<grid, 256, 0, s>>>(L->bxy.as<float4>(), L->zlo.as<float>(), L->zhi.as<float>(),
-                                     slabs.as<SlabInfo>(), c, count.as<uint32_t>());
+                                     slabs.as<SlabInfo>(), c, count.as<uint32_t>(), n_cand, flag);
     CSL_LAUNCH_CHECK("bin count");
     exclusive_scan_u32_to_i64(count.as<uint32_t>(), pair_off.as<int64_t>(), n_cand,
                               total.as<int64_t>(), s);
-    int64_t n_pairs = read_i64(total.as<int64_t>(), s);
+    int64_t n_pairs;
+    if (replay) {
+        n_pairs = rp->plan->n_pairs;
+        k_check_i64<<<1, 32, 0, s>>>(total.as<int64_t>(), n_pairs, flag);
+        CSL_LAUNCH_CHECK("check bin entries");
+    } else {
+        n_pairs = read_i64(total.as<int64_t>(), s);
+        if (rp) rp->plan->n_pairs = n_pairs;
+    }
     if (n_pairs > 0xffffffffLL) fail(CSL_ERR_CAPACITY, "more than 2^32 bin entries in one chunk");
     out.n_pairs = n_pairs;
     if (n_pairs == 0) return;
     out.keys.ensure((size_t)n_pairs * 4, s);
     out.vals.ensure((size_t)n_pairs * 4, s);
     k_bin_emit<<<grid, 256, 0, s>>>(L->bxy.as<float4>(), L->zlo.as<float>(), L->zhi.as<float>(),
-                                    slabs.as<SlabInfo>(), c, pair_off.as<int64_t>(),
-                                    out.keys.as<uint32_t>(), out.vals.as<uint32_t>());
+                                    slabs.as<SlabInfo>(), c, pair_off.as<int64_t>(), n_cand,
+                                    n_pairs, out.keys.as<uint32_t>(), out.vals.as<uint32_t>());
     CSL_LAUNCH_CHECK("bin emit");
     count.release();
     pair_off.release();

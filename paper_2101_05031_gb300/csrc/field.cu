@@ -26,8 +26,6 @@
 // per-pixel evaluation is branch-free.
 #include <math.h>
 
-#include <vector>
-
 #include "field_tile.cuh"
 #include "slice.cuh"
 
@@ -50,17 +48,20 @@ struct FieldConst {
     int64_t mask_wpl;   // mask words per layer
 };
 
+// One (tile, slab) of the field: called by the grid kernel (one CTA per
+// (tile, slab)) and by the persistent batch kernel (one item at a time).
 template <int S, bool COUNT>
-__global__ void __launch_bounds__(kFieldThreads, 4)
-k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
-        const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
-        float* __restrict__ sigma, uint32_t* __restrict__ mask,
-        unsigned long long* __restrict__ n_pairs) {
+__device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
+                                           const uint32_t* __restrict__ vals,
+                                           const uint32_t* __restrict__ tstart,
+                                           const uint32_t* __restrict__ tend, const FieldConst& c,
+                                           float* __restrict__ sigma, uint32_t* __restrict__ mask,
+                                           unsigned long long* __restrict__ n_pairs, int tile,
+                                           int slab) {
     __shared__ float4 s_a[kFieldThreads];   // ax, ay, az (tile-local), ux
     __shared__ float4 s_b[kFieldThreads];   // uy, uz, len, w / R^4
     __shared__ uint64_t s_mask[kFieldThreads];   // byte l: warps reached at layer l
 
-    const int tile = blockIdx.x, slab = blockIdx.y;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
     const uint32_t key = (uint32_t)slab * (uint32_t)c.n_tiles + (uint32_t)tile;
     const uint32_t beg = tstart[key], end = tend[key];
@@ -182,6 +183,101 @@ k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
     }
 }
 
+template <int S, bool COUNT>
+__global__ void __launch_bounds__(kFieldThreads, 4)
+k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
+        const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
+        float* __restrict__ sigma, uint32_t* __restrict__ mask,
+        unsigned long long* __restrict__ n_pairs) {
+    field_tile<S, COUNT>(rec, vals, tstart, tend, c, sigma, mask, n_pairs, blockIdx.x,
+                         blockIdx.y);
+}
+
+// One job of a batch, as the persistent kernel reads it.
+struct FieldJob {
+    FieldConst c;
+    const csl_rec* rec;
+    const uint32_t* vals;
+    const uint32_t* tstart;
+    const uint32_t* tend;
+    float* sigma;
+    uint32_t* mask;
+};
+static_assert(sizeof(FieldJob) % 4 == 0, "FieldJob is copied as 32-bit words");
+
+// Persistent field kernel over the (job, slab, tile) items of a batch: each
+// CTA takes the next item from a shared counter, in the order `order` gives
+// (longest tile lists first, so the short ones fill the tail).
+template <int S>
+__global__ void __launch_bounds__(kFieldThreads, 4)
+k_field_batch(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items,
+              const uint32_t* __restrict__ order, uint32_t n_items, uint32_t* counter) {
+    __shared__ uint32_t s_item;
+    __shared__ FieldJob s_job;
+    uint32_t cur_job = 0xffffffffu;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= n_items) break;
+        const uint2 item = items[order[it]];
+        if (item.x != cur_job) {   // consecutive items often belong to the same job
+            cur_job = item.x;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs + item.x);
+            for (int i = threadIdx.x; i < (int)(sizeof(FieldJob) / 4); i += kFieldThreads)
+                reinterpret_cast<uint32_t*>(&s_job)[i] = src[i];
+            __syncthreads();
+        }
+        const uint32_t n_tiles = (uint32_t)s_job.c.n_tiles;
+        field_tile<S, false>(s_job.rec, s_job.vals, s_job.tstart, s_job.tend, s_job.c,
+                             s_job.sigma, s_job.mask, nullptr, (int)(item.y % n_tiles),
+                             (int)(item.y / n_tiles));
+        __syncthreads();   // shared memory is reused by the next item
+    }
+}
+
+// items[i] = (job, slab * n_tiles + tile) for the jobs' item ranges off[j]..off[j+1].
+__global__ void k_make_items(const int64_t* __restrict__ off, int n_jobs, uint2* __restrict__ items) {
+    const int64_t n = off[n_jobs];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_jobs - 1;   // the last job with off[j] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        items[i] = make_uint2((uint32_t)lo, (uint32_t)(i - off[lo]));
+    }
+}
+
+// Sort keys for the item queue: longest tile list first (16-bit key).
+__global__ void k_item_keys(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items,
+                            uint32_t n, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 it = items[i];
+        const FieldJob& J = jobs[it.x];
+        const uint32_t len = J.tend[it.y] - J.tstart[it.y];
+        keys[i] = 0xffffu - min(len, 0xffffu);
+        vals[i] = i;
+    }
+}
+
+// Corner of each tile column / row and first plane of each slab, computed in
+// double (non-fused) and split into a (hi, lo) float pair.
+__global__ void k_origins(float2* __restrict__ org, int ntx, int nty, int n_slabs, double x0,
+                          double y0, double z0, double px, double dz, int first_layer, int S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v;
+    if (i < ntx) v = __dadd_rn(x0, __dmul_rn((double)(i * kTile), px));
+    else if (i < ntx + nty) v = __dadd_rn(y0, __dmul_rn((double)((i - ntx) * kTile), px));
+    else if (i < ntx + nty + n_slabs)
+        v = __dadd_rn(z0, __dmul_rn((double)(first_layer + (i - ntx - nty) * S), dz));
+    else return;
+    const float hi = (float)v;
+    org[i] = make_float2(hi, (float)__dsub_rn(v, (double)hi));
+}
+
 }  // namespace
 
 void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
@@ -189,18 +285,11 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     FieldConst c;
     c.C = C;
     // tile and slab origins in double, each split into a (hi, lo) float pair
-    std::vector<float2> org((size_t)g.ntx + g.nty + g.n_slabs);
-    auto split = [](double v) {
-        const float hi = (float)v;
-        return make_float2(hi, (float)(v - (double)hi));
-    };
-    for (int i = 0; i < g.ntx; ++i) org[i] = split(g.x0 + (double)(i * kTile) * g.px);
-    for (int j = 0; j < g.nty; ++j) org[g.ntx + j] = split(g.y0 + (double)(j * kTile) * g.px);
-    for (int k = 0; k < g.n_slabs; ++k)
-        org[g.ntx + g.nty + k] = split(g.z0 + (double)(g.first_layer + k * g.S) * g.dz);
-    DevBuf org_d(org.size() * sizeof(float2), s);
-    CSL_CUDA(cudaMemcpyAsync(org_d.get(), org.data(), org.size() * sizeof(float2),
-                             cudaMemcpyHostToDevice, s));
+    DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
+    k_origins<<<(unsigned)ceil_div(g.ntx + g.nty + g.n_slabs, 128), 128, 0, s>>>(
+        org_d.as<float2>(), g.ntx, g.nty, g.n_slabs, g.x0, g.y0, g.z0, g.px, g.dz, g.first_layer,
+        g.S);
+    CSL_LAUNCH_CHECK("origins");
     c.org_x = org_d.as<float2>();
     c.org_y = c.org_x + g.ntx;
     c.org_z = c.org_y + g.nty;

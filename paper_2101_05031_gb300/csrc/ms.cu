@@ -108,7 +108,8 @@ __device__ __forceinline__ float value_at(const float* __restrict__ sg, const Ms
 
 // grid: x over (row J <= ny, mask word k), y = layer
 __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
-                       MsConst c, Dense D, Xing* __restrict__ rec) {
+                       MsConst c, Dense D, Xing* __restrict__ rec, uint32_t n_cap,
+                       uint32_t* flag) {
     const int layer = blockIdx.y;
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (uint32_t)(c.ny + 1) * (uint32_t)c.mwr) return;
@@ -158,6 +159,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         const int64_t eb = 2 * ((int64_t)J * c.W + I);
         if ((hb >> b) & 1u) {   // vertex on the bottom edge (I, J) -> (I+1, J)
             const uint32_t id = id_row(b, 0);
+            if (id >= n_cap) { atomicOr(flag, 1u); continue; }
             const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
             const float t = (sa - c.C) / (sa - sbv);
             const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
@@ -167,6 +169,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         }
         if ((vb >> b) & 1u) {   // vertex on the left edge (I, J) -> (I, J+1)
             const uint32_t id = id_row(b, 1);
+            if (id >= n_cap) { atomicOr(flag, 1u); continue; }
             const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
             const float t = (sa - c.C) / (sa - sbv);
             const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
@@ -184,13 +187,20 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
                            : (sd == 1 ? id_row(b + 1, 1) : (sd == 2 ? id_up(b) : id_row(b, 1)));
         };
         if (__popc(enter) == 1) {
-            rec[side(__ffs(enter) - 1)].succ = side(__ffs(leave) - 1);
+            const uint32_t a = side(__ffs(enter) - 1);
+            if (a < n_cap) rec[a].succ = side(__ffs(leave) - 1);
+            else atomicOr(flag, 1u);
         } else if (enter) {
             const float v2 = value_at(sg, c, I + 1, J + 1);
             const bool joined = 0.25f * (v0 + v1 + v2 + v3) >= c.C;
             const int k0 = __ffs(enter) - 1, k1 = 31 - __clz(enter);
-            rec[side(k0)].succ = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
-            rec[side(k1)].succ = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
+            const uint32_t a0 = side(k0), a1 = side(k1);
+            if (a0 < n_cap && a1 < n_cap) {
+                rec[a0].succ = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
+                rec[a1].succ = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
+            } else {
+                atomicOr(flag, 1u);
+            }
         }
     }
 }
@@ -225,10 +235,14 @@ __global__ void k_split_flags(const Xing* __restrict__ rec, const uint32_t* __re
 
 // spos: exclusive scan of flag. split_id[spos[i]] = i for splitters.
 __global__ void k_split_list(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ spos,
-                             int64_t n, uint32_t* __restrict__ split_id) {
+                             int64_t n, int64_t ns_cap, uint32_t* __restrict__ split_id,
+                             uint32_t* status) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (flag[i]) split_id[spos[i]] = (uint32_t)i;
+        if (flag[i]) {
+            if ((int64_t)spos[i] < ns_cap) split_id[spos[i]] = (uint32_t)i;
+            else atomicOr(status, ST_CAPACITY);
+        }
 }
 
 // Each splitter walks its segment up to the next splitter.
@@ -238,7 +252,14 @@ __global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restr
                            uint32_t* __restrict__ seg_len, uint32_t* status) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
          t += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t j = rec[split_id[t]].succ;
+        const uint32_t s0 = split_id[t];
+        if ((int64_t)s0 >= n) {   // a replay whose sizes changed (flagged): no walk
+            atomicOr(status, ST_CAPACITY);
+            seg_next[t] = (uint32_t)t;
+            seg_len[t] = 1;
+            continue;
+        }
+        uint32_t j = rec[s0].succ;
         int64_t len = 1;
         while ((int64_t)j < n && !flag[j] && len <= n) {
             j = rec[j].succ;
@@ -250,22 +271,37 @@ __global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restr
             seg_len[t] = 1;
             continue;
         }
-        seg_next[t] = spos[j];
+        const uint32_t nxt = spos[j];
+        if ((int64_t)nxt >= ns) {   // more splitters than planned (flagged)
+            atomicOr(status, ST_CAPACITY);
+            seg_next[t] = (uint32_t)t;
+            seg_len[t] = 1;
+            continue;
+        }
+        seg_next[t] = nxt;
         seg_len[t] = (uint32_t)len;
     }
 }
 
 // One doubling step of the cycle minimum over the splitter graph:
-// (cm, nx) -> (min(cm, cm[nx]), nx[nx]). Runs only while the previous step
-// changed something (done[it - 1] != 0); sets done[it] when it changes cm.
+// (cm, nx) -> (min(cm, cm[nx]), nx[nx]); sets done[it] when it changes cm.
+// Once a step changed nothing, the later steps only copy cm forward, so the
+// result is always in the buffer of the last step.
 __global__ void k_jump_min(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ nx,
                            uint32_t* __restrict__ cm2, uint32_t* __restrict__ nx2, int64_t ns,
                            uint32_t* done, int it) {
-    if (it > 0 && done[it - 1] == 0) return;
+    if (it > 0 && done[it - 1] == 0) {   // converged: carry the result forward
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+             t += (int64_t)gridDim.x * blockDim.x)
+            cm2[t] = cm[t];
+        return;
+    }
     bool changed = false;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = cm[t], nt = nx[t];
+        const uint32_t a = cm[t];
+        uint32_t nt = nx[t];
+        if ((int64_t)nt >= ns) nt = (uint32_t)t;   // only in a flagged replay
         const uint32_t b = cm[nt];
         const uint32_t m = b < a ? b : a;
         changed |= m != a;
@@ -279,19 +315,24 @@ __global__ void k_jump_min(const uint32_t* __restrict__ cm, const uint32_t* __re
 __global__ void k_jump_rank(const uint32_t* __restrict__ dist, const uint32_t* __restrict__ nx,
                             uint32_t* __restrict__ dist2, uint32_t* __restrict__ nx2, int64_t ns,
                             uint32_t* done, int it) {
-    if (it > 0 && done[it - 1] == 0) return;
+    if (it > 0 && done[it - 1] == 0) {   // every list ended: carry the result forward
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+             t += (int64_t)gridDim.x * blockDim.x)
+            dist2[t] = dist[t];
+        return;
+    }
     bool live = false;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
          t += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t nt = nx[t];
-        if (nt == 0xffffffffu) {
+        if ((int64_t)nt >= ns) {   // list end (or, in a flagged replay, a bad link)
             dist2[t] = dist[t];
             nx2[t] = nt;
         } else {
             dist2[t] = dist[t] + dist[nt];
             const uint32_t nn = nx[nt];
             nx2[t] = nn;
-            live |= nn != 0xffffffffu;
+            live |= (int64_t)nn < ns;
         }
     }
     if (__syncthreads_or(live) && threadIdx.x == 0) done[it] = 1u;
@@ -367,8 +408,9 @@ __global__ void k_long_setup(const uint32_t* __restrict__ long_list,
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nl;
          u += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = long_list[u];
+        const uint32_t nt = seg_next[t];   // < ns by construction of k_segments
         lcm[u] = split_id[t];
-        lnx[u] = long_pos[seg_next[t]];
+        lnx[u] = long_pos[nt];
     }
 }
 
@@ -384,7 +426,7 @@ __global__ void k_long_break(const uint32_t* __restrict__ lcm, const uint32_t* _
         const uint32_t t = long_list[u];
         const uint32_t nt = seg_next[t];
         const uint32_t nu = long_pos[nt];
-        nx[u] = lcm[nu] == split_id[nt] ? kNil : nu;
+        nx[u] = ((int64_t)nu >= nl || lcm[nu] == split_id[nt]) ? kNil : nu;
         dist[u] = seg_len[t];
     }
 }
@@ -393,13 +435,15 @@ __global__ void k_long_break(const uint32_t* __restrict__ lcm, const uint32_t* _
 __global__ void k_long_ranks(const uint32_t* __restrict__ lcm, const uint32_t* __restrict__ dist,
                              const uint32_t* __restrict__ long_list,
                              const uint32_t* __restrict__ long_pos,
-                             const uint32_t* __restrict__ spos, int64_t nl,
+                             const uint32_t* __restrict__ spos, int64_t nl, int64_t ns,
                              uint32_t* __restrict__ cm, uint32_t* __restrict__ rank_start,
                              uint32_t* __restrict__ loop_len) {
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nl;
          u += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = long_list[u];
-        const uint32_t hu = long_pos[spos[lcm[u]]];
+        const uint32_t sp = spos[lcm[u]];
+        uint32_t hu = (int64_t)sp < ns ? long_pos[sp] : kNil;
+        if ((int64_t)hu >= nl) hu = (uint32_t)u;   // only in a flagged replay
         cm[t] = lcm[u];
         rank_start[t] = dist[hu] - dist[u];
         if (hu == (uint32_t)u) loop_len[t] = dist[u];
@@ -415,6 +459,17 @@ __global__ void k_head_flags(const uint32_t* __restrict__ cm, const uint32_t* __
         packed[t] = cm[t] == split_id[t] ? (((int64_t)1 << 32) | loop_len[t]) : 0;
 }
 
+// Replay checks: a device count against the planned one, and the status word.
+__global__ void k_check_u32(const uint32_t* __restrict__ v, uint32_t expect, uint32_t* flag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *v != expect) atomicOr(flag, 1u);
+}
+__global__ void k_check_packed(const int64_t* __restrict__ total, int64_t n_loops, int64_t n_cross,
+                               const uint32_t* __restrict__ status, uint32_t* flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if ((*total >> 32) != n_loops || (*total & 0xffffffffLL) != n_cross) atomicOr(flag, 1u);
+    if (*status) atomicOr(flag, 2u);
+}
+
 // Each splitter writes its segment at its loop's offset + rank_start.
 __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ cm,
                                  const uint32_t* __restrict__ spos,
@@ -422,13 +477,16 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
                                  const uint32_t* __restrict__ seg_len,
                                  const uint32_t* __restrict__ rank_start,
                                  const int64_t* __restrict__ scan, int64_t ns, int64_t n,
-                                 int64_t* __restrict__ loop_off, float2* __restrict__ oxy,
-                                 int32_t* __restrict__ oeid) {
+                                 int64_t n_loops, int64_t* __restrict__ loop_off,
+                                 float2* __restrict__ oxy, int32_t* __restrict__ oeid) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t h = spos[cm[t]];               // the head splitter of this loop
+        const uint32_t ht = cm[t];
+        if ((int64_t)ht >= n) continue;              // only if the links were inconsistent
+        const uint32_t h = spos[ht];                 // the head splitter of this loop
+        if ((int64_t)h >= ns) continue;
         const int64_t voff = scan[h] & 0xffffffffLL;
-        if (h == (uint32_t)t) loop_off[scan[h] >> 32] = voff;
+        if (h == (uint32_t)t && (scan[h] >> 32) < n_loops) loop_off[scan[h] >> 32] = voff;
         const int64_t base = voff + (int64_t)rank_start[t];
         uint32_t j = split_id[t];
         const int64_t len = seg_len[t];
@@ -458,7 +516,8 @@ __global__ void k_layer_loops(const uint32_t* __restrict__ prefix, int64_t edge_
 }  // namespace
 
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
-                    bool want_eid, ChunkContours& out, cudaStream_t s) {
+                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp) {
+    const bool replay = rp && rp->replay;
     MsConst c;
     c.nx = g.nx;
     c.ny = g.ny;
@@ -477,7 +536,15 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     // 32-bit crossing ids: fewer than 2^27 edge words keeps every count below 2^32
     if (n_words >= ((int64_t)1 << 27)) fail(CSL_ERR_CAPACITY, "marching squares: chunk too large");
 
-    DevBuf ew((size_t)n_words * 4, s), prefix((size_t)n_words * 4, s), total(8, s);
+    // small: [0] status, [1] crossings, [2] splitters, [3..66] done, [67] long count
+    DevBuf small(4 * 80, s);
+    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 4 * 80, s));
+    uint32_t* status = small.as<uint32_t>();
+    uint32_t* done = small.as<uint32_t>() + 3;
+    uint32_t* n_long = small.as<uint32_t>() + 67;
+    uint32_t* flag = rp ? rp->flag : status;   // where replay mismatches go
+
+    DevBuf ew((size_t)n_words * 4, s), prefix((size_t)n_words * 4, s);
     {
         const int64_t n_thr = (int64_t)c.H * c.mwr;
         dim3 grid((unsigned)ceil_div(n_thr, 256), (unsigned)g.n_layers);
@@ -486,11 +553,18 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     }
     k_popc<<<grid_for(n_words, 256), 256, 0, s>>>(ew.as<uint32_t>(), n_words, prefix.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms popc");
-    exclusive_scan_u32(prefix.as<uint32_t>(), prefix.as<uint32_t>(), n_words, total.as<uint32_t>(),
-                       s);
-    uint32_t n_cross_u = 0;
-    read_to_host(&n_cross_u, total.get(), 4, s);
-    const int64_t n_cross = n_cross_u;
+    exclusive_scan_u32(prefix.as<uint32_t>(), prefix.as<uint32_t>(), n_words, status + 1, s);
+    int64_t n_cross;
+    if (replay) {
+        n_cross = rp->plan->n_cross;
+        k_check_u32<<<1, 32, 0, s>>>(status + 1, (uint32_t)n_cross, flag);
+        CSL_LAUNCH_CHECK("check crossings");
+    } else {
+        uint32_t v = 0;
+        read_to_host(&v, status + 1, 4, s);
+        n_cross = v;
+        if (rp) rp->plan->n_cross = n_cross;
+    }
     out.n_verts = n_cross;
     out.layer_loops.ensure((size_t)(g.n_layers + 1) * 8, s);
     if (n_cross == 0) {
@@ -498,6 +572,7 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         out.n_loops = 0;
         out.loop_off.ensure(8, s);
         CSL_CUDA(cudaMemsetAsync(out.loop_off.get(), 0, 8, s));
+        if (rp && !replay) rp->plan->ns = rp->plan->nl = rp->plan->n_loops = 0;
         return;
     }
     DevBuf rec((size_t)n_cross * sizeof(Xing), s);
@@ -506,43 +581,48 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     {
         const int64_t n_thr = (int64_t)(c.ny + 1) * c.mwr;
         dim3 grid((unsigned)ceil_div(n_thr, 256), (unsigned)g.n_layers);
-        k_emit<<<grid, 256, 0, s>>>(sigma, mask, c, D, rec.as<Xing>());
+        k_emit<<<grid, 256, 0, s>>>(sigma, mask, c, D, rec.as<Xing>(), (uint32_t)n_cross, flag);
         CSL_LAUNCH_CHECK("ms emit");
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
-    DevBuf pred((size_t)n_cross * 4, s), flag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
-    DevBuf small(8 + 4 * 128, s);   // [0] status, [1] splitters, [2..65] done, [66] long count
-    uint32_t* status = small.as<uint32_t>();
-    uint32_t* done = small.as<uint32_t>() + 2;
-    CSL_CUDA(cudaMemsetAsync(small.get(), 0, 8 + 4 * 128, s));
+    DevBuf pred((size_t)n_cross * 4, s), sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
     CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms pred");
     k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
-                                     flag.as<uint32_t>());
+                                     sflag.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms splitter flags");
-    exclusive_scan_u32(flag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, small.as<uint32_t>() + 1,
-                       s);
-    uint32_t head2[2];
-    read_to_host(head2, small.get(), 8, s);
-    if (head2[0]) fail(CSL_ERR_CUDA, "marching squares: a crossing has no successor");
-    const int64_t ns = head2[1];
+    exclusive_scan_u32(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, status + 2, s);
+    int64_t ns;
+    if (replay) {
+        ns = rp->plan->ns;
+        k_check_u32<<<1, 32, 0, s>>>(status + 2, (uint32_t)ns, flag);
+        CSL_LAUNCH_CHECK("check splitters");
+    } else {
+        uint32_t head2[3];
+        read_to_host(head2, small.get(), 12, s);
+        if (head2[0]) fail(CSL_ERR_CUDA, "marching squares: a crossing has no successor");
+        ns = head2[2];
+        if (rp) rp->plan->ns = ns;
+    }
     pred.release();
     DevBuf split_id((size_t)ns * 4, s), seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
+    // a replay whose sizes changed leaves entries unwritten: make them valid ids
+    if (replay) CSL_CUDA(cudaMemsetAsync(split_id.get(), 0, (size_t)ns * 4, s));
     const unsigned gs = grid_for(ns, 256);
-    k_split_list<<<gx, 256, 0, s>>>(flag.as<uint32_t>(), spos.as<uint32_t>(), n_cross,
-                                    split_id.as<uint32_t>());
+    k_split_list<<<gx, 256, 0, s>>>(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, ns,
+                                    split_id.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms splitter list");
-    k_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), flag.as<uint32_t>(), spos.as<uint32_t>(),
+    k_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), sflag.as<uint32_t>(), spos.as<uint32_t>(),
                                   split_id.as<uint32_t>(), ns, n_cross, seg_next.as<uint32_t>(),
                                   seg_len.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms segments");
-    flag.release();
+    sflag.release();
     // short splitter cycles by walking them; long ones by pointer jumping
     DevBuf cm((size_t)ns * 4, s), long_list((size_t)ns * 4, s), long_pos((size_t)ns * 4, s);
     DevBuf rank_start((size_t)ns * 4, s), loop_len((size_t)ns * 4, s);
-    uint32_t* n_long = done + 64;
+    if (replay) CSL_CUDA(cudaMemsetAsync(long_list.get(), 0, (size_t)ns * 4, s));
     k_short_cycles<<<gs, 256, 0, s>>>(split_id.as<uint32_t>(), seg_next.as<uint32_t>(), ns,
                                       cm.as<uint32_t>(), long_list.as<uint32_t>(),
                                       long_pos.as<uint32_t>(), n_long);
@@ -551,11 +631,19 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
                                      seg_next.as<uint32_t>(), seg_len.as<uint32_t>(), ns,
                                      rank_start.as<uint32_t>(), loop_len.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms short ranks");
-    uint32_t nl_u = 0;
-    read_to_host(&nl_u, n_long, 4, s);
-    const int64_t nl = nl_u;
+    int64_t nl;
+    if (replay) {
+        nl = rp->plan->nl;
+        k_check_u32<<<1, 32, 0, s>>>(n_long, (uint32_t)nl, flag);
+        CSL_LAUNCH_CHECK("check long cycles");
+    } else {
+        uint32_t v = 0;
+        read_to_host(&v, n_long, 4, s);
+        nl = v;
+        if (rp) rp->plan->nl = nl;
+    }
     if (nl > 0) {
-        // cycle minimum by doubling; a step that changes nothing ends it
+        // cycle minimum by doubling (later steps copy the converged result forward)
         int max_it = 1;
         while (((int64_t)1 << max_it) < nl + 1) ++max_it;
         max_it += 1;
@@ -575,15 +663,11 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
             std::swap(a_cm, b_cm);
             std::swap(a_nx, b_nx);
         }
-        // steps after the first one that changed nothing return at once: the
-        // result is in the buffer of the last step that ran (B after an odd count)
-        uint32_t done_h[64];
-        read_to_host(done_h, done, 4 * max_it, s);
-        int ran = 1;
-        while (ran < max_it && done_h[ran - 1]) ++ran;
-        uint32_t* lcm = (ran & 1) ? cmB.as<uint32_t>() : cmA.as<uint32_t>();
-        DevBuf dA((size_t)nl * 4, s), dB((size_t)nl * 4, s);
-        uint32_t *nxr = nxA.as<uint32_t>(), *nxr2 = nxB.as<uint32_t>();   // free again
+        uint32_t* lcm = a_cm;   // the buffer the last step wrote
+        DevBuf dA((size_t)nl * 4, s), dB((size_t)nl * 4, s), nxr_buf((size_t)nl * 4, s);
+        uint32_t *nxr = nxr_buf.as<uint32_t>(), *nxr2 = (lcm == cmA.as<uint32_t>())
+                                                            ? cmB.as<uint32_t>()
+                                                            : cmA.as<uint32_t>();
         k_long_break<<<gl, 256, 0, s>>>(lcm, long_list.as<uint32_t>(), long_pos.as<uint32_t>(),
                                         split_id.as<uint32_t>(), seg_next.as<uint32_t>(),
                                         seg_len.as<uint32_t>(), nl, nxr, dA.as<uint32_t>());
@@ -596,12 +680,8 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
             std::swap(dist, dist2);
             std::swap(nxr, nxr2);
         }
-        read_to_host(done_h, done, 4 * max_it, s);
-        ran = 1;
-        while (ran < max_it && done_h[ran - 1]) ++ran;
-        dist = (ran & 1) ? dB.as<uint32_t>() : dA.as<uint32_t>();
         k_long_ranks<<<gl, 256, 0, s>>>(lcm, dist, long_list.as<uint32_t>(),
-                                        long_pos.as<uint32_t>(), spos.as<uint32_t>(), nl,
+                                        long_pos.as<uint32_t>(), spos.as<uint32_t>(), nl, ns,
                                         cm.as<uint32_t>(), rank_start.as<uint32_t>(),
                                         loop_len.as<uint32_t>());
         CSL_LAUNCH_CHECK("ms long ranks");
@@ -611,22 +691,29 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
                                     loop_len.as<uint32_t>(), ns, packed.as<int64_t>());
     CSL_LAUNCH_CHECK("ms heads");
     exclusive_scan_i64(packed.as<int64_t>(), scan.as<int64_t>(), ns, tot.as<int64_t>(), s);
-    const int64_t packed_total = read_i64(tot.as<int64_t>(), s);
-    uint32_t st = 0;
-    read_to_host(&st, status, 4, s);
-    if (st) fail(CSL_ERR_CUDA, "marching squares: inconsistent successor links");
-    const int64_t n_loops = packed_total >> 32;
-    if ((packed_total & 0xffffffffLL) != n_cross)
-        fail(CSL_ERR_CUDA, "marching squares: loops do not cover every crossing");
+    int64_t n_loops;
+    if (replay) {
+        n_loops = rp->plan->n_loops;
+        k_check_packed<<<1, 32, 0, s>>>(tot.as<int64_t>(), n_loops, n_cross, status, flag);
+        CSL_LAUNCH_CHECK("check loops");
+    } else {
+        const int64_t packed_total = read_i64(tot.as<int64_t>(), s);
+        uint32_t st = 0;
+        read_to_host(&st, status, 4, s);
+        if (st) fail(CSL_ERR_CUDA, "marching squares: inconsistent successor links");
+        n_loops = packed_total >> 32;
+        if ((packed_total & 0xffffffffLL) != n_cross)
+            fail(CSL_ERR_CUDA, "marching squares: loops do not cover every crossing");
+        if (rp) rp->plan->n_loops = n_loops;
+    }
     out.n_loops = n_loops;
     out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
     out.xy.ensure((size_t)n_cross * 8, s);
     if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
     k_write_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), cm.as<uint32_t>(), spos.as<uint32_t>(),
                                         split_id.as<uint32_t>(), seg_len.as<uint32_t>(),
-                                        rank_start.as<uint32_t>(),
-                                        scan.as<int64_t>(), ns, n_cross,
-                                        out.loop_off.as<int64_t>(), out.xy.as<float2>(),
+                                        rank_start.as<uint32_t>(), scan.as<int64_t>(), ns, n_cross,
+                                        n_loops, out.loop_off.as<int64_t>(), out.xy.as<float2>(),
                                         want_eid ? out.eid.as<int32_t>() : nullptr);
     CSL_LAUNCH_CHECK("ms write");
     k_layer_loops<<<(unsigned)ceil_div(g.n_layers + 1, 128), 128, 0, s>>>(

@@ -28,8 +28,23 @@ struct SlabBins {
     int64_t n_pairs = 0;
 };
 
+// Sizes that a chunk's pipeline discovers on the host (each needs a read
+// back). A planning run records them; a replay run uses them instead, reads
+// nothing back (so it can be captured in a CUDA graph), bounds every write by
+// them and sets *flag when the device finds other sizes (the inputs changed).
+struct ChunkPlan {
+    int64_t n_cand = 0, max_window = 0, n_pairs = 0;     // binner
+    int64_t n_cross = 0, ns = 0, nl = 0, n_loops = 0;    // contours
+};
+struct Replay {
+    bool replay = false;         // false: record into *plan; true: use *plan
+    ChunkPlan* plan = nullptr;
+    uint32_t* flag = nullptr;    // device word, OR-ed with 1 on a size mismatch
+};
+
 // Bins the lattice's records into (slab, tile) lists for one chunk.
-void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s);
+void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStream_t s,
+               const Replay* rp = nullptr);
 
 // Inside mask of a chunk (the binary image of Sec. 4): bit I % 32 of word
 // [layer][J][I / 32] is set when padded sample (I, J), i.e. pixel (I-1, J-1),
@@ -54,8 +69,10 @@ struct ChunkContours {
     DevBuf xy;            // float2 [n_verts]
     DevBuf eid;           // int32 [n_verts]
 };
+// Contours of a chunk. In a replay (rp->replay), out's arrays must already
+// hold rp->plan's sizes; they are filled in place.
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
-                    bool want_eid, ChunkContours& out, cudaStream_t s);
+                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp = nullptr);
 
 // Volume fraction per density cell and its adjoint (vf.cu).
 void vf_forward(const csl_lattice* L, const csl_cells& cells, float* vf, cudaStream_t s);
