@@ -112,6 +112,21 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank's layers count only once all are done)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, t_max_ms):
+    """Units processed by all ranks per second of the slowest rank."""
+    return units_per_rank_step * steps * world / (t_max_ms / 1e3)
+
+
 def slice_kwargs(cfg, rank, world):
     z0 = cfg["z0"] + cfg["dz"] * rank / world
     return dict(z0=z0, dz=cfg["dz"], n_layers=cfg["n_layers"], x0=cfg["x0"], y0=cfg["y0"],
@@ -221,6 +236,50 @@ def run_10m(steps, warmup):
     return {"workload": cfg["name"], "struts": int(cfg["edges"].shape[0]),
             "pixel_evals_per_s": cfg["nx"] * cfg["ny"] * cfg["n_layers"] / (ms / 1e3),
             "layers_per_s": cfg["n_layers"] / (ms / 1e3), "ms_per_step": ms}
+
+
+def run_batch(steps, warmup):
+    """64 seeded Freudenthal lattices of uneven size (1k-500k struts, boxes of
+    10-80 mm), 100 layers each at 0.05 mm pixels: the jobs as one autotuned,
+    graph-captured batch against slicing them one after another with
+    csl_slice_layers (contours left on the device in both)."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    import synth
+    cfg = synth.config(4)
+    jobs = []
+    for jb in cfg["jobs"]:
+        lat = cs.Lattice(jb["nodes"], jb["edges"], jb["radius"], R=jb["R"], C=jb["C"])
+        jobs.append((lat, dict(z0=jb["z0"], dz=jb["dz"], n_layers=jb["n_layers"], x0=jb["x0"],
+                               y0=jb["y0"], nx=jb["nx"], ny=jb["ny"], pixel=jb["pixel"])))
+    t0 = time.perf_counter()
+    b = cs.Batch(jobs, autotune=True)
+    create_s = time.perf_counter() - t0
+    info = b.info()
+    stream = torch.cuda.current_stream()
+    batch_ms = _event_ms(b.run, steps, warmup, stream)
+
+    def plain():
+        for lat, d in jobs:
+            lat.slice(**d, on_device=True).free()
+
+    plain_ms = _event_ms(plain, steps, warmup, stream)
+    px = int(info.pixel_evals)
+    cands = [{"slab": int(info.cand_slab[i]), "ctas_per_sm": int(info.cand_ctas[i]),
+              "ms": float(info.cand_ms[i])} for i in range(info.n_candidates)]
+    out = {"workload": cfg["name"], "jobs": len(jobs),
+           "struts": int(sum(jb["edges"].shape[0] for jb in cfg["jobs"])),
+           "pixel_evals_per_step": px,
+           "batched": {"ms_per_step": batch_ms, "pixel_evals_per_s": px / (batch_ms / 1e3),
+                       "slab": int(info.slab), "ctas_per_sm": int(info.ctas_per_sm),
+                       "graph_nodes": int(info.graph_nodes), "queue_items": int(info.n_items),
+                       "create_s": create_s, "plan_ms": info.plan_ms, "tune_ms": info.tune_ms,
+                       "candidates": cands},
+           "per_job": {"ms_per_step": plain_ms, "pixel_evals_per_s": px / (plain_ms / 1e3)},
+           "batched_over_per_job": plain_ms / batch_ms}
+    b.close()
+    return out
 
 
 # --------------------------------------------------------------------------- main
@@ -334,14 +393,10 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist, "cuda")
     px_per_step = cfg["nx"] * cfg["ny"] * cfg["n_layers"]
-    value = px_per_step * args.steps * world / (t_max / 1e3)
-    layers_per_s = cfg["n_layers"] * args.steps * world / (t_max / 1e3)
+    value = whole_job_rate(px_per_step, args.steps, world, t_max)
+    layers_per_s = whole_job_rate(cfg["n_layers"], args.steps, world, t_max)
     clocks = clk.summary()
 
     # roofline of the field kernel: FP32 ALU
@@ -400,12 +455,9 @@ def main():
         a1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = a0.elapsed_time(a1) / args.e2e_steps
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        line["e2e"] = {"value": px_per_step * world / (e2e_ms / 1e3), "unit": "pixel-evals/s",
+        e2e_ms = max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps, dist, "cuda")
+        line["e2e"] = {"value": whole_job_rate(px_per_step, 1, world, e2e_ms),
+                       "unit": "pixel-evals/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": e2e_ms}
 
@@ -413,6 +465,7 @@ def main():
         del lat
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)
+        line["batched_64"] = run_batch(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:

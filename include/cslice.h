@@ -234,6 +234,93 @@ csl_status csl_volume_fraction_backward(csl_lattice* lat, const csl_cells* cells
                                         float* grad_nodes, void* stream);
 
 /*
+ * Batched slicing: many (lattice, slicing request) jobs -- lattices of uneven
+ * size, or slab ranges of one lattice -- run as one CUDA graph whose field
+ * stage is a single persistent launch. The paper slices one part at a time
+ * (Sec. 4); batching is this library's own addition, so that many small
+ * parts fill the GPU.
+ *
+ * csl_batch_create plans the batch: it runs every job once in the ordinary
+ * way (reading the sizes the pipeline discovers: binner entries, crossings,
+ * splitters, loops), keeps every buffer at those sizes, and captures a replay
+ * of all jobs that reads nothing back into a CUDA graph: the binner and the
+ * contour stages of the jobs run on parallel branches, and the field of all
+ * jobs is one persistent kernel whose CTAs take (job, slab, tile) items from
+ * a queue sorted longest tile list first. With autotune set, it times the
+ * graph for every slab depth S in {2, 4, 8} and 2, 3 or 4 resident CTAs per
+ * SM and keeps the fastest; the choice is cached per process for the same
+ * job sizes. The tile is fixed at 16 x 16 pixels and the staging chunk at 256
+ * records (one per thread of the 8-warp CTA).
+ *
+ * csl_batch_run launches the graph on `stream` and waits for it. The jobs'
+ * lattices are read at run time, so radii and node positions may change
+ * between runs (csl_lattice_update), but every count must stay what the plan
+ * saw: when the device finds another count it writes nothing out of range,
+ * and the run returns CSL_ERR_CAPACITY (create the batch again). The results
+ * of the last run stay in the batch: csl_batch_contours copies one job's
+ * contours out, csl_batch_sigma gives the device address of its field.
+ *
+ * Lattices must outlive the batch, and must not be freed or re-uploaded
+ * while it exists. Results are bit-identical to csl_slice_layers of each job
+ * with the same slab depth (the same kernels sum the same terms in the same
+ * order; the first plane of a slab is the origin of its FP32 z coordinates).
+ */
+typedef struct csl_batch csl_batch;   /* opaque */
+
+typedef struct csl_batch_opts {
+    int32_t autotune;         /* nonzero: time the (slab, CTAs per SM) candidates        */
+    int32_t slab;             /* without autotune: 0 (8, or less for short jobs) or 2, 4, 8 */
+    int32_t ctas_per_sm;      /* without autotune: 0 (4) or 1 .. 4                     */
+    int32_t branches;         /* parallel graph branches for binner and contours: 0 (8) or 1 .. 32 */
+} csl_batch_opts;
+
+#define CSL_BATCH_MAX_CANDIDATES 16
+typedef struct csl_batch_info {
+    int32_t n_jobs;
+    int32_t slab;             /* chosen slab depth                                       */
+    int32_t ctas_per_sm;      /* chosen persistent CTAs per SM                           */
+    int32_t from_cache;       /* 1: the choice came from the per-process cache           */
+    int64_t n_items;          /* (job, slab, tile) items of the field queue              */
+    int64_t n_pairs;          /* binner entries over all jobs                            */
+    int64_t n_crossings;      /* contour vertices over all jobs                          */
+    int64_t n_loops;
+    int64_t graph_nodes;
+    int64_t pixel_evals;      /* sum over jobs of n_layers * nx * ny                     */
+    double plan_ms;           /* host time of the planning runs                          */
+    double tune_ms;           /* host time of the autotuning                             */
+    int32_t n_candidates;     /* autotuned candidates and their best graph time          */
+    int32_t cand_slab[CSL_BATCH_MAX_CANDIDATES];
+    int32_t cand_ctas[CSL_BATCH_MAX_CANDIDATES];
+    float cand_ms[CSL_BATCH_MAX_CANDIDATES];
+} csl_batch_info;
+
+/*
+ * csl_batch_create -- plan (and, with opts->autotune, tune) a batch.
+ *   lats[j], descs[j]  job j: a lattice and a slicing request as for
+ *                      csl_slice_layers; only z0, dz, n_layers (>= 1), nx, ny,
+ *                      x0, y0, pixel and the CSL_SLICE_EDGE_IDS flag are used.
+ *                      A job must fit one streamed chunk (all of its layers'
+ *                      Sigma at once, fewer than 2^27 contour edge words).
+ *   n_jobs             >= 1
+ *   opts               may be NULL (no autotuning, defaults)
+ * Errors: INVALID_ARG (a NULL lattice, a bad request, a job too large for one
+ * chunk), OOM, CUDA. Synchronises the stream.
+ */
+csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* descs, int32_t n_jobs,
+                            const csl_batch_opts* opts, void* stream, csl_batch** out);
+/* Launch the graph on stream and wait; CSL_ERR_CAPACITY if a count changed. */
+csl_status csl_batch_run(csl_batch* b, void* stream);
+/* Contours of job j from the last run (csl_contours_free; dst_on_device as
+ * CSL_SLICE_CONTOURS_ON_DEVICE). */
+csl_status csl_batch_contours(const csl_batch* b, int32_t job, int32_t dst_on_device,
+                              csl_contours** out);
+/* Device address of job j's Sigma, float[n_layers][ny][nx], owned by the batch
+ * and overwritten by every run. */
+csl_status csl_batch_sigma(const csl_batch* b, int32_t job, float** out);
+csl_status csl_batch_get_info(const csl_batch* b, csl_batch_info* out);
+void csl_batch_free(csl_batch* b);
+
+/*
  * csl_field_layers_static -- Sigma on the layers of desc for a lattice given
  * as raw device arrays, WITHOUT allocating any memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device

@@ -24,6 +24,7 @@ SLICE_NO_CONTOURS = 4
 SLICE_TIME_KERNELS = 8
 SLICE_COUNT_PAIRS = 16
 STATIC_MAX_EDGES = 262144
+BATCH_MAX_CANDIDATES = 16
 
 
 class Params(ctypes.Structure):
@@ -62,6 +63,20 @@ class CellsDesc(ctypes.Structure):
                 ("temperature", c_f64)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("autotune", c_i32), ("slab", c_i32), ("ctas_per_sm", c_i32), ("branches", c_i32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_jobs", c_i32), ("slab", c_i32), ("ctas_per_sm", c_i32), ("from_cache", c_i32),
+                ("n_items", c_i64), ("n_pairs", c_i64), ("n_crossings", c_i64), ("n_loops", c_i64),
+                ("graph_nodes", c_i64), ("pixel_evals", c_i64), ("plan_ms", c_f64),
+                ("tune_ms", c_f64), ("n_candidates", c_i32),
+                ("cand_slab", c_i32 * BATCH_MAX_CANDIDATES),
+                ("cand_ctas", c_i32 * BATCH_MAX_CANDIDATES),
+                ("cand_ms", c_f32 * BATCH_MAX_CANDIDATES)]
+
+
 class CslError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -89,6 +104,13 @@ SIGNATURES = [
     ("csl_volume_fraction", c_i32, [c_vp, ctypes.POINTER(CellsDesc), c_vp, c_vp]),
     ("csl_volume_fraction_backward", c_i32, [c_vp, ctypes.POINTER(CellsDesc), c_vp, c_vp, c_vp,
                                              c_vp]),
+    ("csl_batch_create", c_i32, [ctypes.POINTER(c_vp), ctypes.POINTER(SliceDesc), c_i32,
+                                 ctypes.POINTER(BatchOpts), c_vp, ctypes.POINTER(c_vp)]),
+    ("csl_batch_run", c_i32, [c_vp, c_vp]),
+    ("csl_batch_contours", c_i32, [c_vp, c_i32, c_i32, ctypes.POINTER(ctypes.POINTER(Contours))]),
+    ("csl_batch_sigma", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
+    ("csl_batch_get_info", c_i32, [c_vp, ctypes.POINTER(BatchInfo)]),
+    ("csl_batch_free", None, [c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),
 ]

@@ -14,8 +14,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcslice.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# --fmad=false: no implicit multiply-add contraction in device code, so every
+# floating-point result is fixed by its source expression (explicit fmaf where
+# a fused operation is meant) and identical in every kernel that inlines it.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-         "--expt-relaxed-constexpr"]
+         "--fmad=false", "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:

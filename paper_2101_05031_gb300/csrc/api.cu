@@ -13,6 +13,86 @@
 
 using namespace csl;
 
+namespace csl {
+
+void require_arg(bool ok, const char* msg) {
+    if (!ok) fail(CSL_ERR_INVALID_ARG, msg);
+}
+
+// Resolves tile / slab / chunk sizes and the rounding margins of the binner.
+SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
+    require_arg(d.tile == 0 || d.tile == kTile, "tile must be 0 or 16");
+    SlicePlan p;
+    int S = d.slab;
+    if (S == 0) S = d.n_layers >= 8 ? 8 : (d.n_layers >= 4 ? 4 : (d.n_layers >= 2 ? 2 : 1));
+    require_arg(S == 1 || S == 2 || S == 4 || S == 8, "slab must be 0, 1, 2, 4 or 8");
+    p.S = S;
+    p.ntx = (int)ceil_div(d.nx, kTile);
+    p.nty = (int)ceil_div(d.ny, kTile);
+    const int64_t plane = (int64_t)d.nx * d.ny;
+    int chunk = d.chunk_layers;
+    if (chunk == 0) {
+        // about 1 GiB of Sigma per chunk, whole slabs, at least one slab
+        int64_t c = ((int64_t)1 << 30) / (4 * plane);
+        c = std::max<int64_t>(S, c - c % S);
+        c = std::min<int64_t>(c, std::max(d.n_layers, 1));
+        chunk = (int)c;
+    }
+    require_arg(chunk > 0 && (chunk % S == 0 || chunk >= d.n_layers),
+            "chunk_layers must be a positive multiple of the slab depth");
+    // marching squares needs < 2^27 edge words per chunk
+    const int64_t words_per_layer = 2 * mask_words_per_layer(d.nx, d.ny);
+    if ((int64_t)chunk * words_per_layer >= ((int64_t)1 << 27)) {
+        int64_t c = (((int64_t)1 << 27) - 1) / words_per_layer;
+        c -= c % S;
+        require_arg(c >= S, "grid too large for one slab per chunk");
+        chunk = (int)c;
+    }
+    p.chunk = chunk;
+    double scale = 1.0;
+    for (int k = 0; k < 3; ++k)
+        scale = std::max({scale, fabs((double)L->bbox_lo[k]), fabs((double)L->bbox_hi[k])});
+    scale = std::max({scale, fabs(d.x0), fabs(d.y0), fabs(d.x0 + d.nx * d.pixel),
+                      fabs(d.y0 + d.ny * d.pixel), fabs(d.z0),
+                      fabs(d.z0 + (double)std::max(d.n_layers - 1, 0) * d.dz)});
+    p.margin = (float)(L->R + 8e-6 * scale + 1e-6);
+    return p;
+}
+
+ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SlicePlan& p, int first,
+                     int n) {
+    ChunkGeom g;
+    g.nx = d.nx;
+    g.ny = d.ny;
+    g.ntx = p.ntx;
+    g.nty = p.nty;
+    g.x0 = d.x0;
+    g.y0 = d.y0;
+    g.px = d.pixel;
+    g.z0 = d.z0;
+    g.dz = d.dz;
+    g.first_layer = first;
+    g.n_layers = n;
+    g.S = p.S;
+    g.n_slabs = (int)ceil_div(n, p.S);
+    g.R = L->R;
+    g.margin_xy = p.margin;
+    g.margin_z = p.margin;
+    return g;
+}
+
+void validate_desc(const csl_slice_desc* d) {
+    require_arg(d != nullptr, "desc is NULL");
+    require_arg(d->n_layers >= 0, "n_layers < 0");
+    require_arg(d->nx >= 1 && d->ny >= 1 && d->nx <= 32000 && d->ny <= 32000,
+            "nx, ny must be in [1, 32000]");
+    require_arg(isfinite(d->pixel) && d->pixel > 0, "pixel must be > 0");
+    require_arg(isfinite(d->x0) && isfinite(d->y0) && isfinite(d->z0), "non-finite origin");
+    require_arg(d->n_layers <= 1 || (isfinite(d->dz) && d->dz > 0), "dz must be > 0");
+}
+
+}  // namespace csl
+
 namespace {
 
 thread_local csl_stats t_stats = {};
@@ -47,87 +127,10 @@ void copy_in(DevBuf& dst, const void* src, size_t bytes, bool on_device, cudaStr
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
 }
 
-// Resolves tile / slab / chunk sizes and the rounding margins of the binner.
-struct Plan {
-    int S, chunk, ntx, nty;
-    float margin;
-};
-
-Plan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
-    require(d.tile == 0 || d.tile == kTile, "tile must be 0 or 16");
-    Plan p;
-    int S = d.slab;
-    if (S == 0) S = d.n_layers >= 8 ? 8 : (d.n_layers >= 4 ? 4 : (d.n_layers >= 2 ? 2 : 1));
-    require(S == 1 || S == 2 || S == 4 || S == 8, "slab must be 0, 1, 2, 4 or 8");
-    p.S = S;
-    p.ntx = (int)ceil_div(d.nx, kTile);
-    p.nty = (int)ceil_div(d.ny, kTile);
-    const int64_t plane = (int64_t)d.nx * d.ny;
-    int chunk = d.chunk_layers;
-    if (chunk == 0) {
-        // about 1 GiB of Sigma per chunk, whole slabs, at least one slab
-        int64_t c = ((int64_t)1 << 30) / (4 * plane);
-        c = std::max<int64_t>(S, c - c % S);
-        c = std::min<int64_t>(c, std::max(d.n_layers, 1));
-        chunk = (int)c;
-    }
-    require(chunk > 0 && (chunk % S == 0 || chunk >= d.n_layers),
-            "chunk_layers must be a positive multiple of the slab depth");
-    // marching squares needs < 2^27 edge words per chunk
-    const int64_t words_per_layer = 2 * mask_words_per_layer(d.nx, d.ny);
-    if ((int64_t)chunk * words_per_layer >= ((int64_t)1 << 27)) {
-        int64_t c = (((int64_t)1 << 27) - 1) / words_per_layer;
-        c -= c % S;
-        require(c >= S, "grid too large for one slab per chunk");
-        chunk = (int)c;
-    }
-    p.chunk = chunk;
-    double scale = 1.0;
-    for (int k = 0; k < 3; ++k)
-        scale = std::max({scale, fabs((double)L->bbox_lo[k]), fabs((double)L->bbox_hi[k])});
-    scale = std::max({scale, fabs(d.x0), fabs(d.y0), fabs(d.x0 + d.nx * d.pixel),
-                      fabs(d.y0 + d.ny * d.pixel), fabs(d.z0),
-                      fabs(d.z0 + (double)std::max(d.n_layers - 1, 0) * d.dz)});
-    p.margin = (float)(L->R + 8e-6 * scale + 1e-6);
-    return p;
-}
-
-ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const Plan& p, int first,
-                     int n) {
-    ChunkGeom g;
-    g.nx = d.nx;
-    g.ny = d.ny;
-    g.ntx = p.ntx;
-    g.nty = p.nty;
-    g.x0 = d.x0;
-    g.y0 = d.y0;
-    g.px = d.pixel;
-    g.z0 = d.z0;
-    g.dz = d.dz;
-    g.first_layer = first;
-    g.n_layers = n;
-    g.S = p.S;
-    g.n_slabs = (int)ceil_div(n, p.S);
-    g.R = L->R;
-    g.margin_xy = p.margin;
-    g.margin_z = p.margin;
-    return g;
-}
-
 __global__ void k_add_i64(int64_t* a, int64_t n, int64_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         a[i] += v;
-}
-
-void validate_desc(const csl_slice_desc* d) {
-    require(d != nullptr, "desc is NULL");
-    require(d->n_layers >= 0, "n_layers < 0");
-    require(d->nx >= 1 && d->ny >= 1 && d->nx <= 32000 && d->ny <= 32000,
-            "nx, ny must be in [1, 32000]");
-    require(isfinite(d->pixel) && d->pixel > 0, "pixel must be > 0");
-    require(isfinite(d->x0) && isfinite(d->y0) && isfinite(d->z0), "non-finite origin");
-    require(d->n_layers <= 1 || (isfinite(d->dz) && d->dz > 0), "dz must be > 0");
 }
 
 }  // namespace
@@ -266,7 +269,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         const bool on_dev = (d.flags & CSL_SLICE_CONTOURS_ON_DEVICE) != 0;
         const bool want_eid = (d.flags & CSL_SLICE_EDGE_IDS) != 0;
         cudaStream_t s = (cudaStream_t)stream;
-        Plan p = make_plan(L, d);
+        SlicePlan p = make_plan(L, d);
         device_bytes_peak_and_reset();
         launches_and_reset();
         csl_stats st = {};
@@ -469,7 +472,7 @@ csl_status csl_debug_slab_bins(csl_lattice* L, const csl_slice_desc* desc, int32
         cudaStream_t s = (cudaStream_t)stream;
         csl_slice_desc d = *desc;
         if (d.n_layers < first_layer + n_slab_layers) d.n_layers = first_layer + n_slab_layers;
-        Plan p = make_plan(L, d);
+        SlicePlan p = make_plan(L, d);
         ChunkGeom g = chunk_geom(L, d, p, first_layer, n_slab_layers);
         g.S = n_slab_layers;
         g.n_slabs = 1;

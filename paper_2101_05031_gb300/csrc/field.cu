@@ -26,6 +26,8 @@
 // per-pixel evaluation is branch-free.
 #include <math.h>
 
+#include <vector>
+
 #include "field_tile.cuh"
 #include "slice.cuh"
 
@@ -280,19 +282,16 @@ __global__ void k_origins(float2* __restrict__ org, int ntx, int nty, int n_slab
 
 }  // namespace
 
-void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
-                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s) {
+namespace {
+
+// Kernel constants of a chunk; org = the chunk's origin tables (ntx + nty +
+// n_slabs float2, as k_origins writes them).
+FieldConst make_field_const(const ChunkGeom& g, float C, const float2* org) {
     FieldConst c;
     c.C = C;
-    // tile and slab origins in double, each split into a (hi, lo) float pair
-    DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
-    k_origins<<<(unsigned)ceil_div(g.ntx + g.nty + g.n_slabs, 128), 128, 0, s>>>(
-        org_d.as<float2>(), g.ntx, g.nty, g.n_slabs, g.x0, g.y0, g.z0, g.px, g.dz, g.first_layer,
-        g.S);
-    CSL_LAUNCH_CHECK("origins");
-    c.org_x = org_d.as<float2>();
-    c.org_y = c.org_x + g.ntx;
-    c.org_z = c.org_y + g.nty;
+    c.org_x = org;
+    c.org_y = org + g.ntx;
+    c.org_z = org + g.ntx + g.nty;
     c.mwr = (int32_t)mask_words_per_row(g.nx);
     c.mask_wpl = mask_words_per_layer(g.nx, g.ny);
     c.nx = g.nx;
@@ -322,6 +321,23 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     c.tc.cull = c.cull;
     c.tc.cull_line2 = c.cull_line2;
     c.tc.inv_R4 = c.inv_R4;
+    return c;
+}
+
+void launch_origins(const ChunkGeom& g, float2* org, cudaStream_t s) {
+    k_origins<<<(unsigned)ceil_div(g.ntx + g.nty + g.n_slabs, 128), 128, 0, s>>>(
+        org, g.ntx, g.nty, g.n_slabs, g.x0, g.y0, g.z0, g.px, g.dz, g.first_layer, g.S);
+    CSL_LAUNCH_CHECK("origins");
+}
+
+}  // namespace
+
+void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
+                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s) {
+    // tile and slab origins in double, each split into a (hi, lo) float pair
+    DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
+    launch_origins(g, org_d.as<float2>(), s);
+    const FieldConst c = make_field_const(g, C, org_d.as<float2>());
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
     const csl_rec* rec = L->rec.as<csl_rec>();
     const uint32_t* vals = bins.vals.as<uint32_t>();
@@ -345,6 +361,80 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     }
 #undef CSL_FIELD_CASE
     CSL_LAUNCH_CHECK("field");
+}
+
+void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb, cudaStream_t s) {
+    const int n_jobs = (int)jobs.size();
+    if (n_jobs == 0) fail(CSL_ERR_INVALID_ARG, "empty batch");
+    const int S = jobs[0].g.S;
+    size_t n_org = 0;
+    std::vector<int64_t> off(n_jobs + 1, 0);
+    for (int j = 0; j < n_jobs; ++j) {
+        const ChunkGeom& g = jobs[j].g;
+        if (g.S != S) fail(CSL_ERR_INVALID_ARG, "batch: one slab depth for every job");
+        n_org += (size_t)g.ntx + g.nty + g.n_slabs;
+        off[j + 1] = off[j] + (int64_t)g.n_slabs * g.ntx * g.nty;
+    }
+    if (off[n_jobs] >= 0xffffffffLL) fail(CSL_ERR_CAPACITY, "batch: more than 2^32 - 1 tiles");
+    fb.S = S;
+    fb.n_items = off[n_jobs];
+    fb.origins.alloc_persistent(n_org * sizeof(float2));
+    std::vector<FieldJob> hj(n_jobs);
+    size_t o = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const FieldBatchJob& J = jobs[j];
+        float2* org = fb.origins.as<float2>() + o;
+        launch_origins(J.g, org, s);
+        o += (size_t)J.g.ntx + J.g.nty + J.g.n_slabs;
+        hj[j].c = make_field_const(J.g, (float)J.L->C, org);
+        hj[j].rec = J.L->rec.as<csl_rec>();
+        hj[j].vals = J.bins->vals.as<uint32_t>();
+        hj[j].tstart = J.bins->tile_start.as<uint32_t>();
+        hj[j].tend = J.bins->tile_end.as<uint32_t>();
+        hj[j].sigma = J.sigma;
+        hj[j].mask = J.mask;
+    }
+    fb.jobs.alloc_persistent(sizeof(FieldJob) * n_jobs);
+    DevBuf off_d((size_t)(n_jobs + 1) * 8, s);
+    CSL_CUDA(cudaMemcpyAsync(fb.jobs.get(), hj.data(), sizeof(FieldJob) * n_jobs,
+                             cudaMemcpyHostToDevice, s));
+    CSL_CUDA(cudaMemcpyAsync(off_d.get(), off.data(), (size_t)(n_jobs + 1) * 8,
+                             cudaMemcpyHostToDevice, s));
+    const size_t n = (size_t)fb.n_items;
+    fb.items.alloc_persistent(n * sizeof(uint2));
+    fb.keys.alloc_persistent(n * 4);
+    fb.vals.alloc_persistent(n * 4);
+    fb.tmp_keys.alloc_persistent(n * 4);
+    fb.tmp_vals.alloc_persistent(n * 4);
+    fb.counter.alloc_persistent(4);
+    k_make_items<<<grid_for(fb.n_items, 256), 256, 0, s>>>(off_d.as<int64_t>(), n_jobs,
+                                                          fb.items.as<uint2>());
+    CSL_LAUNCH_CHECK("batch items");
+    CSL_CUDA(cudaStreamSynchronize(s));   // the host tables above go out of scope
+}
+
+void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s) {
+    if (fb.n_items == 0) return;
+    const uint32_t n = (uint32_t)fb.n_items;
+    k_item_keys<<<grid_for(fb.n_items, 256), 256, 0, s>>>(
+        fb.jobs.as<FieldJob>(), fb.items.as<uint2>(), n, fb.keys.as<uint32_t>(),
+        fb.vals.as<uint32_t>());
+    CSL_LAUNCH_CHECK("batch item keys");
+    radix_sort_pairs(fb.keys.as<uint32_t>(), fb.vals.as<uint32_t>(), fb.tmp_keys.as<uint32_t>(),
+                     fb.tmp_vals.as<uint32_t>(), fb.n_items, 16, s);
+    CSL_CUDA(cudaMemsetAsync(fb.counter.get(), 0, 4, s));
+    const FieldJob* jobs = fb.jobs.as<FieldJob>();
+    const uint2* items = fb.items.as<uint2>();
+    const uint32_t* order = fb.vals.as<uint32_t>();
+    uint32_t* counter = fb.counter.as<uint32_t>();
+    switch (fb.S) {
+        case 1: k_field_batch<1><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;
+        case 2: k_field_batch<2><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;
+        case 4: k_field_batch<4><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;
+        case 8: k_field_batch<8><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;
+        default: fail(CSL_ERR_INVALID_ARG, "slab depth must be 1, 2, 4 or 8");
+    }
+    CSL_LAUNCH_CHECK("batch field");
 }
 
 }  // namespace csl

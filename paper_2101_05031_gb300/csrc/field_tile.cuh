@@ -151,10 +151,11 @@ __device__ __forceinline__ float segment_term_R4(float t0, float h2, float len) 
     const float d = fmaxf(tau2 - tau1, 0.0f);   // 2 h
     const float s = tau2 + tau1;                 // 2 m
     const float cc = fmaf(-0.25f * s, s, h2);    // h2 - m^2
-    const float dd = 0.15f * d * d;              // 0.6 h^2
-    const float Av = cc - dd;
-    const float B2 = dd * s * s;                 // (2 m h sqrt(0.6))^2
-    return d * fmaf(5.0f / 9.0f, fmaf(Av, Av, B2), (4.0f / 9.0f) * cc * cc);
+    const float d15 = 0.15f * d;
+    const float Av = fmaf(-d15, d, cc);          // h2 - m^2 - 0.6 h^2
+    const float ds = d15 * s;
+    const float B2 = ds * (d * s);               // (2 m h sqrt(0.6))^2 = 0.15 d^2 s^2
+    return d * fmaf(5.0f / 9.0f, fmaf(Av, Av, B2), (4.0f / 9.0f) * (cc * cc));
 }
 
 }  // namespace csl

@@ -1,6 +1,8 @@
 // Internal interfaces of the slicing pipeline (binner, field, contours).
 #pragma once
 
+#include <vector>
+
 #include "lattice.cuh"
 
 namespace csl {
@@ -61,6 +63,27 @@ inline int64_t mask_words_per_layer(int nx, int ny) {
 void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
                  float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s);
 
+// Field of many chunks (the jobs of a batch, one chunk each) in one
+// persistent launch: CTAs take (job, slab, tile) items from a queue sorted
+// longest tile list first. Every job has the same slab depth.
+struct FieldBatchJob {
+    const csl_lattice* L;
+    ChunkGeom g;
+    const SlabBins* bins;   // must stay allocated (same buffers) while the batch lives
+    float* sigma;
+    uint32_t* mask;         // zero on entry of every run
+};
+struct FieldBatch {
+    DevBuf jobs, origins, items, keys, vals, tmp_keys, tmp_vals, counter;
+    int64_t n_items = 0;
+    int S = 0;
+};
+// One-time tables (synchronises s).
+void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb, cudaStream_t s);
+// The run itself: queue order, counter reset, persistent launch of n_ctas
+// CTAs; reads nothing back (capturable in a CUDA graph).
+void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s);
+
 // Contours of the chunk's layers (device arrays, layer-local edge ids).
 struct ChunkContours {
     int64_t n_verts = 0, n_loops = 0;
@@ -73,6 +96,19 @@ struct ChunkContours {
 // hold rp->plan's sizes; they are filled in place.
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
                     bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp = nullptr);
+
+// Slicing request resolution (api.cu): tile / slab / chunk sizes and the
+// binner's rounding margin; the geometry of one chunk; argument checks that
+// fail with CSL_ERR_INVALID_ARG.
+struct SlicePlan {
+    int S, chunk, ntx, nty;
+    float margin;
+};
+SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d);
+ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SlicePlan& p, int first,
+                     int n);
+void validate_desc(const csl_slice_desc* d);
+void require_arg(bool ok, const char* msg);
 
 // Volume fraction per density cell and its adjoint (vf.cu).
 void vf_forward(const csl_lattice* L, const csl_cells& cells, float* vf, cudaStream_t s);

@@ -41,7 +41,8 @@ def test_structs_match_header_layout(tmp_path):
     from paper_2101_05031_gb300 import _lib
     mirrors = {"csl_params": _lib.Params, "csl_lattice_info": _lib.LatticeInfo,
                "csl_slice_desc": _lib.SliceDesc, "csl_contours": _lib.Contours,
-               "csl_stats": _lib.Stats}
+               "csl_stats": _lib.Stats, "csl_batch_opts": _lib.BatchOpts,
+               "csl_batch_info": _lib.BatchInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -74,6 +75,18 @@ def test_errors_cross_the_abi_as_codes():
     d.n_layers = 1
     st = lib.csl_slice_layers(None, ctypes.byref(d), None, None)
     assert st == 1 and b"NULL" in lib.csl_last_error()
+    # batches: argument checks come before any device call
+    descs = (_lib.SliceDesc * 1)()
+    lats = (ctypes.c_void_p * 1)()
+    st = lib.csl_batch_create(lats, descs, 0, None, None, ctypes.byref(out))
+    assert st == 1 and b"n_jobs" in lib.csl_last_error()
+    bad = _lib.BatchOpts(0, 3, 0, 0)
+    st = lib.csl_batch_create(lats, descs, 1, ctypes.byref(bad), None, ctypes.byref(out))
+    assert st == 1 and b"slab" in lib.csl_last_error()
+    st = lib.csl_batch_run(None, None)
+    assert st == 1
+    info = _lib.BatchInfo()
+    assert lib.csl_batch_get_info(None, ctypes.byref(info)) == 1
 
 
 def test_no_gpu_reports_not_ready():
