@@ -135,7 +135,7 @@ def slice_kwargs(cfg, rank, world):
 
 # --------------------------------------------------------------------------- oracle sample
 
-def oracle_sample(cfg, window=256, layer=None, min_seconds=8.0):
+def oracle_sample(cfg, window=256, layer=None, min_seconds=12.0):
     """Times the FP64 oracle (single thread) on a window of one layer: the
     oracle gets the edges whose xy box grown by R meets the window and whose
     z range grown by R contains the layer (its own Eq. 8 sweep then runs)."""
