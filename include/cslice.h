@@ -139,6 +139,10 @@ typedef struct csl_slice_desc {
  * grid edge; a saddle cell joins its inside corners when the mean of its four
  * corner values is >= C.
  */
+/* Host arrays (on_device = 0) share one page-locked block, taken from a
+ * per-process cache so that device-to-host copies run at the link's speed;
+ * csl_contours_free returns the block to the cache (free blocks above 64 GiB
+ * in total are released). */
 typedef struct csl_contours {
     int32_t n_layers;
     int32_t on_device;        /* 1: the arrays below are device pointers           */

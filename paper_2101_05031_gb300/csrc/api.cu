@@ -227,10 +227,7 @@ void csl_contours_free(csl_contours* c) {
         cudaFree(c->xy);
         cudaFree(c->edge_id);
     } else {
-        free(c->layer_loop_off);
-        free(c->loop_vert_off);
-        free(c->xy);
-        free(c->edge_id);
+        host_block_free(c->layer_loop_off);   // one block holds all four arrays
     }
     delete c;
 }
@@ -356,33 +353,30 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
 
         // Gather the chunks into the result: offsets are rebased on the device,
         // then every array is copied straight to its place (device or host).
-        csl_contours* c = new csl_contours();
-        memset(c, 0, sizeof(*c));
-        c->n_layers = d.n_layers;
-        c->on_device = on_dev ? 1 : 0;
         int64_t n_loops = 0, n_verts = 0;
         for (auto& cc : dev_chunks) { n_loops += cc.n_loops; n_verts += cc.n_verts; }
-        c->n_loops = n_loops;
-        c->n_verts = n_verts;
-        auto give_up = [&](const char* what) {
-            csl_contours_free(c);
-            fail(CSL_ERR_OOM, what);
-        };
-        auto dst_alloc = [&](void** p, size_t b) {
-            if (on_dev) {
+        csl_contours* c = nullptr;
+        if (on_dev) {
+            c = new csl_contours();
+            memset(c, 0, sizeof(*c));
+            c->n_layers = d.n_layers;
+            c->on_device = 1;
+            c->n_loops = n_loops;
+            c->n_verts = n_verts;
+            auto dst_alloc = [&](void** p, size_t b) {
                 if (cudaMalloc(p, b ? b : 16) != cudaSuccess) {
                     cudaGetLastError();
-                    give_up("device allocation of the contours failed");
+                    csl_contours_free(c);
+                    fail(CSL_ERR_OOM, "device allocation of the contours failed");
                 }
-            } else {
-                *p = malloc(b ? b : 16);
-                if (!*p) give_up("host allocation of the contours failed");
-            }
-        };
-        dst_alloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8);
-        dst_alloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
-        dst_alloc((void**)&c->xy, (size_t)n_verts * 8);
-        if (want_eid) dst_alloc((void**)&c->edge_id, (size_t)n_verts * 4);
+            };
+            dst_alloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8);
+            dst_alloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
+            dst_alloc((void**)&c->xy, (size_t)n_verts * 8);
+            if (want_eid) dst_alloc((void**)&c->edge_id, (size_t)n_verts * 4);
+        } else {
+            c = new_host_contours(d.n_layers, n_loops, n_verts, want_eid);
+        }
         const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         timed(st.output_ms, [&] {
             int64_t lb = 0, vb = 0;

@@ -419,32 +419,33 @@ csl_status csl_batch_contours(const csl_batch* b, int32_t job, int32_t dst_on_de
         *out = nullptr;
         const auto& J = job_at(b, job);
         const bool on_dev = dst_on_device != 0;
-        csl_contours* c = new csl_contours();
-        memset(c, 0, sizeof(*c));
-        c->n_layers = J.d.n_layers;
-        c->on_device = on_dev ? 1 : 0;
-        c->n_loops = J.cont.n_loops;
-        c->n_verts = J.cont.n_verts;
+        const size_t nl = (size_t)J.d.n_layers + 1, nlo = (size_t)J.cont.n_loops + 1;
+        const size_t nv = (size_t)J.cont.n_verts;
+        csl_contours* c = nullptr;
+        if (on_dev) {
+            c = new csl_contours();
+            memset(c, 0, sizeof(*c));
+            c->n_layers = J.d.n_layers;
+            c->on_device = 1;
+            c->n_loops = J.cont.n_loops;
+            c->n_verts = J.cont.n_verts;
+        } else {
+            c = new_host_contours(J.d.n_layers, J.cont.n_loops, J.cont.n_verts, J.want_eid);
+        }
         try {
             auto alloc = [&](void** p, size_t bytes) {
-                if (bytes == 0) bytes = 16;
-                if (on_dev) {
-                    if (cudaMalloc(p, bytes) != cudaSuccess) {
-                        cudaGetLastError();
-                        fail(CSL_ERR_OOM, "device allocation of the contours failed");
-                    }
-                } else {
-                    *p = malloc(bytes);
-                    if (!*p) fail(CSL_ERR_OOM, "host allocation of the contours failed");
+                if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+                    cudaGetLastError();
+                    fail(CSL_ERR_OOM, "device allocation of the contours failed");
                 }
             };
+            if (on_dev) {
+                alloc((void**)&c->layer_loop_off, nl * 8);
+                alloc((void**)&c->loop_vert_off, nlo * 8);
+                alloc((void**)&c->xy, nv * 8);
+                if (J.want_eid) alloc((void**)&c->edge_id, nv * 4);
+            }
             const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-            const size_t nl = (size_t)J.d.n_layers + 1, nlo = (size_t)J.cont.n_loops + 1;
-            const size_t nv = (size_t)J.cont.n_verts;
-            alloc((void**)&c->layer_loop_off, nl * 8);
-            alloc((void**)&c->loop_vert_off, nlo * 8);
-            alloc((void**)&c->xy, nv * 8);
-            if (J.want_eid) alloc((void**)&c->edge_id, nv * 4);
             CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off, J.cont.layer_loops.get(), nl * 8, kind,
                                      b->st));
             CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off, J.cont.loop_off.get(), nlo * 8, kind,

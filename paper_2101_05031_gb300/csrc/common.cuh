@@ -70,6 +70,17 @@ int64_t device_bytes_peak_and_reset();
 void set_last_error(const std::string& m);
 const char* last_error_cstr();
 
+// Host memory for results handed to the caller: page-locked blocks (so that
+// device-to-host copies run at the link's speed) kept in a per-process cache
+// and reused by later results once the caller frees them. Falls back to
+// malloc when page-locked memory cannot be had. Thread-safe.
+void* host_block_alloc(size_t bytes);
+void host_block_free(void* p);
+
+// Host contours in one host block: [layer_loop_off | loop_vert_off | xy | edge_id];
+// csl_contours_free releases the block (its base is layer_loop_off).
+csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_verts, bool want_eid);
+
 int64_t read_i64(const int64_t* dev, cudaStream_t s);   // synchronising
 void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s);  // synchronising
 
