@@ -251,7 +251,7 @@ csl_status csl_volume_fraction_backward(csl_lattice* lat, const csl_cells* cells
  * contour stages of the jobs run on parallel branches, and the field of all
  * jobs is one persistent kernel whose CTAs take (job, slab, tile) items from
  * a queue sorted longest tile list first. With autotune set, it times the
- * graph for every slab depth S in {2, 4, 8} and 2, 3 or 4 resident CTAs per
+ * graph for every slab depth S in {2, 4, 8} and 2, 4 or 6 resident CTAs per
  * SM and keeps the fastest; the choice is cached per process for the same
  * job sizes. The tile is fixed at 16 x 16 pixels and the staging chunk at 256
  * records (one per thread of the 8-warp CTA).
@@ -274,7 +274,7 @@ typedef struct csl_batch csl_batch;   /* opaque */
 typedef struct csl_batch_opts {
     int32_t autotune;         /* nonzero: time the (slab, CTAs per SM) candidates        */
     int32_t slab;             /* without autotune: 0 (8, or less for short jobs) or 2, 4, 8 */
-    int32_t ctas_per_sm;      /* without autotune: 0 (4) or 1 .. 4                     */
+    int32_t ctas_per_sm;      /* without autotune: 0 (4) or 1 .. 6                     */
     int32_t branches;         /* parallel graph branches for binner and contours: 0 (8) or 1 .. 32 */
 } csl_batch_opts;
 

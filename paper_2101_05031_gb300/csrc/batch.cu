@@ -281,7 +281,7 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
         if (opts) o = *opts;
         require_arg(o.slab == 0 || o.slab == 2 || o.slab == 4 || o.slab == 8,
                     "slab must be 0, 2, 4 or 8");
-        require_arg(o.ctas_per_sm >= 0 && o.ctas_per_sm <= 4, "ctas_per_sm must be in [0, 4]");
+        require_arg(o.ctas_per_sm >= 0 && o.ctas_per_sm <= 6, "ctas_per_sm must be in [0, 6]");
         require_arg(o.branches >= 0 && o.branches <= 32, "branches must be in [0, 32]");
         cudaStream_t user = (cudaStream_t)stream;
         CSL_CUDA(cudaStreamSynchronize(user));   // inputs enqueued before the call are ready
@@ -352,7 +352,7 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
                 double plan_ms = 0.0;
                 float best = 1e30f;
                 int bS = 8, bC = 4, nc = 0;
-                const int slabs[3] = {2, 4, 8}, ctas_c[3] = {2, 3, 4};
+                const int slabs[3] = {2, 4, 8}, ctas_c[3] = {2, 4, 6};
                 for (int si = 0; si < 3; ++si) {
                     const double tp = now_ms();
                     plan_jobs(b, slabs[si]);

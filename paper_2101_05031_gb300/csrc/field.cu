@@ -84,9 +84,6 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
         const float oxh = ox.x, oxl = ox.y, oyh = oy.x, oyl = oy.y, ozh = oz.x, ozl = oz.y;
         const float pxl = ((float)il + 0.5f) * c.fpx;
         const float pyl = ((float)jl + 0.5f) * c.fpx;
-        float zloc[S];
-#pragma unroll
-        for (int l = 0; l < S; ++l) zloc[l] = (float)l * c.fdz;
         const TileCull cull = c.tc;
 
         for (uint32_t c0 = beg; c0 < end; c0 += kFieldThreads) {
@@ -122,7 +119,7 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
 #pragma unroll
                     for (int l = 0; l < S; ++l) {
                         if (lm & (1u << l)) {
-                            const float dz = zloc[l] - A.z;
+                            const float dz = (float)l * c.fdz - A.z;
                             const float t0 = fmaf(dz, B.y, txy);
                             const float ex = fmaf(-t0, A.w, dx);
                             const float ey = fmaf(-t0, B.x, dy);
@@ -186,7 +183,7 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
 }
 
 template <int S, bool COUNT>
-__global__ void __launch_bounds__(kFieldThreads, 4)
+__global__ void __launch_bounds__(kFieldThreads, 8)
 k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
         const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
         float* __restrict__ sigma, uint32_t* __restrict__ mask,
@@ -211,7 +208,7 @@ static_assert(sizeof(FieldJob) % 4 == 0, "FieldJob is copied as 32-bit words");
 // CTA takes the next item from a shared counter, in the order `order` gives
 // (longest tile lists first, so the short ones fill the tail).
 template <int S>
-__global__ void __launch_bounds__(kFieldThreads, 4)
+__global__ void __launch_bounds__(kFieldThreads, 6)
 k_field_batch(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items,
               const uint32_t* __restrict__ order, uint32_t n_items, uint32_t* counter) {
     __shared__ uint32_t s_item;

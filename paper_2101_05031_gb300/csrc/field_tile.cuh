@@ -91,6 +91,72 @@ __device__ __forceinline__ void load_record(const csl_rec* rp_rec, float oxh, fl
     B = make_float4(r1.x, r1.y, r1.z, r1.w * inv_R4);
 }
 
+// Extent of a staged edge (A, B) in layer l of a 16 x 16 tile: the pixel rows
+// j0..j1 and columns i0..i1 whose centres lie in the xy box of the edge clipped
+// to |z - z_l| <= cull, grown by cull. Packed as j0 | j1 << 4 | i0 << 8 |
+// i1 << 12 | 1 << 16; 0 when the box misses the tile or the layer.
+__device__ __forceinline__ uint32_t item_extent(const float4 A, const float4 B, int l,
+                                                const TileCull& c) {
+    const float ax = A.x, ay = A.y, az = A.z, ux = A.w, uy = B.x, uz = B.y, len = B.z;
+    const float zl = (float)l * c.fdz;
+    float t_lo = 0.0f, t_hi = len;
+    if (uz > 1e-12f) {
+        const float inv_uz = 1.0f / uz;
+        t_lo = fmaxf((zl - c.cull - az) * inv_uz, 0.0f);
+        t_hi = fminf((zl + c.cull - az) * inv_uz, len);
+    } else if (fabsf(az - zl) > c.cull) {
+        return 0u;
+    }
+    if (t_lo > t_hi) return 0u;
+    const float xa = fmaf(t_lo, ux, ax), xb = fmaf(t_hi, ux, ax);
+    const float ya = fmaf(t_lo, uy, ay), yb = fmaf(t_hi, uy, ay);
+    const float inv_px = 1.0f / c.fpx;
+    // pixel i has its centre at (i + 1/2) px: i in [ceil(x_min/px - 1/2), floor(x_max/px - 1/2)]
+    const float fx0 = fmaf(fminf(xa, xb) - c.cull, inv_px, -0.5f);
+    const float fx1 = fmaf(fmaxf(xa, xb) + c.cull, inv_px, -0.5f);
+    const float fy0 = fmaf(fminf(ya, yb) - c.cull, inv_px, -0.5f);
+    const float fy1 = fmaf(fmaxf(ya, yb) + c.cull, inv_px, -0.5f);
+    const int i0 = max(0, (int)ceilf(fmaxf(fx0, -1.0f)));
+    const int i1 = min(15, (int)floorf(fminf(fx1, 16.0f)));
+    const int j0 = max(0, (int)ceilf(fmaxf(fy0, -1.0f)));
+    const int j1 = min(15, (int)floorf(fminf(fy1, 16.0f)));
+    if (i0 > i1 || j0 > j1) return 0u;
+    return (uint32_t)j0 | ((uint32_t)j1 << 4) | ((uint32_t)i0 << 8) | ((uint32_t)i1 << 12) |
+           (1u << 16);
+}
+
+// Pixels i0..i1 of row j (within the extent e) whose centres lie within
+// sqrt(r2) of the edge's line in plane zl (tile-local). The line meets the
+// row's line {(x, y_j, zl)} at distance |Z u_y - Y u_z| / sqrt(a), a = u_y^2 +
+// u_z^2, closest at X* = u_x (Y u_y + Z u_z) / a, and the squared distance
+// grows as a (X - X*)^2, so the row's points within the radius are
+// |X - X*| <= sqrt(r2 a - (Z u_y - Y u_z)^2) / a. Widened by 0.05 px. An edge
+// along x (a ~ 0) keeps the extent's columns.
+__device__ __forceinline__ bool row_span(const float4 A, const float4 B, float zl, int j,
+                                         uint32_t e, const TileCull& c, float r2, int& i0,
+                                         int& i1) {
+    const float ux = A.w, uy = B.x, uz = B.y;
+    i0 = (int)((e >> 8) & 15u);
+    i1 = (int)((e >> 12) & 15u);
+    const float a = fmaf(uy, uy, uz * uz);
+    if (a > 1e-6f) {
+        const float Y = fmaf((float)j, c.fpx, 0.5f * c.fpx) - A.y;
+        const float Z = zl - A.z;
+        const float dm = fmaf(Z, uy, -(Y * uz));
+        const float q = fmaf(r2, a, -(dm * dm));
+        if (q < 0.0f) return false;
+        const float inv_a = 1.0f / a;
+        const float xs = ux * fmaf(Y, uy, Z * uz) * inv_a + A.x;
+        const float half = sqrt_approx(q) * inv_a;
+        const float inv_px = 1.0f / c.fpx;
+        const float f0 = fmaf(xs - half, inv_px, -0.55f);
+        const float f1 = fmaf(xs + half, inv_px, -0.45f);
+        i0 = max(i0, (int)ceilf(fmaxf(f0, -1.0f)));
+        i1 = min(i1, (int)floorf(fminf(f1, 16.0f)));
+    }
+    return i0 <= i1;
+}
+
 // The warps of one layer l whose 8 x 4 block the staged edge (A, B) may reach
 // (the test of stage_record for a single layer): bit w set for warp w.
 __device__ __forceinline__ uint32_t cull_layer(const float4 A, const float4 B, int l,

@@ -161,7 +161,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
             const uint32_t id = id_row(b, 0);
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
             const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
-            const float t = (sa - c.C) / (sa - sbv);
+            const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
             const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
             *reinterpret_cast<float2*>(&rec[id].x) =
                 make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
@@ -171,7 +171,7 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
             const uint32_t id = id_row(b, 1);
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
             const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
-            const float t = (sa - c.C) / (sa - sbv);
+            const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
             const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
             *reinterpret_cast<float2*>(&rec[id].x) =
                 make_float2(c.fx0 + ((float)I - 0.5f) * c.fpx, c.fy0 + yp * c.fpx);
@@ -205,8 +205,9 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
     }
 }
 
-// pred[succ[i]] = i. Every crossing must have exactly one successor in range;
-// anything else is reported through *status and nothing is written out of range.
+// pred[succ[i]] = i (thread i writes next to its neighbours' targets: the
+// successors of consecutive crossings are close). A successor out of range is
+// reported through *status and nothing is written.
 __global__ void k_pred(const Xing* __restrict__ rec, int64_t n, uint32_t* __restrict__ pred,
                        uint32_t* status) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -224,12 +225,18 @@ __device__ __forceinline__ bool is_splitter(uint32_t i, uint32_t pred_i, uint32_
     return (pred_i > i && succ_i > i) || ((i * 2654435761u) >> 27) == 0u;
 }
 
+// flag[i] = 1 for splitters; nxt[i] = successor | (splitter << 31), the only
+// array the segment walks read.
 __global__ void k_split_flags(const Xing* __restrict__ rec, const uint32_t* __restrict__ pred,
-                              int64_t n, uint32_t* __restrict__ flag) {
+                              int64_t n, uint32_t* __restrict__ flag,
+                              uint32_t* __restrict__ nxt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t q = (uint32_t)i;
-        flag[i] = is_splitter(q, pred[q], rec[q].succ) ? 1u : 0u;
+        const uint32_t sc = rec[q].succ;
+        const bool sp = is_splitter(q, pred[q], sc);
+        flag[i] = sp ? 1u : 0u;
+        nxt[i] = (sc & 0x7fffffffu) | (sp ? 0x80000000u : 0u);
     }
 }
 
@@ -245,8 +252,9 @@ __global__ void k_split_list(const uint32_t* __restrict__ flag, const uint32_t* 
         }
 }
 
-// Each splitter walks its segment up to the next splitter.
-__global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ flag,
+// Each splitter walks its segment up to the next splitter (nxt: successor |
+// splitter bit, one 4-byte load per step).
+__global__ void k_segments(const uint32_t* __restrict__ nxt,
                            const uint32_t* __restrict__ spos, const uint32_t* __restrict__ split_id,
                            int64_t ns, int64_t n, uint32_t* __restrict__ seg_next,
                            uint32_t* __restrict__ seg_len, uint32_t* status) {
@@ -259,10 +267,12 @@ __global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restr
             seg_len[t] = 1;
             continue;
         }
-        uint32_t j = rec[s0].succ;
+        uint32_t j = nxt[s0] & 0x7fffffffu;
         int64_t len = 1;
-        while ((int64_t)j < n && !flag[j] && len <= n) {
-            j = rec[j].succ;
+        while ((int64_t)j < n && len <= n) {
+            const uint32_t v = nxt[j];
+            if (v >> 31) break;   // the next splitter
+            j = v & 0x7fffffffu;
             ++len;
         }
         if ((int64_t)j >= n || len > n) {   // corrupt links: report, never loop forever
@@ -271,14 +281,14 @@ __global__ void k_segments(const Xing* __restrict__ rec, const uint32_t* __restr
             seg_len[t] = 1;
             continue;
         }
-        const uint32_t nxt = spos[j];
-        if ((int64_t)nxt >= ns) {   // more splitters than planned (flagged)
+        const uint32_t sn = spos[j];
+        if ((int64_t)sn >= ns) {   // more splitters than planned (flagged)
             atomicOr(status, ST_CAPACITY);
             seg_next[t] = (uint32_t)t;
             seg_len[t] = 1;
             continue;
         }
-        seg_next[t] = nxt;
+        seg_next[t] = sn;
         seg_len[t] = (uint32_t)len;
     }
 }
@@ -575,6 +585,8 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         if (rp && !replay) rp->plan->ns = rp->plan->nl = rp->plan->n_loops = 0;
         return;
     }
+    // the successor bit trick of k_split_flags needs ids below 2^31
+    if (n_cross >= ((int64_t)1 << 31)) fail(CSL_ERR_CAPACITY, "marching squares: too many crossings");
     DevBuf rec((size_t)n_cross * sizeof(Xing), s);
     CSL_CUDA(cudaMemsetAsync(rec.get(), 0xff, (size_t)n_cross * sizeof(Xing), s));
     Dense D{ew.as<uint32_t>(), prefix.as<uint32_t>(), c.edge_wpl, c.ewr};
@@ -586,12 +598,13 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
     DevBuf pred((size_t)n_cross * 4, s), sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
+    DevBuf nxt((size_t)n_cross * 4, s);
     CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms pred");
     k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
-                                     sflag.as<uint32_t>());
+                                     sflag.as<uint32_t>(), nxt.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms splitter flags");
     exclusive_scan_u32(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, status + 2, s);
     int64_t ns;
@@ -614,11 +627,12 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     k_split_list<<<gx, 256, 0, s>>>(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, ns,
                                     split_id.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms splitter list");
-    k_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), sflag.as<uint32_t>(), spos.as<uint32_t>(),
+    k_segments<<<gs, 256, 0, s>>>(nxt.as<uint32_t>(), spos.as<uint32_t>(),
                                   split_id.as<uint32_t>(), ns, n_cross, seg_next.as<uint32_t>(),
                                   seg_len.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms segments");
     sflag.release();
+    nxt.release();
     // short splitter cycles by walking them; long ones by pointer jumping
     DevBuf cm((size_t)ns * 4, s), long_list((size_t)ns * 4, s), long_pos((size_t)ns * 4, s);
     DevBuf rank_start((size_t)ns * 4, s), loop_len((size_t)ns * 4, s);

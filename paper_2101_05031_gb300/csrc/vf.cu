@@ -122,6 +122,7 @@ struct GradConst {
     int32_t nx, ny, ntx, n_tiles, n_layers;
     int32_t cx, cy, m, first_cl;
     float R2, fpx, fdz, C, invT, inv_m3;
+    float span_r2;   // squared radius of the footprint rows (R plus slack)
     TileCull tc;
     const float2* org_x;
     const float2* org_y;
@@ -132,14 +133,14 @@ struct GradConst {
 // staged edge. partial[entry] = {sum alpha R^4 I, sum alpha w dI/da (3),
 // sum alpha w dI/db (3), 0}.
 template <int S>
-__global__ void __launch_bounds__(kVfThreads, 2)
+__global__ void __launch_bounds__(kVfThreads, 4)
 k_vf_grad(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
           const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, GradConst c,
           const float* __restrict__ g_cells, float4* __restrict__ partial) {
     __shared__ float4 s_a[kVfThreads];
     __shared__ float4 s_b[kVfThreads];
     __shared__ uint64_t s_mask[kVfThreads];
-    extern __shared__ float s_part[];   // [kVfThreads][kTileWarps][7]
+    __shared__ float s_alpha[S * kTile * kTile];   // [layer][j][i]
 
     const int tile = blockIdx.x, slab = blockIdx.y;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
@@ -147,6 +148,7 @@ k_vf_grad(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t beg = tstart[key], end = tend[key];
     if (end <= beg) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    (void)lane;
     const int wx = warp & 1, wy = warp >> 1;
     const int il = wx * 8 + (lane & 7), jl = wy * 4 + (lane >> 3);
     const int l0 = slab * S;
@@ -209,104 +211,79 @@ k_vf_grad(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
             alpha[l] = g_cells[cell] * c.inv_m3 * s * (1.0f - s) * c.invT;
         }
     }
-    // pass 2: derivatives per staged edge
+    // alpha of every sample of the tile, for pass 2 (0 outside the grid / slab)
+#pragma unroll
+    for (int l = 0; l < S; ++l) s_alpha[(l * kTile + jl) * kTile + il] = alpha[l];
+    // pass 2: one staged edge per thread; the thread visits the samples of its
+    // edge's footprint (rows of the clipped box, cut to the pixels within R of
+    // the line) and sums the 7 partials in registers, in a fixed order. A
+    // sample with alpha == 0 (the sigmoid saturates to 0 or 1 in FP32) adds
+    // exactly nothing and is skipped.
     for (uint32_t c0 = beg; c0 < end; c0 += kVfThreads) {
         const int cnt = (int)min((uint32_t)kVfThreads, end - c0);
-        if ((int)threadIdx.x < cnt) {
-            float4 A, B;
-            s_mask[threadIdx.x] = stage_record(rec + vals[c0 + threadIdx.x], ox.x, ox.y, oy.x,
-                                               oy.y, oz.x, oz.y, nl, cull, A, B);
-            s_a[threadIdx.x] = A;
-            s_b[threadIdx.x] = B;
-        }
-        for (int q = threadIdx.x; q < cnt * kTileWarps * 7; q += kVfThreads) s_part[q] = 0.0f;
-        __syncthreads();
-        for (int i0 = 0; i0 < cnt; i0 += 32) {
-            const int i = i0 + lane;
-            const uint32_t wm = i < cnt ? (uint32_t)(s_mask[i] >> (warp * 8)) & 0xffu : 0u;
-            uint32_t ball = __ballot_sync(0xffffffffu, wm != 0u);
-            while (ball) {
-                const int b = __ffs(ball) - 1;
-                ball &= ball - 1u;
-                const uint32_t lm = __shfl_sync(0xffffffffu, wm, b);
-                const float4 A = s_a[i0 + b], B = s_b[i0 + b];
-                const float ux = A.w, uy = B.x, uz = B.y, len = B.z;
-                const float inv_len = len > 0.0f ? 1.0f / len : 0.0f;
-                const float dx = pxl - A.x, dy = pyl - A.y;
-                const float txy = fmaf(dy, uy, dx * ux);
-                float gw = 0.0f, gax = 0.0f, gay = 0.0f, gaz = 0.0f, gbx = 0.0f, gby = 0.0f,
-                      gbz = 0.0f;
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    if (lm & (1u << l)) {
-                        const float dz = (float)l * c.fdz - A.z;
-                        const float t0 = fmaf(dz, uz, txy);
-                        const float ex = fmaf(-t0, ux, dx), ey = fmaf(-t0, uy, dy);
-                        const float ez = fmaf(-t0, uz, dz);
-                        const float h2 = fmaxf(c.R2 - fmaf(ez, ez, fmaf(ey, ey, ex * ex)), 0.0f);
-                        const float w = sqrt_approx(h2);
-                        const float tau1 = fmaxf(-t0, -w), tau2 = fminf(len - t0, w);
-                        const float hh = 0.5f * fmaxf(tau2 - tau1, 0.0f);   // half width
-                        const float mm = 0.5f * (tau2 + tau1);               // midpoint
-                        const float del = 0.7745966692414834f * hh;          // sqrt(0.6) h
-                        const float ta = mm - del, tb = mm + del;
-                        const float ga = fmaf(-ta, ta, h2), gm = fmaf(-mm, mm, h2),
-                                    gb = fmaf(-tb, tb, h2);
-                        const float W1 = (5.0f / 9.0f) * hh, W2 = (8.0f / 9.0f) * hh;
-                        const float wa = W1 * ga, wm2 = W2 * gm, wb = W1 * gb;
-                        const float I4 = fmaf(wa, ga, fmaf(wm2, gm, wb * gb));
-                        const float M0 = wa + wm2 + wb;
-                        const float M1 = fmaf(wa, ta, fmaf(wm2, mm, wb * tb));
-                        const float M2 = fmaf(wa * ta, ta, fmaf(wm2 * mm, mm, wb * tb * tb));
-                        const float r = t0 * inv_len;
-                        const float il4 = I4 * inv_len;
-                        const float cau = fmaf(1.0f - r, M1, -M2 * inv_len);
-                        const float cae = fmaf(1.0f - r, M0, -M1 * inv_len);
-                        const float cbu = fmaf(r, M1, M2 * inv_len);
-                        const float cbe = fmaf(r, M0, M1 * inv_len);
-                        const float al = alpha[l], alw = alpha[l] * B.w;
-                        gw = fmaf(al, I4, gw);
-                        // R^4 dI/da = -u I4/L - 4 (u cau - e cae); times alpha w/R^4
-                        gax = fmaf(alw, fmaf(-ux, il4, -4.0f * fmaf(ux, cau, -ex * cae)), gax);
-                        gay = fmaf(alw, fmaf(-uy, il4, -4.0f * fmaf(uy, cau, -ey * cae)), gay);
-                        gaz = fmaf(alw, fmaf(-uz, il4, -4.0f * fmaf(uz, cau, -ez * cae)), gaz);
-                        gbx = fmaf(alw, fmaf(ux, il4, -4.0f * fmaf(ux, cbu, -ex * cbe)), gbx);
-                        gby = fmaf(alw, fmaf(uy, il4, -4.0f * fmaf(uy, cbu, -ey * cbe)), gby);
-                        gbz = fmaf(alw, fmaf(uz, il4, -4.0f * fmaf(uz, cbu, -ez * cbe)), gbz);
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    gw += __shfl_xor_sync(0xffffffffu, gw, o);
-                    gax += __shfl_xor_sync(0xffffffffu, gax, o);
-                    gay += __shfl_xor_sync(0xffffffffu, gay, o);
-                    gaz += __shfl_xor_sync(0xffffffffu, gaz, o);
-                    gbx += __shfl_xor_sync(0xffffffffu, gbx, o);
-                    gby += __shfl_xor_sync(0xffffffffu, gby, o);
-                    gbz += __shfl_xor_sync(0xffffffffu, gbz, o);
-                }
-                if (lane == 0) {
-                    float* p = s_part + ((i0 + b) * kTileWarps + warp) * 7;
-                    p[0] = gw;
-                    p[1] = gax;
-                    p[2] = gay;
-                    p[3] = gaz;
-                    p[4] = gbx;
-                    p[5] = gby;
-                    p[6] = gbz;
+        __syncthreads();   // s_alpha written (first chunk) / nothing else shared here
+        if ((int)threadIdx.x >= cnt) continue;
+        float4 A, B;
+        load_record(rec + vals[c0 + threadIdx.x], ox.x, ox.y, oy.x, oy.y, oz.x, oz.y,
+                    cull.inv_R4, A, B);
+        const float ux = A.w, uy = B.x, uz = B.y, len = B.z;
+        const float inv_len = len > 0.0f ? 1.0f / len : 0.0f;
+        float gw = 0.0f, gax = 0.0f, gay = 0.0f, gaz = 0.0f, gbx = 0.0f, gby = 0.0f, gbz = 0.0f;
+        for (int l = 0; l < nl; ++l) {
+            const uint32_t e = item_extent(A, B, l, cull);
+            if (!e) continue;
+            const float zl = (float)l * c.fdz;
+            const int j0 = (int)(e & 15u), j1 = (int)((e >> 4) & 15u);
+            for (int j = j0; j <= j1; ++j) {
+                int i0, i1;
+                if (!row_span(A, B, zl, j, e, cull, c.span_r2, i0, i1)) continue;
+                const float dy = ((float)j + 0.5f) * c.fpx - A.y;
+                const float dz = zl - A.z;
+                const float* arow = s_alpha + (l * kTile + j) * kTile;
+                for (int i = i0; i <= i1; ++i) {
+                    const float al = arow[i];
+                    if (al == 0.0f) continue;
+                    const float dx = ((float)i + 0.5f) * c.fpx - A.x;
+                    const float txy = fmaf(dy, uy, dx * ux);
+                    const float t0 = fmaf(dz, uz, txy);
+                    const float ex = fmaf(-t0, ux, dx), ey = fmaf(-t0, uy, dy);
+                    const float ez = fmaf(-t0, uz, dz);
+                    const float h2 = fmaxf(c.R2 - fmaf(ez, ez, fmaf(ey, ey, ex * ex)), 0.0f);
+                    if (h2 == 0.0f) continue;
+                    const float w = sqrt_approx(h2);
+                    const float tau1 = fmaxf(-t0, -w), tau2 = fminf(len - t0, w);
+                    const float hh = 0.5f * fmaxf(tau2 - tau1, 0.0f);   // half width
+                    const float mm = 0.5f * (tau2 + tau1);               // midpoint
+                    const float del = 0.7745966692414834f * hh;          // sqrt(0.6) h
+                    const float ta = mm - del, tb = mm + del;
+                    const float ga = fmaf(-ta, ta, h2), gm = fmaf(-mm, mm, h2),
+                                gb = fmaf(-tb, tb, h2);
+                    const float W1 = (5.0f / 9.0f) * hh, W2 = (8.0f / 9.0f) * hh;
+                    const float wa = W1 * ga, wm2 = W2 * gm, wb = W1 * gb;
+                    const float I4 = fmaf(wa, ga, fmaf(wm2, gm, wb * gb));
+                    const float M0 = wa + wm2 + wb;
+                    const float M1 = fmaf(wa, ta, fmaf(wm2, mm, wb * tb));
+                    const float M2 = fmaf(wa * ta, ta, fmaf(wm2 * mm, mm, wb * tb * tb));
+                    const float r = t0 * inv_len;
+                    const float il4 = I4 * inv_len;
+                    const float cau = fmaf(1.0f - r, M1, -M2 * inv_len);
+                    const float cae = fmaf(1.0f - r, M0, -M1 * inv_len);
+                    const float cbu = fmaf(r, M1, M2 * inv_len);
+                    const float cbe = fmaf(r, M0, M1 * inv_len);
+                    const float alw = al * B.w;
+                    gw = fmaf(al, I4, gw);
+                    // R^4 dI/da = -u I4/L - 4 (u cau - e cae); times alpha w/R^4
+                    gax = fmaf(alw, fmaf(-ux, il4, -4.0f * fmaf(ux, cau, -ex * cae)), gax);
+                    gay = fmaf(alw, fmaf(-uy, il4, -4.0f * fmaf(uy, cau, -ey * cae)), gay);
+                    gaz = fmaf(alw, fmaf(-uz, il4, -4.0f * fmaf(uz, cau, -ez * cae)), gaz);
+                    gbx = fmaf(alw, fmaf(ux, il4, -4.0f * fmaf(ux, cbu, -ex * cbe)), gbx);
+                    gby = fmaf(alw, fmaf(uy, il4, -4.0f * fmaf(uy, cbu, -ey * cbe)), gby);
+                    gbz = fmaf(alw, fmaf(uz, il4, -4.0f * fmaf(uz, cbu, -ez * cbe)), gbz);
                 }
             }
         }
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            float v[7] = {0, 0, 0, 0, 0, 0, 0};
-            const float* p = s_part + threadIdx.x * kTileWarps * 7;
-            for (int w = 0; w < kTileWarps; ++w)
-                for (int q = 0; q < 7; ++q) v[q] += p[w * 7 + q];
-            partial[2 * (int64_t)(c0 + threadIdx.x)] = make_float4(v[0], v[1], v[2], v[3]);
-            partial[2 * (int64_t)(c0 + threadIdx.x) + 1] = make_float4(v[4], v[5], v[6], 0.0f);
-        }
-        __syncthreads();
+        partial[2 * (int64_t)(c0 + threadIdx.x)] = make_float4(gw, gax, gay, gaz);
+        partial[2 * (int64_t)(c0 + threadIdx.x) + 1] = make_float4(gbx, gby, gbz, 0.0f);
     }
 }
 
@@ -480,8 +457,6 @@ void vf_backward(csl_lattice* L, const csl_cells& cells, const float* grad_vf, f
     const int cz = cells.dims[2];
     DevBuf acc((size_t)ne * 32, s);
     CSL_CUDA(cudaMemsetAsync(acc.get(), 0, (size_t)ne * 32, s));
-    const size_t smem = (size_t)kVfThreads * kTileWarps * 7 * sizeof(float);
-    static bool smem_set[4] = {false, false, false, false};
     for (int first = 0; first < cz; first += per) {
         const int n = std::min(per, cz - first);
         ChunkGeom g = vf_geom(L, cells, first, n);
@@ -507,29 +482,27 @@ void vf_backward(csl_lattice* L, const csl_cells& cells, const float* grad_vf, f
         c.invT = (float)(1.0 / cells.temperature);
         c.inv_m3 = 1.0f / (float)(cells.m * cells.m * cells.m);
         c.tc = tile_cull(g);
+        {
+            const double rs = L->R * (1.0 + 2e-4) + 1e-6;
+            c.span_r2 = (float)(rs * rs);
+        }
         c.org_x = org.as<float2>();
         c.org_y = c.org_x + g.ntx;
         c.org_z = c.org_y + g.nty;
         dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
-#define CSL_VF_CASE(SV, IDX)                                                                   \
+#define CSL_VF_CASE(SV)                                                                        \
     case SV:                                                                                   \
-        if (!smem_set[IDX]) {                                                                  \
-            CSL_CUDA(cudaFuncSetAttribute(k_vf_grad<SV>,                                       \
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                                          (int)smem));                                         \
-            smem_set[IDX] = true;                                                              \
-        }                                                                                      \
-        k_vf_grad<SV><<<grid, kVfThreads, smem, s>>>(L->rec.as<csl_rec>(),                     \
-                                                     bins.vals.as<uint32_t>(),                 \
-                                                     bins.tile_start.as<uint32_t>(),           \
-                                                     bins.tile_end.as<uint32_t>(), c, grad_vf, \
-                                                     partial.as<float4>());                    \
+        k_vf_grad<SV><<<grid, kVfThreads, 0, s>>>(L->rec.as<csl_rec>(),                        \
+                                                  bins.vals.as<uint32_t>(),                    \
+                                                  bins.tile_start.as<uint32_t>(),              \
+                                                  bins.tile_end.as<uint32_t>(), c, grad_vf,    \
+                                                  partial.as<float4>());                       \
         break;
         switch (cells.m) {
-            CSL_VF_CASE(1, 0)
-            CSL_VF_CASE(2, 1)
-            CSL_VF_CASE(4, 2)
-            CSL_VF_CASE(8, 3)
+            CSL_VF_CASE(1)
+            CSL_VF_CASE(2)
+            CSL_VF_CASE(4)
+            CSL_VF_CASE(8)
             default: fail(CSL_ERR_INVALID_ARG, "m must be 1, 2, 4 or 8");
         }
 #undef CSL_VF_CASE

@@ -116,7 +116,7 @@ def test_autotune_and_cache(job_set):
     info = b.info()
     ref = [_per_job(lat, d, info.slab) for lat, d in jobs[:3]]
     assert info.n_candidates == 9 and info.from_cache == 0
-    assert info.slab in (2, 4, 8) and info.ctas_per_sm in (2, 3, 4)
+    assert info.slab in (2, 4, 8) and info.ctas_per_sm in (2, 4, 6)
     ms = list(info.cand_ms)[:9]
     assert all(m > 0 for m in ms)
     best = int(np.argmin(ms))
