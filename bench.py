@@ -34,7 +34,7 @@ F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the fiel
 # DRAM bytes (read + write) per pixel-layer of one field-kernel launch, from an
 # ncu capture of the current field kernel on the 12.96M-strut graded lattice
 # (1.12 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
-FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.1226e9 / (64 * 2000 * 2000)
+FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.1262e9 / (64 * 2000 * 2000)
 N_SM = 152
 FP32_LANES = 128
 MAX_SM_MHZ = 2070.0
@@ -320,7 +320,15 @@ def main():
                     help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
+    ap.add_argument("--only", choices=["10M", "vf", "batched"],
+                    help="run only one of the extra lines and print it (profiling runs)")
     args = ap.parse_args()
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch}[args.only]
+        print(json.dumps(fn(args.steps, args.warmup)), flush=True)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -227,7 +227,8 @@ void csl_contours_free(csl_contours* c) {
         cudaFree(c->xy);
         cudaFree(c->edge_id);
     } else {
-        host_block_free(c->layer_loop_off);   // one block holds all four arrays
+        host_block_free(c->layer_loop_off);   // offsets block
+        host_block_free(c->xy);               // vertex block (edge ids included)
     }
     delete c;
 }
@@ -312,6 +313,36 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             mask_ws.alloc((size_t)chunk_alloc * mask_layer * 4, s);
 
         std::vector<ChunkContours> dev_chunks;
+        // Host output: the vertices of each chunk are copied to the host while
+        // the next chunks are computed (a second stream), into the largest
+        // cached page-locked block, as far as it reaches; the rest is copied
+        // at the end. Without a cached block everything is copied at the end.
+        struct Spec {
+            void* block = nullptr;
+            size_t bytes = 0, eid_off = 0;
+            int64_t cap = 0;          // vertices that fit
+            int64_t copied = 0;       // vertices already copied (chunks 0..k)
+            cudaStream_t cs = nullptr;
+            cudaEvent_t ev = nullptr;
+            ~Spec() {
+                if (cs) cudaStreamSynchronize(cs);
+                if (ev) cudaEventDestroy(ev);
+                if (cs) cudaStreamDestroy(cs);
+                if (block) host_block_free(block);
+            }
+        } spec;
+        if (want_contours && !on_dev && d.n_layers > 0) {
+            spec.block = host_block_take_largest(&spec.bytes);
+            if (spec.block) {
+                spec.eid_off = vertex_block_eid_offset(spec.bytes, want_eid);
+                spec.cap = want_eid ? std::min<int64_t>(spec.eid_off / 8,
+                                                        (spec.bytes - spec.eid_off) / 4)
+                                    : (int64_t)(spec.bytes / 8);
+                CSL_CUDA(cudaStreamCreateWithFlags(&spec.cs, cudaStreamNonBlocking));
+                CSL_CUDA(cudaEventCreateWithFlags(&spec.ev, cudaEventDisableTiming));
+            }
+        }
+        bool spec_all = spec.block != nullptr;   // every chunk's vertices went to the block
         for (int first = 0; first < d.n_layers; first += p.chunk) {
             const int n = std::min(p.chunk, d.n_layers - first);
             ChunkGeom g = chunk_geom(L, d, p, first, n);
@@ -337,6 +368,22 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             });
             st.crossings += cc.n_verts;
             st.loops += cc.n_loops;
+            if (spec_all && spec.copied + cc.n_verts <= spec.cap) {
+                if (cc.n_verts) {
+                    CSL_CUDA(cudaEventRecord(spec.ev, s));
+                    CSL_CUDA(cudaStreamWaitEvent(spec.cs, spec.ev, 0));
+                    char* base = static_cast<char*>(spec.block);
+                    CSL_CUDA(cudaMemcpyAsync(base + spec.copied * 8, cc.xy.get(), cc.n_verts * 8,
+                                             cudaMemcpyDeviceToHost, spec.cs));
+                    if (want_eid)
+                        CSL_CUDA(cudaMemcpyAsync(base + spec.eid_off + spec.copied * 4,
+                                                 cc.eid.get(), cc.n_verts * 4,
+                                                 cudaMemcpyDeviceToHost, spec.cs));
+                }
+                spec.copied += cc.n_verts;
+            } else {
+                spec_all = false;
+            }
             dev_chunks.push_back(std::move(cc));
         }
         CSL_CUDA(cudaStreamSynchronize(s));
@@ -374,6 +421,9 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             dst_alloc((void**)&c->loop_vert_off, (size_t)(n_loops + 1) * 8);
             dst_alloc((void**)&c->xy, (size_t)n_verts * 8);
             if (want_eid) dst_alloc((void**)&c->edge_id, (size_t)n_verts * 4);
+        } else if (spec_all) {
+            c = new_host_contours(d.n_layers, n_loops, n_verts, want_eid, spec.block);
+            spec.block = nullptr;   // now owned by c
         } else {
             c = new_host_contours(d.n_layers, n_loops, n_verts, want_eid);
         }
@@ -398,7 +448,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                                          (size_t)(n + 1) * 8, kind, s));
                 CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off + lb, cc.loop_off.get(),
                                          (size_t)(cc.n_loops + 1) * 8, kind, s));
-                if (cc.n_verts) {
+                if (cc.n_verts && !(spec_all && !on_dev)) {   // else already on the host
                     CSL_CUDA(cudaMemcpyAsync(c->xy + 2 * vb, cc.xy.get(), cc.n_verts * 8, kind, s));
                     if (want_eid)
                         CSL_CUDA(cudaMemcpyAsync(c->edge_id + vb, cc.eid.get(), cc.n_verts * 4,
@@ -416,6 +466,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                                          on_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
             }
             CSL_CUDA(cudaStreamSynchronize(s));
+            if (spec.cs) CSL_CUDA(cudaStreamSynchronize(spec.cs));
         });
         dev_chunks.clear();
         finish_stats();

@@ -77,9 +77,17 @@ const char* last_error_cstr();
 void* host_block_alloc(size_t bytes);
 void host_block_free(void* p);
 
-// Host contours in one host block: [layer_loop_off | loop_vert_off | xy | edge_id];
-// csl_contours_free releases the block (its base is layer_loop_off).
-csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_verts, bool want_eid);
+// Takes the largest cached free block out of the cache (nullptr if none).
+void* host_block_take_largest(size_t* bytes);
+
+// Host contours in two host blocks: [layer_loop_off | loop_vert_off] and the
+// vertex block [xy ... | edge_id ...] (edge ids from vertex_block_eid_offset);
+// csl_contours_free releases both (their bases are layer_loop_off and xy).
+// vertex_block: a block the vertices were already copied into (taken from the
+// cache, large enough), or nullptr to allocate one.
+size_t vertex_block_eid_offset(size_t block_bytes, bool want_eid);
+csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_verts, bool want_eid,
+                                void* vertex_block = nullptr);
 
 int64_t read_i64(const int64_t* dev, cudaStream_t s);   // synchronising
 void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s);  // synchronising

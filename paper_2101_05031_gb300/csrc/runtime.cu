@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -173,14 +174,44 @@ void host_block_free(void* p) {
     for (void* q : drop) cudaFreeHost(q);
 }
 
-csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_verts, bool want_eid) {
+void* host_block_take_largest(size_t* bytes) {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    if (g_host_free.empty()) {
+        *bytes = 0;
+        return nullptr;
+    }
+    auto it = std::prev(g_host_free.end());
+    void* p = it->second;
+    *bytes = it->first;
+    g_host_free_bytes -= it->first;
+    g_host_free.erase(it);
+    return p;
+}
+
+size_t vertex_block_eid_offset(size_t block_bytes, bool want_eid) {
+    // 8 bytes of xy and 4 of edge id per vertex: the edge ids start at 2/3
+    return want_eid ? ((block_bytes / 12) * 8 + 15) & ~(size_t)15 : block_bytes;
+}
+
+csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_verts, bool want_eid,
+                                void* vertex_block) {
     auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t b0 = up16((size_t)(n_layers + 1) * 8), b1 = up16((size_t)(n_loops + 1) * 8);
-    const size_t b2 = up16((size_t)n_verts * 8), b3 = want_eid ? up16((size_t)n_verts * 4) : 0;
-    char* base = static_cast<char*>(host_block_alloc(b0 + b1 + b2 + b3));
+    char* offs = static_cast<char*>(host_block_alloc(b0 + b1));
+    char* verts = static_cast<char*>(vertex_block);
+    if (!verts) {
+        try {
+            const size_t vb = (size_t)n_verts * (want_eid ? 12 : 8) + 32;
+            verts = static_cast<char*>(host_block_alloc(vb));
+        } catch (...) {
+            host_block_free(offs);
+            throw;
+        }
+    }
     csl_contours* c = new (std::nothrow) csl_contours();
     if (!c) {
-        host_block_free(base);
+        host_block_free(offs);
+        if (!vertex_block) host_block_free(verts);
         fail(CSL_ERR_OOM, "host allocation failed");
     }
     memset(c, 0, sizeof(*c));
@@ -188,14 +219,70 @@ csl_contours* new_host_contours(int32_t n_layers, int64_t n_loops, int64_t n_ver
     c->on_device = 0;
     c->n_loops = n_loops;
     c->n_verts = n_verts;
-    c->layer_loop_off = reinterpret_cast<int64_t*>(base);
-    c->loop_vert_off = reinterpret_cast<int64_t*>(base + b0);
-    c->xy = reinterpret_cast<float*>(base + b0 + b1);
-    c->edge_id = want_eid ? reinterpret_cast<int32_t*>(base + b0 + b1 + b2) : nullptr;
+    c->layer_loop_off = reinterpret_cast<int64_t*>(offs);
+    c->loop_vert_off = reinterpret_cast<int64_t*>(offs + b0);
+    c->xy = reinterpret_cast<float*>(verts);
+    if (want_eid) {
+        // the edge ids follow the vertices in the same block
+        size_t bytes = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_host_mu);
+            auto it = g_host_pinned.find(verts);
+            bytes = it != g_host_pinned.end() ? it->second : (size_t)n_verts * 12 + 32;
+        }
+        c->edge_id = reinterpret_cast<int32_t*>(verts + vertex_block_eid_offset(bytes, true));
+    }
     return c;
 }
 
+// Small read-backs go through a kernel that stores into page-locked host
+// memory, not through a copy engine: a copy engine may be busy with a large
+// device-to-host transfer of results on another stream, and a small copy
+// queued behind it would stall the host for the duration of that transfer.
+__global__ void k_read_back(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                            int n_words) {
+    for (int i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = src[i];
+}
+
+namespace {
+constexpr size_t kReadBackBytes = 64 << 10;
+// (host pointer, device pointer) of this host thread's buffer, kept for the
+// thread's lifetime; {nullptr, nullptr} when page-locked memory is unavailable.
+std::pair<uint32_t*, uint32_t*> read_back_buffer() {
+    static thread_local uint32_t* host = nullptr;
+    static thread_local uint32_t* dev = nullptr;
+    if (!host) {
+        void* p = nullptr;
+        void* d = nullptr;
+        if (cudaHostAlloc(&p, kReadBackBytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return {nullptr, nullptr};
+        }
+        if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(p);
+            return {nullptr, nullptr};
+        }
+        host = static_cast<uint32_t*>(p);
+        dev = static_cast<uint32_t*>(d);
+    }
+    return {host, dev};
+}
+}  // namespace
+
 void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    std::pair<uint32_t*, uint32_t*> buf{nullptr, nullptr};
+    if (bytes <= kReadBackBytes && bytes % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
+        buf = read_back_buffer();
+    if (buf.first) {
+        k_read_back<<<1, 256, 0, s>>>(static_cast<const uint32_t*>(src), buf.second,
+                                      (int)(bytes / 4));
+        CSL_LAUNCH_CHECK("read back");
+        CSL_CUDA(cudaStreamSynchronize(s));
+        memcpy(dst, buf.first, bytes);
+        return;
+    }
     CSL_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
     CSL_CUDA(cudaStreamSynchronize(s));
 }

@@ -249,6 +249,31 @@ def test_device_contours_match_host(c1):
         assert np.array_equal(a, b)
 
 
+def test_host_results_streamed_into_cached_blocks(c1):
+    """Host results reuse page-locked blocks: a later call copies each chunk's
+    vertices into the largest cached block while it computes the next chunks
+    (or, when that block is too small, copies everything at the end). Every
+    path gives the device result exactly."""
+    cfg, lat = c1
+    kw = dict(z0=cfg["z0"], dz=cfg["dz"], x0=0, y0=0, nx=200, ny=200, pixel=0.1,
+              edge_ids=True, chunk_layers=4, slab=4)
+    ref = lat.slice(n_layers=12, on_device=True, **kw).to_host()
+
+    def same(h):
+        for a, b in zip((h.layer_loop_off, h.loop_vert_off, h.xy, h.edge_id),
+                        (ref.layer_loop_off, ref.loop_vert_off, ref.xy, ref.edge_id)):
+            assert np.array_equal(a, b)
+
+    small = lat.slice(n_layers=2, **kw)   # leaves a small block in the cache
+    del small
+    same(lat.slice(n_layers=12, **kw))   # block too small: copied at the end
+    for _ in range(2):                    # now a block of the right size is cached
+        same(lat.slice(n_layers=12, **kw))
+    kw_noeid = dict(kw, edge_ids=False)
+    h = lat.slice(n_layers=12, **kw_noeid)
+    assert h.edge_id is None and np.array_equal(h.xy, ref.xy)
+
+
 def test_isolated_strut_circle_on_gpu():
     """The cross-section of an isolated long strut is the circle of its radius."""
     cs = _cslice()
