@@ -110,7 +110,8 @@ void csl_lattice_free(csl_lattice* lat);
 #define CSL_SLICE_CONTOURS_ON_DEVICE 1   /* leave the contour arrays in device memory */
 #define CSL_SLICE_EDGE_IDS 2             /* also return the grid-edge id of every vertex */
 #define CSL_SLICE_NO_CONTOURS 4          /* field (and sigma_out) only; no marching squares */
-#define CSL_SLICE_TIME_KERNELS 8         /* time the field kernel with CUDA events (csl_stats) */
+#define CSL_SLICE_TIME_KERNELS 8         /* time each stage with CUDA events (csl_stats); the chunks
+                                            then run one after another on the caller's stream */
 #define CSL_SLICE_COUNT_PAIRS 16         /* count (pixel, layer, edge) pairs with a nonzero term */
 
 typedef struct csl_slice_desc {

@@ -305,12 +305,38 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         };
 
         const int64_t plane = (int64_t)d.nx * d.ny;
-        DevBuf sigma_ws, mask_ws;
+        const int n_chunks = d.n_layers > 0 ? (int)ceil_div(d.n_layers, p.chunk) : 0;
+        // Two chunks in flight (not when timing the stages): chunk k runs on
+        // streams[k % 2] with its own Sigma and mask buffers, so that while the
+        // host waits for a size read back by one chunk's binner or contour
+        // stage, the other chunk's kernels keep the GPU busy.
+        const int n_par = (n_chunks > 1 && !time_kernels) ? 2 : 1;
+        struct Side {
+            cudaStream_t s2 = nullptr;
+            cudaEvent_t fork = nullptr;
+            ~Side() {
+                if (s2) cudaStreamSynchronize(s2);
+                if (fork) cudaEventDestroy(fork);
+                if (s2) cudaStreamDestroy(s2);
+            }
+        } side;
+        cudaStream_t streams[2] = {s, s};
+        if (n_par == 2) {
+            CSL_CUDA(cudaStreamCreateWithFlags(&side.s2, cudaStreamNonBlocking));
+            CSL_CUDA(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+            CSL_CUDA(cudaEventRecord(side.fork, s));   // the second stream follows earlier work on s
+            CSL_CUDA(cudaStreamWaitEvent(side.s2, side.fork, 0));
+            streams[1] = side.s2;
+        }
+        DevBuf sigma_ws[2], mask_ws[2];
         const int chunk_alloc = std::min(p.chunk, std::max(d.n_layers, 1));
-        if (!d.sigma_out && d.n_layers > 0) sigma_ws.alloc((size_t)chunk_alloc * plane * 4, s);
         const int64_t mask_layer = mask_words_per_layer(d.nx, d.ny);
-        if (want_contours && d.n_layers > 0)
-            mask_ws.alloc((size_t)chunk_alloc * mask_layer * 4, s);
+        for (int b = 0; b < n_par; ++b) {
+            if (!d.sigma_out && d.n_layers > 0)
+                sigma_ws[b].alloc((size_t)chunk_alloc * plane * 4, streams[b]);
+            if (want_contours && d.n_layers > 0)
+                mask_ws[b].alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
+        }
 
         std::vector<ChunkContours> dev_chunks;
         // Host output: the vertices of each chunk are copied to the host while
@@ -343,34 +369,20 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             }
         }
         bool spec_all = spec.block != nullptr;   // every chunk's vertices went to the block
-        for (int first = 0; first < d.n_layers; first += p.chunk) {
-            const int n = std::min(p.chunk, d.n_layers - first);
-            ChunkGeom g = chunk_geom(L, d, p, first, n);
-            float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane : sigma_ws.as<float>();
-            {
-                SlabBins bins;
-                timed(st.bin_ms, [&] { bin_chunk(L, g, bins, s); });
-                st.candidate_pairs += bins.n_pairs;
-                uint32_t* mask = want_contours ? mask_ws.as<uint32_t>() : nullptr;
-                if (mask)
-                    CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, s));
-                timed(st.field_ms, [&] {
-                    field_chunk(L, g, bins, (float)L->C, sigma, mask,
-                                count_pairs ? pair_count.as<unsigned long long>() : nullptr, s);
-                });
-                ++st.field_launches;
-            }
-            ++st.chunks;
-            if (!want_contours) continue;
+        auto contour_stage = [&](int k, const ChunkGeom& g) {
+            cudaStream_t ks = streams[k % n_par];
+            const float* sigma = d.sigma_out ? d.sigma_out + (int64_t)g.first_layer * plane
+                                             : sigma_ws[k % n_par].as<float>();
             ChunkContours cc;
             timed(st.contour_ms, [&] {
-                contours_chunk(g, L->C, sigma, mask_ws.as<uint32_t>(), want_eid, cc, s);
+                contours_chunk(g, L->C, sigma, mask_ws[k % n_par].as<uint32_t>(), want_eid, cc,
+                               ks);
             });
             st.crossings += cc.n_verts;
             st.loops += cc.n_loops;
             if (spec_all && spec.copied + cc.n_verts <= spec.cap) {
                 if (cc.n_verts) {
-                    CSL_CUDA(cudaEventRecord(spec.ev, s));
+                    CSL_CUDA(cudaEventRecord(spec.ev, ks));
                     CSL_CUDA(cudaStreamWaitEvent(spec.cs, spec.ev, 0));
                     char* base = static_cast<char*>(spec.block);
                     CSL_CUDA(cudaMemcpyAsync(base + spec.copied * 8, cc.xy.get(), cc.n_verts * 8,
@@ -385,7 +397,41 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 spec_all = false;
             }
             dev_chunks.push_back(std::move(cc));
+        };
+        int prev = -1;
+        ChunkGeom g_prev{};
+        for (int k = 0; k < n_chunks; ++k) {
+            const int first = k * p.chunk;
+            const int n = std::min(p.chunk, d.n_layers - first);
+            ChunkGeom g = chunk_geom(L, d, p, first, n);
+            cudaStream_t ks = streams[k % n_par];
+            float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane
+                                       : sigma_ws[k % n_par].as<float>();
+            {
+                SlabBins bins;
+                timed(st.bin_ms, [&] { bin_chunk(L, g, bins, ks); });
+                st.candidate_pairs += bins.n_pairs;
+                uint32_t* mask = want_contours ? mask_ws[k % n_par].as<uint32_t>() : nullptr;
+                if (mask)
+                    CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, ks));
+                timed(st.field_ms, [&] {
+                    field_chunk(L, g, bins, (float)L->C, sigma, mask,
+                                count_pairs ? pair_count.as<unsigned long long>() : nullptr, ks);
+                });
+                ++st.field_launches;
+            }
+            ++st.chunks;
+            if (n_par == 1) {   // one set of buffers: this chunk's contours now
+                if (want_contours) contour_stage(k, g);
+                continue;
+            }
+            // the previous chunk's contours, while this chunk's field runs
+            if (want_contours && prev >= 0) contour_stage(prev, g_prev);
+            prev = k;
+            g_prev = g;
         }
+        if (want_contours && prev >= 0) contour_stage(prev, g_prev);
+        if (side.s2) CSL_CUDA(cudaStreamSynchronize(side.s2));
         CSL_CUDA(cudaStreamSynchronize(s));
         if (count_pairs) {
             int64_t pc[2];
