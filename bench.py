@@ -425,6 +425,9 @@ def main():
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (peak * clocks["sm_mhz"] / MAX_SM_MHZ)
+    # check of the derived peak: an FFMA microbenchmark of the library on this GPU
+    ffma_tflops, _ = cs.measure_fp32_peak()
+    roof["peak_check_ffma_microbenchmark_tflops"] = ffma_tflops
 
     line = {"metric": METRIC, "value": value, "unit": "pixel-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

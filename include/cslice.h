@@ -126,6 +126,10 @@ typedef struct csl_slice_desc {
     int32_t slab;             /* layers per slab: 0 (auto), 1, 2, 4 or 8               */
     int32_t chunk_layers;     /* layers per streamed chunk: 0 (auto) or a multiple of slab */
     int32_t reserved_;
+    uint32_t* mask_out;       /* optional device uint32[n_layers][ny][ceil(nx/32)]: the binary
+                                 image of each layer (Sec. 4, the DLP mask): bit i % 32 of word
+                                 [k][j][i / 32] is set when pixel (i, j) of layer k is inside
+                                 (Sigma >= C); bits past nx are 0 */
 } csl_slice_desc;
 
 /*
@@ -159,7 +163,8 @@ typedef struct csl_contours {
  * csl_slice_layers -- evaluate the field on every pixel of every layer,
  * threshold it at C and trace the contours.
  *   lat   lattice from csl_lattice_upload
- *   desc  slicing request; desc->sigma_out, when set, receives Sigma
+ *   desc  slicing request; desc->sigma_out, when set, receives Sigma, and
+ *         desc->mask_out, when set, the bit-packed inside mask
  *   out   receives the contours (library-owned; csl_contours_free); may be
  *         NULL with CSL_SLICE_NO_CONTOURS
  * Errors: INVALID_ARG for n_layers < 0, dz <= 0 (when n_layers > 1),
@@ -377,6 +382,16 @@ typedef struct csl_stats {
     int64_t evaluated_terms;  /* terms the field kernel evaluated (CSL_SLICE_COUNT_PAIRS) */
 } csl_stats;
 csl_status csl_last_stats(csl_stats* out);
+
+/*
+ * csl_measure_fp32_peak -- FP32 throughput of the device, measured with a
+ * kernel of independent FFMA chains at full occupancy (best of 5 timed
+ * launches after one warm-up). A measurement helper for the roofline of the
+ * ALU-bound kernels; not part of the method. *tflops receives TFLOP/s (FFMA =
+ * 2 flops); *sm_clock_ghz (may be NULL) the device's nominal maximum SM clock.
+ * Synchronises the stream.
+ */
+csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* stream);
 
 const char* csl_last_error(void);
 const char* csl_version(void);

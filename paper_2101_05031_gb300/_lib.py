@@ -41,7 +41,7 @@ class SliceDesc(ctypes.Structure):
     _fields_ = [("z0", c_f64), ("dz", c_f64), ("n_layers", c_i32), ("nx", c_i32), ("ny", c_i32),
                 ("flags", c_i32), ("x0", c_f64), ("y0", c_f64), ("pixel", c_f64),
                 ("sigma_out", c_vp), ("tile", c_i32), ("slab", c_i32), ("chunk_layers", c_i32),
-                ("reserved_", c_i32)]
+                ("reserved_", c_i32), ("mask_out", c_vp)]
 
 
 class Contours(ctypes.Structure):
@@ -111,6 +111,7 @@ SIGNATURES = [
     ("csl_batch_sigma", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
     ("csl_batch_get_info", c_i32, [c_vp, ctypes.POINTER(BatchInfo)]),
     ("csl_batch_free", None, [c_vp]),
+    ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),
 ]

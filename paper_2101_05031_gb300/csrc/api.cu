@@ -127,6 +127,24 @@ void copy_in(DevBuf& dst, const void* src, size_t bytes, bool on_device, cudaStr
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
 }
 
+// The inside mask without its padding ring: out[(k * ny + j) * wpr + w] holds
+// pixels 32 w .. 32 w + 31 of row j of layer k; in the padded mask, pixel i of
+// row j is bit i + 1 of row j + 1 (the ring bits are 0, so bits past nx are 0).
+__global__ void k_unpad_mask(const uint32_t* __restrict__ pad, int nx, int ny, int n_layers,
+                             int64_t mwr, int64_t mask_wpl, uint32_t* __restrict__ out) {
+    const int64_t wpr = (nx + 31) / 32;
+    const int64_t n = (int64_t)n_layers * ny * wpr;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = t % wpr, row = t / wpr;
+        const int64_t j = row % ny, k = row / ny;
+        const uint32_t* pr = pad + k * mask_wpl + (j + 1) * mwr;
+        const uint32_t lo = pr[w] >> 1;
+        const uint32_t hi = w + 1 < mwr ? pr[w + 1] << 31 : 0u;
+        out[t] = lo | hi;
+    }
+}
+
 __global__ void k_add_i64(int64_t* a, int64_t n, int64_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -334,7 +352,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         for (int b = 0; b < n_par; ++b) {
             if (!d.sigma_out && d.n_layers > 0)
                 sigma_ws[b].alloc((size_t)chunk_alloc * plane * 4, streams[b]);
-            if (want_contours && d.n_layers > 0)
+            if ((want_contours || d.mask_out) && d.n_layers > 0)
                 mask_ws[b].alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
         }
 
@@ -411,7 +429,8 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 SlabBins bins;
                 timed(st.bin_ms, [&] { bin_chunk(L, g, bins, ks); });
                 st.candidate_pairs += bins.n_pairs;
-                uint32_t* mask = want_contours ? mask_ws[k % n_par].as<uint32_t>() : nullptr;
+                uint32_t* mask = (want_contours || d.mask_out) ? mask_ws[k % n_par].as<uint32_t>()
+                                                               : nullptr;
                 if (mask)
                     CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, ks));
                 timed(st.field_ms, [&] {
@@ -419,6 +438,14 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                                 count_pairs ? pair_count.as<unsigned long long>() : nullptr, ks);
                 });
                 ++st.field_launches;
+                if (d.mask_out) {
+                    const int64_t wpr = ceil_div(d.nx, 32);
+                    const int64_t n_out = (int64_t)n * d.ny * wpr;
+                    k_unpad_mask<<<grid_for(n_out, 256), 256, 0, ks>>>(
+                        mask, d.nx, d.ny, n, mask_words_per_row(d.nx), mask_layer,
+                        d.mask_out + (int64_t)first * d.ny * wpr);
+                    CSL_LAUNCH_CHECK("mask out");
+                }
             }
             ++st.chunks;
             if (n_par == 1) {   // one set of buffers: this chunk's contours now

@@ -313,6 +313,7 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
                 J.L = lats[j];
                 J.d = descs[j];
                 J.d.sigma_out = nullptr;
+                J.d.mask_out = nullptr;
                 J.want_eid = (J.d.flags & CSL_SLICE_EDGE_IDS) != 0;
                 min_layers = std::min(min_layers, J.d.n_layers);
                 sigma_floats += (int64_t)J.d.n_layers * J.d.nx * J.d.ny;

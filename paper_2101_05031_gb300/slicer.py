@@ -179,8 +179,10 @@ class Lattice:
             pr = ctypes.c_void_p(t.data_ptr())
         _lib.check(_lib.load().csl_lattice_update(self._h, pn, pr, _stream_ptr(stream)))
 
-    def _desc(self, z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab, chunk_layers):
+    def _desc(self, z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab, chunk_layers,
+              mask_out=None):
         d = _lib.SliceDesc()
+        d.mask_out = ctypes.c_void_p(mask_out.data_ptr()) if mask_out is not None else None
         d.z0, d.dz, d.n_layers = float(z0), float(dz), int(n_layers)
         d.nx, d.ny, d.flags = int(nx), int(ny), int(flags)
         d.x0, d.y0, d.pixel = float(x0), float(y0), float(pixel)
@@ -188,11 +190,13 @@ class Lattice:
         d.tile, d.slab, d.chunk_layers = 0, int(slab), int(chunk_layers)
         return d
 
-    def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None,
+    def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None, mask_out=None,
               contours=True, on_device=False, edge_ids=False, slab=0, chunk_layers=0,
               time_kernels=False, count_pairs=False, stream=None):
         """csl_slice_layers. sigma_out: optional CUDA float32 tensor
-        [n_layers, ny, nx] that receives Sigma. Returns a ContourSet (host),
+        [n_layers, ny, nx] that receives Sigma; mask_out: optional CUDA int32
+        tensor [n_layers, ny, ceil(nx / 32)] that receives the bit-packed inside
+        mask (bit i % 32 of word i / 32: pixel i inside). Returns a ContourSet (host),
         a DeviceContours (on_device=True) or None (contours=False)."""
         if sigma_out is not None:
             if not (sigma_out.is_cuda and sigma_out.dtype == torch.float32
@@ -200,6 +204,12 @@ class Lattice:
                     and sigma_out.numel() >= int(n_layers) * int(ny) * int(nx)):
                 raise ValueError("sigma_out must be a contiguous CUDA float32 tensor "
                                  "of n_layers * ny * nx elements")
+        if mask_out is not None:
+            wpr = (int(nx) + 31) // 32
+            if not (mask_out.is_cuda and mask_out.element_size() == 4 and mask_out.is_contiguous()
+                    and mask_out.numel() >= int(n_layers) * int(ny) * wpr):
+                raise ValueError("mask_out must be a contiguous CUDA tensor of 32-bit words, "
+                                 "n_layers * ny * ceil(nx / 32) of them")
         flags = 0
         if not contours:
             flags |= _lib.SLICE_NO_CONTOURS
@@ -212,7 +222,7 @@ class Lattice:
         if count_pairs:
             flags |= _lib.SLICE_COUNT_PAIRS
         d = self._desc(z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab,
-                       chunk_layers)
+                       chunk_layers, mask_out)
         out = ctypes.POINTER(_lib.Contours)()
         _lib.check(_lib.load().csl_slice_layers(self._h, ctypes.byref(d), _stream_ptr(stream),
                                                 ctypes.byref(out)))
@@ -253,6 +263,15 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_peak(stream=None):
+    """(TFLOP/s of an FFMA microbenchmark at full occupancy, nominal max SM clock in GHz)."""
+    t = ctypes.c_double()
+    g = ctypes.c_double()
+    _lib.check(_lib.load().csl_measure_fp32_peak(ctypes.byref(t), ctypes.byref(g),
+                                                 _stream_ptr(stream)))
+    return t.value, g.value
 
 
 def last_stats() -> _lib.Stats:

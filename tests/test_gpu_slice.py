@@ -274,6 +274,30 @@ def test_host_results_streamed_into_cached_blocks(c1):
     assert h.edge_id is None and np.array_equal(h.xy, ref.xy)
 
 
+@pytest.mark.parametrize("nx,contours,chunk", [(200, False, 0), (70, True, 2)])
+def test_mask_out_is_the_thresholded_field(c1, nx, contours, chunk):
+    """The bit-packed binary image (Sec. 4, the DLP mask) is exactly Sigma >= C
+    of the returned field, bits past nx are 0, and it matches the oracle's
+    classification away from the iso-value."""
+    cfg, lat = c1
+    n, ny = 6, 90
+    wpr = (nx + 31) // 32
+    sig = torch.empty((n, ny, nx), dtype=torch.float32, device="cuda")
+    mk = torch.full((n, ny, wpr), -1, dtype=torch.int32, device="cuda")
+    lat.slice(z0=cfg["z0"], dz=cfg["dz"], n_layers=n, x0=cfg["x0"] + 3.0, y0=cfg["y0"] + 1.0,
+              nx=nx, ny=ny, pixel=cfg["pixel"], sigma_out=sig, mask_out=mk, contours=contours,
+              slab=2, chunk_layers=chunk)
+    torch.cuda.synchronize()
+    words = mk.cpu().numpy().view(np.uint32)
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little").reshape(n, ny, wpr * 32)
+    s = sig.cpu().numpy()
+    assert np.array_equal(bits[:, :, :nx].astype(bool), s >= cfg["C"])
+    assert not bits[:, :, nx:].any()
+    ref = oracle_slice(cfg, n_layers=n, nx=nx, ny=ny, x0=cfg["x0"] + 3.0, y0=cfg["y0"] + 1.0)
+    far = np.abs(ref - cfg["C"]) >= 1e-5 * cfg["C"]
+    assert np.array_equal(bits[:, :, :nx].astype(bool)[far], (ref >= cfg["C"])[far])
+
+
 def test_isolated_strut_circle_on_gpu():
     """The cross-section of an isolated long strut is the circle of its radius."""
     cs = _cslice()
