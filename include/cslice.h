@@ -187,6 +187,37 @@ csl_status csl_contours_copy(const csl_contours* c, int64_t* layer_loop_off, int
                              float* xy, int32_t* edge_id, int32_t dst_on_device, void* stream);
 
 /*
+ * Zigzag infill of the contours (Sec. 6: the interior of each layer is filled
+ * by a zigzag toolpath after its boundary contours). Scan lines
+ * y_m = y0 + m spacing, m in [0, n_lines), the same in every layer (y_m is
+ * computed in double and rounded once to float). A contour edge a -> b crosses
+ * line m when min(a_y, b_y) <= y_m < max(a_y, b_y), decided in float, at
+ * x = a_x + t (b_x - a_x), t = (y_m - a_y) / (b_y - a_y) in float. Along a line
+ * the crossings sorted by x pair up into the inside segments. Each layer's
+ * toolpath visits the lines in increasing m; on even lines its segments run
+ * from low to high x in increasing x, on odd lines from high to low x in
+ * decreasing x (the zigzag).
+ *   contours  device contours (csl_slice_layers with CSL_SLICE_CONTOURS_ON_DEVICE)
+ *   out       layer_seg_off [n_layers + 1] and seg [n_segments][3] = (x_from,
+ *             x_to, y) in toolpath order, in mm (library-owned; csl_hatches_free);
+ *             host page-locked blocks, or device memory with dst_on_device
+ * Errors: INVALID_ARG (host contours, spacing <= 0, non-finite y0, n_lines < 0),
+ * CAPACITY (n_layers * n_lines >= 2^32), CUDA (a line with an odd number of
+ * crossings: contours that are not closed). Synchronises the stream.
+ */
+typedef struct csl_hatches {
+    int32_t n_layers;
+    int32_t on_device;
+    int64_t n_segments;
+    int64_t* layer_seg_off;   /* [n_layers + 1] first segment of each layer */
+    float* seg;               /* [n_segments][3] x_from, x_to, y           */
+} csl_hatches;
+csl_status csl_hatch_layers(const csl_contours* contours, double y0, double spacing,
+                            int32_t n_lines, int32_t dst_on_device, void* stream,
+                            csl_hatches** out);
+void csl_hatches_free(csl_hatches* h);
+
+/*
  * Bins of one slab, for inspection: the edges (as sorted-record positions
  * mapped back to original edge ids, ascending) that the binner assigns to each
  * tile of the slab made of layers [first_layer, first_layer + n_slab_layers).

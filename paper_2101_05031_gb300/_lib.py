@@ -50,6 +50,11 @@ class Contours(ctypes.Structure):
                 ("edge_id", c_vp)]
 
 
+class Hatches(ctypes.Structure):
+    _fields_ = [("n_layers", c_i32), ("on_device", c_i32), ("n_segments", c_i64),
+                ("layer_seg_off", c_vp), ("seg", c_vp)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("candidate_pairs", c_i64), ("crossings", c_i64), ("loops", c_i64),
                 ("chunks", c_i64), ("device_bytes_peak", c_i64), ("kernel_launches", c_i64),
@@ -111,6 +116,9 @@ SIGNATURES = [
     ("csl_batch_sigma", c_i32, [c_vp, c_i32, ctypes.POINTER(c_vp)]),
     ("csl_batch_get_info", c_i32, [c_vp, ctypes.POINTER(BatchInfo)]),
     ("csl_batch_free", None, [c_vp]),
+    ("csl_hatch_layers", c_i32, [ctypes.POINTER(Contours), c_f64, c_f64, c_i32, c_i32, c_vp,
+                                 ctypes.POINTER(ctypes.POINTER(Hatches))]),
+    ("csl_hatches_free", None, [ctypes.POINTER(Hatches)]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),

@@ -85,6 +85,24 @@ class DeviceContours:
             eid.ctypes.data_as(ctypes.c_void_p) if eid is not None else None, 0, _stream_ptr(None)))
         return ContourSet(lo, vo, xy, eid)
 
+    def hatch(self, y0, spacing, n_lines, stream=None):
+        """Zigzag infill (csl_hatch_layers): (layer_seg_off[n_layers + 1],
+        seg[n_segments, 3] = (x_from, x_to, y) in toolpath order), host arrays."""
+        lib = _lib.load()
+        h = ctypes.POINTER(_lib.Hatches)()
+        _lib.check(lib.csl_hatch_layers(self._ptr, float(y0), float(spacing), int(n_lines), 0,
+                                        _stream_ptr(stream), ctypes.byref(h)))
+        try:
+            c = h.contents
+            off = np.ctypeslib.as_array((ctypes.c_int64 * (c.n_layers + 1)).from_address(
+                c.layer_seg_off)).copy()
+            n = c.n_segments
+            seg = (np.ctypeslib.as_array((ctypes.c_float * (3 * n)).from_address(c.seg)).copy()
+                   .reshape(n, 3) if n else np.zeros((0, 3), np.float32))
+        finally:
+            lib.csl_hatches_free(h)
+        return off, seg
+
     def free(self):
         if self._ptr is not None:
             _lib.load().csl_contours_free(self._ptr)

@@ -42,7 +42,7 @@ def test_structs_match_header_layout(tmp_path):
     mirrors = {"csl_params": _lib.Params, "csl_lattice_info": _lib.LatticeInfo,
                "csl_slice_desc": _lib.SliceDesc, "csl_contours": _lib.Contours,
                "csl_stats": _lib.Stats, "csl_batch_opts": _lib.BatchOpts,
-               "csl_batch_info": _lib.BatchInfo}
+               "csl_batch_info": _lib.BatchInfo, "csl_hatches": _lib.Hatches}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
