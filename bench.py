@@ -281,6 +281,32 @@ def run_batch(steps, warmup):
     return out
 
 
+def run_hatch(steps, warmup):
+    """Zigzag infill of the 10M-strut graded lattice's contours (500 layers of
+    2000^2 px; scan lines every 0.1 mm): contours left on the device, then
+    csl_hatch_layers with the segments copied to the host."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    cfg = workload("graded-10M")
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    dev = lat.slice(**slice_kwargs(cfg, 0, 1), on_device=True)
+    n_lines = int(round(cfg["ny"] * cfg["pixel"] / 0.1))
+    y0 = cfg["y0"] + 0.05
+    out = {}
+
+    def step():
+        off, seg = dev.hatch(y0, 0.1, n_lines)
+        out["segments"] = int(seg.shape[0])
+
+    ms = _event_ms(step, steps, warmup, torch.cuda.current_stream())
+    return {"workload": cfg["name"] + ", scan lines every 0.1 mm", "layers": cfg["n_layers"],
+            "contour_vertices": int(dev.n_verts), "segments": out["segments"],
+            "ms_per_step": ms, "segments_per_s": out["segments"] / (ms / 1e3),
+            "vertices_per_s": dev.n_verts / (ms / 1e3),
+            "d2h_bytes_per_step": out["segments"] * 12 + (cfg["n_layers"] + 1) * 8}
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args, cfg, rank, world):
@@ -320,13 +346,13 @@ def main():
                     help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
-    ap.add_argument("--only", choices=["10M", "vf", "batched"],
+    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch"],
                     help="run only one of the extra lines and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
-        fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch}[args.only]
+        fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch, "hatch": run_hatch}[args.only]
         print(json.dumps(fn(args.steps, args.warmup)), flush=True)
         return
 
@@ -483,6 +509,7 @@ def main():
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)
         line["batched_64"] = run_batch(args.steps, args.warmup)
+        line["zigzag_infill_10M"] = run_hatch(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:

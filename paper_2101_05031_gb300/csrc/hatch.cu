@@ -26,16 +26,20 @@
 namespace csl {
 namespace {
 
-__device__ __forceinline__ float line_y(double y0, double sp, int m) {
-    return (float)(y0 + (double)m * sp);
+// The scan lines' y, computed once in double and rounded to float.
+__global__ void k_line_table(double y0, double sp, int n, float* __restrict__ ys) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) ys[m] = (float)(y0 + (double)m * sp);
 }
 
-// first m in [0, n] with line_y(m) >= v  (the lines are non-decreasing in m)
-__device__ int first_line_at_or_above(double y0, double sp, int n, float v) {
-    double e = ceil(((double)v - y0) / sp);
-    int m = e < 0.0 ? 0 : (e > (double)n ? n : (int)e);
-    while (m > 0 && line_y(y0, sp, m - 1) >= v) --m;
-    while (m < n && line_y(y0, sp, m) < v) ++m;
+// first m in [0, n] with ys[m] >= v (the table is non-decreasing): a float
+// estimate, then exact comparisons against the table
+__device__ __forceinline__ int first_line_at_or_above(const float* __restrict__ ys, float y0f,
+                                                      float inv_sp, int n, float v) {
+    const float e = ceilf((v - y0f) * inv_sp);
+    int m = e < 0.0f ? 0 : (e > (float)n ? n : (int)e);
+    while (m > 0 && ys[m - 1] >= v) --m;
+    while (m < n && ys[m] < v) ++m;
     return m;
 }
 
@@ -57,7 +61,8 @@ __global__ void k_incl(const uint32_t* __restrict__ flag, uint32_t* __restrict__
 }
 
 struct HatchConst {
-    double y0, sp;
+    const float* ys;   // the lines' y (k_line_table)
+    float y0f, inv_sp;
     int32_t n_lines;
     int64_t n_verts;
 };
@@ -80,8 +85,8 @@ __global__ void k_count(const float2* __restrict__ xy, const int64_t* __restrict
         const float lo = fminf(ya, yb), hi = fmaxf(ya, yb);
         uint32_t k = 0;
         if (lo < hi) {
-            const int m0 = first_line_at_or_above(c.y0, c.sp, c.n_lines, lo);
-            const int m1 = first_line_at_or_above(c.y0, c.sp, c.n_lines, hi);
+            const int m0 = first_line_at_or_above(c.ys, c.y0f, c.inv_sp, c.n_lines, lo);
+            const int m1 = first_line_at_or_above(c.ys, c.y0f, c.inv_sp, c.n_lines, hi);
             k = (uint32_t)(m1 - m0);
         }
         cnt[v] = k;
@@ -100,12 +105,12 @@ __global__ void k_emit_crossings(const float2* __restrict__ xy, const int64_t* _
         const float2 a = xy[v], b = xy[w];
         const float lo = fminf(a.y, b.y), hi = fmaxf(a.y, b.y);
         if (!(lo < hi)) continue;
-        const int m0 = first_line_at_or_above(c.y0, c.sp, c.n_lines, lo);
-        const int m1 = first_line_at_or_above(c.y0, c.sp, c.n_lines, hi);
+        const int m0 = first_line_at_or_above(c.ys, c.y0f, c.inv_sp, c.n_lines, lo);
+        const int m1 = first_line_at_or_above(c.ys, c.y0f, c.inv_sp, c.n_lines, hi);
         const uint32_t base = layer_of[loop_of[v]] * (uint32_t)c.n_lines;
         int64_t p = pos[v];
         for (int m = m0; m < m1; ++m, ++p) {
-            const float ym = line_y(c.y0, c.sp, m);
+            const float ym = c.ys[m];
             const float t = __fdiv_rn(ym - a.y, b.y - a.y);
             key[p] = base + (uint32_t)m;
             xs[p] = fmaf(t, b.x - a.x, a.x);
@@ -167,7 +172,7 @@ __global__ void k_zigzag(const uint32_t* __restrict__ seg_key, const float2* __r
         const int64_t o = odd ? (int64_t)run_lo[k] + run_hi[k] - 1 - s : s;
         out[3 * o] = odd ? x.y : x.x;
         out[3 * o + 1] = odd ? x.x : x.y;
-        out[3 * o + 2] = line_y(c.y0, c.sp, m);
+        out[3 * o + 2] = c.ys[m];
     }
 }
 
@@ -215,7 +220,13 @@ csl_status csl_hatch_layers(const csl_contours* ct, double y0, double spacing, i
         if (n_verts >= 0xffffffffLL || n_loops >= 0xffffffffLL)
             fail(CSL_ERR_CAPACITY, "too many vertices");
         cudaStream_t s = (cudaStream_t)stream;
-        HatchConst c{y0, spacing, n_lines, n_verts};
+        DevBuf ys_d((size_t)(n_lines > 0 ? n_lines : 1) * 4, s);
+        if (n_lines > 0) {
+            k_line_table<<<(unsigned)ceil_div(n_lines, 256), 256, 0, s>>>(y0, spacing, n_lines,
+                                                                         ys_d.as<float>());
+            CSL_LAUNCH_CHECK("hatch lines");
+        }
+        HatchConst c{ys_d.as<float>(), (float)y0, (float)(1.0 / spacing), n_lines, n_verts};
         const float2* xy = reinterpret_cast<const float2*>(ct->xy);
 
         int64_t n_rec = 0;
