@@ -132,3 +132,63 @@ def test_volume_fraction_1M_sampled_cells():
     gn = gn.cpu().numpy().astype(np.float64)[used]
     reln = np.linalg.norm(gn - ref_n) / np.linalg.norm(ref_n)
     assert reln <= 1e-4, reln
+
+
+def test_batched_64_lattices_windows():
+    """The full 64-lattice batch (autotuned graph, as the benchmark runs it):
+    sampled windows of four jobs against the oracle, and each job's loops
+    inside its windows."""
+    import paper_2101_05031_gb300 as cs
+    cfg = synth.config(4)
+    jobs = []
+    for jb in cfg["jobs"]:
+        lat = cs.Lattice(jb["nodes"], jb["edges"], jb["radius"], R=jb["R"], C=jb["C"])
+        jobs.append((lat, dict(z0=jb["z0"], dz=jb["dz"], n_layers=jb["n_layers"], x0=jb["x0"],
+                               y0=jb["y0"], nx=jb["nx"], ny=jb["ny"], pixel=jb["pixel"],
+                               edge_ids=True)))
+    b = cs.Batch(jobs, autotune=True)
+    b.run()
+    r = np.random.default_rng(34)
+    matched = 0
+    sizes = np.array([jb["edges"].shape[0] for jb in cfg["jobs"]])
+    # the largest job, the smallest, and two in between
+    order = np.argsort(sizes)
+    for j in (int(order[-1]), int(order[0]), int(order[len(order) // 2]), int(order[10])):
+        jb = cfg["jobs"][j]
+        sig = b.sigma(j)
+        cont = b.contours(j)
+        nx, ny, px = jb["nx"], jb["ny"], jb["pixel"]
+        W = nx + 2
+        for _ in range(2):
+            k = int(r.integers(0, jb["n_layers"]))
+            win = min(200, nx - 2, ny - 2)
+            i0 = int(r.integers(0, nx - win + 1))
+            j0 = int(r.integers(0, ny - win + 1))
+            wx0, wy0 = jb["x0"] + i0 * px, jb["y0"] + j0 * px
+            z = jb["z0"] + k * jb["dz"]
+            sn, se, sr, _ = _edges_near(jb, wx0, wy0, win * px, z, z)
+            ref = oracle.slice_sigma(sn, se, sr, R=jb["R"], C=jb["C"], z0=z, dz=1.0, n_layers=1,
+                                     x0=wx0, y0=wy0, nx=win, ny=win, pixel=px)[0]
+            got = sig[k, j0:j0 + win, i0:i0 + win].cpu().numpy()
+            helpers.assert_field(got, ref, jb["C"])
+            off, eid, xy = oracle.marching_squares(ref, x0=wx0, y0=wy0, pixel=px, C=jb["C"])
+            band = helpers.band_cells(ref, jb["C"])
+            gpu = {int(e[0]): (e, p) for e, p in cont.layer(k)}
+            for li in range(len(off) - 1):
+                le, lxy = eid[off[li]:off[li + 1]], xy[off[li]:off[li + 1]]
+                s_ = le // 2
+                I, J = s_ % (win + 2), s_ // (win + 2)
+                if (I <= 1).any() or (J <= 1).any() or (I >= win).any() or (J >= win).any():
+                    continue
+                cells = helpers._edge_cells(le, win)
+                if band[cells[:, 1], cells[:, 0]].any():
+                    continue
+                glob = 2 * ((J + j0) * W + (I + i0)) + (le % 2)
+                assert int(glob[0]) in gpu, "loop missing on the GPU"
+                ge, gxy = gpu[int(glob[0])]
+                assert np.array_equal(ge, glob)
+                d = np.max(np.hypot(gxy[:, 0] - lxy[:, 0], gxy[:, 1] - lxy[:, 1])) / px
+                assert d <= helpers.VERTEX_TOL_PX
+                matched += 1
+    assert matched >= 8
+    b.close()
