@@ -134,17 +134,6 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
     const uint32_t e0 = D.ew[wb], e1 = D.ew[wb + 1], p0 = D.prefix[wb], p1 = D.prefix[wb + 1];
     const uint32_t e2 = last ? 0u : D.ew[wb + 2], p2 = last ? 0u : D.prefix[wb + 2];
     const uint32_t u0 = D.ew[wu], u1 = D.ew[wu + 1], q0 = D.prefix[wu], q1 = D.prefix[wu + 1];
-    // crossing on edge (32 k + si, J, b), si in [0, 32]; and (32 k + si, J + 1, 0)
-    auto id_row = [&](int si, int bb) -> uint32_t {
-        const int wsel = si >> 4, bit = 2 * (si & 15) + bb;
-        const uint32_t e = wsel == 0 ? e0 : (wsel == 1 ? e1 : e2);
-        const uint32_t p = wsel == 0 ? p0 : (wsel == 1 ? p1 : p2);
-        return p + __popc(e & ((1u << bit) - 1u));
-    };
-    auto id_up = [&](int si) -> uint32_t {
-        const uint32_t e = si < 16 ? u0 : u1, p = si < 16 ? q0 : q1;
-        return p + __popc(e & ((1u << (2 * (si & 15))) - 1u));
-    };
     while (active) {
         const int b = __ffs(active) - 1;
         active &= active - 1u;
@@ -153,13 +142,30 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         const uint32_t in_c0 = (in0 >> b) & 1u, in_c3 = (up >> b) & 1u;
         const uint32_t in_c1 = b < 31 ? (in0 >> (b + 1)) & 1u : in1 & 1u;
         const uint32_t in_c2 = b < 31 ? (up >> (b + 1)) & 1u : up1 & 1u;
-        const float v0 = value_at(sg, c, I, J);
-        const float v1 = value_at(sg, c, I + 1, J);
-        const float v3 = value_at(sg, c, I, J + 1);
+        // ids of the crossings on the cell's sides (valid where the side crosses):
+        // in the interleaved edge words, sample si's h edge is bit 2 (si % 16) and
+        // its v edge the next bit; the right side is sample b + 1's v edge, the
+        // top side the h edge of sample b in the row above
+        const int bit = 2 * (b & 15);
+        const uint32_t eb_w = b < 16 ? e0 : e1, pb_w = b < 16 ? p0 : p1;
+        const uint32_t id_bottom = pb_w + __popc(eb_w & ((1u << bit) - 1u));
+        const uint32_t id_left = id_bottom + ((eb_w >> bit) & 1u);
+        const int sr = b + 1, bit_r = 2 * (sr & 15) + 1;
+        const uint32_t er_w = sr < 16 ? e0 : (sr < 32 ? e1 : e2);
+        const uint32_t pr_w = sr < 16 ? p0 : (sr < 32 ? p1 : p2);
+        const uint32_t id_right = pr_w + __popc(er_w & ((1u << bit_r) - 1u));
+        const uint32_t id_top = (b < 16 ? q0 : q1) + __popc((b < 16 ? u0 : u1) & ((1u << bit) - 1u));
+        auto side = [&](int sd) -> uint32_t {   // sides: 0 bottom, 1 right, 2 top, 3 left
+            return sd == 0 ? id_bottom : (sd == 1 ? id_right : (sd == 2 ? id_top : id_left));
+        };
+        const bool h_own = (hb >> b) & 1u, v_own = (vb >> b) & 1u;
+        // Sigma only where a vertex is placed (or a saddle is decided)
+        const float v0 = (h_own || v_own) ? value_at(sg, c, I, J) : 0.0f;
         const int64_t eb = 2 * ((int64_t)J * c.W + I);
-        if ((hb >> b) & 1u) {   // vertex on the bottom edge (I, J) -> (I+1, J)
-            const uint32_t id = id_row(b, 0);
+        if (h_own) {   // vertex on the bottom edge (I, J) -> (I+1, J)
+            const uint32_t id = id_bottom;
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
+            const float v1 = value_at(sg, c, I + 1, J);
             const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
             const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
             const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
@@ -167,9 +173,10 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
                 make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
             rec[id].eid = (int32_t)eb;
         }
-        if ((vb >> b) & 1u) {   // vertex on the left edge (I, J) -> (I, J+1)
-            const uint32_t id = id_row(b, 1);
+        if (v_own) {   // vertex on the left edge (I, J) -> (I, J+1)
+            const uint32_t id = id_left;
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
+            const float v3 = value_at(sg, c, I, J + 1);
             const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
             const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
             const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
@@ -182,17 +189,14 @@ __global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restri
         const uint32_t nxt = ((cs >> 1) | (cs << 3)) & 0xfu;
         const uint32_t enter = cs & ~nxt & 0xfu;   // inside -> outside
         const uint32_t leave = ~cs & nxt & 0xfu;   // outside -> inside
-        auto side = [&](int sd) -> uint32_t {   // sides: 0 bottom, 1 right, 2 top, 3 left
-            return sd == 0 ? id_row(b, 0)
-                           : (sd == 1 ? id_row(b + 1, 1) : (sd == 2 ? id_up(b) : id_row(b, 1)));
-        };
         if (__popc(enter) == 1) {
             const uint32_t a = side(__ffs(enter) - 1);
             if (a < n_cap) rec[a].succ = side(__ffs(leave) - 1);
             else atomicOr(flag, 1u);
         } else if (enter) {
-            const float v2 = value_at(sg, c, I + 1, J + 1);
-            const bool joined = 0.25f * (v0 + v1 + v2 + v3) >= c.C;
+            const float w0 = value_at(sg, c, I, J), w1 = value_at(sg, c, I + 1, J);
+            const float w2 = value_at(sg, c, I + 1, J + 1), w3 = value_at(sg, c, I, J + 1);
+            const bool joined = 0.25f * (w0 + w1 + w2 + w3) >= c.C;
             const int k0 = __ffs(enter) - 1, k1 = 31 - __clz(enter);
             const uint32_t a0 = side(k0), a1 = side(k1);
             if (a0 < n_cap && a1 < n_cap) {
