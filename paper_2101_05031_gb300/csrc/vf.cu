@@ -133,7 +133,7 @@ struct GradConst {
 // staged edge. partial[entry] = {sum alpha R^4 I, sum alpha w dI/da (3),
 // sum alpha w dI/db (3), 0}.
 template <int S>
-__global__ void __launch_bounds__(kVfThreads, 4)
+__global__ void __launch_bounds__(kVfThreads, 6)
 k_vf_grad(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
           const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, GradConst c,
           const float* __restrict__ g_cells, float4* __restrict__ partial) {
