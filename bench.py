@@ -31,6 +31,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixel-evals/s and layers/s at 10M and 100M struts; backward/forward time ratio"
 F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the field kernel
+# FP32 instructions the field kernel executes per cycle as a fraction of the
+# FP32 peak (every evaluated lane), from an ncu capture of one launch
+NCU_FIELD_EXECUTED_FRAC = 8473.0 / (152 * 128 * 2)
+HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
+# algorithmic bytes of the HBM-bound stages
+BIN_BYTES_PER_WINDOW_RECORD = 24   # xy box (16) + z range (8) of a record read per slab window
+BIN_BYTES_PER_ENTRY = 8            # (key, record) of a bin entry written
+MS_BYTES_PER_PIXEL = 0.125         # inside-mask bit of a pixel read
+MS_BYTES_PER_CROSSING = 16         # two Sigma values read, the vertex (x, y) written
+MS_BYTES_PER_LOOP = 8              # the loop's vertex offset written
 # DRAM bytes (read + write) per pixel-layer of one field-kernel launch, from an
 # ncu capture of the current field kernel on the 12.96M-strut graded lattice
 # (1.12 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
@@ -454,6 +464,30 @@ def main():
     # check of the derived peak: an FFMA microbenchmark of the library on this GPU
     ffma_tflops, _ = cs.measure_fp32_peak()
     roof["peak_check_ffma_microbenchmark_tflops"] = ffma_tflops
+    roof["executed_frac_ncu"] = NCU_FIELD_EXECUTED_FRAC
+    roof["executed_basis"] = ("ncu FFMA + FADD + FMUL thread instructions per cycle of one "
+                              "field launch on the 12.96M-strut graded lattice, every evaluated "
+                              "lane included (profiles/k_field_graded-10M.txt)")
+    # the HBM-bound stages, against the measured copy bandwidth: algorithmic
+    # bytes (the minimum each stage must move) over its event-timed duration
+    px_layers = cfg["nx"] * cfg["ny"] * cfg["n_layers"]
+    bin_bytes = st.window_records * BIN_BYTES_PER_WINDOW_RECORD + \
+        st.candidate_pairs * BIN_BYTES_PER_ENTRY
+    ms_bytes = px_layers * MS_BYTES_PER_PIXEL + st.crossings * MS_BYTES_PER_CROSSING + \
+        st.loops * MS_BYTES_PER_LOOP
+    secondary = {}
+    for name, nbytes, t_ms in (("binner", bin_bytes, bin_ms), ("contours", ms_bytes, contour_ms)):
+        gbs = nbytes / (t_ms / 1e3) / 1e9 if t_ms > 0 else 0.0
+        secondary[name] = {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS, "unit": "GB/s",
+                           "frac": gbs / HBM_GBS, "algorithmic_bytes_per_step": nbytes,
+                           "ms_per_step": t_ms}
+    secondary["binner"]["basis"] = (f"{BIN_BYTES_PER_WINDOW_RECORD} B per record of a slab's "
+                                    f"z window + {BIN_BYTES_PER_ENTRY} B per (slab, tile, "
+                                    "edge) entry written")
+    secondary["contours"]["basis"] = (f"{MS_BYTES_PER_PIXEL} B per pixel-layer (inside "
+                                      f"mask) + {MS_BYTES_PER_CROSSING} B per vertex (two "
+                                      f"Sigma values read, x y written) + {MS_BYTES_PER_LOOP} B "
+                                      "per loop offset")
 
     line = {"metric": METRIC, "value": value, "unit": "pixel-evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -464,6 +498,7 @@ def main():
                        "l2": "inputs larger than L2 (32-byte records x struts)",
                        "parallelism": f"{world} GPU(s), layers offset per rank"},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+            "roofline_hbm_stages": secondary,
             "contours_per_step": {"loops": n_loops, "vertices": n_verts},
             "phase_ms_per_step": {"bin": bin_ms, "field": field_ms, "contours": contour_ms,
                                   "gather": output_ms, "sum": staged_ms,

@@ -411,6 +411,7 @@ typedef struct csl_stats {
     double contour_ms;        /* ... of marching squares and loop assembly            */
     double output_ms;         /* ... of gathering the chunks into the result          */
     int64_t evaluated_terms;  /* terms the field kernel evaluated (CSL_SLICE_COUNT_PAIRS) */
+    int64_t window_records;   /* records the binner examined (the slabs' z windows, summed) */
 } csl_stats;
 csl_status csl_last_stats(csl_stats* out);
 

@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
                 ("chunks", c_i64), ("device_bytes_peak", c_i64), ("kernel_launches", c_i64),
                 ("field_launches", c_i64), ("field_ms", c_f64), ("contributing_pairs", c_i64),
                 ("bin_ms", c_f64), ("contour_ms", c_f64), ("output_ms", c_f64),
-                ("evaluated_terms", c_i64)]
+                ("evaluated_terms", c_i64), ("window_records", c_i64)]
 
 
 class CellsDesc(ctypes.Structure):

@@ -429,6 +429,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 SlabBins bins;
                 timed(st.bin_ms, [&] { bin_chunk(L, g, bins, ks); });
                 st.candidate_pairs += bins.n_pairs;
+                st.window_records += bins.n_cand;
                 uint32_t* mask = (want_contours || d.mask_out) ? mask_ws[k % n_par].as<uint32_t>()
                                                                : nullptr;
                 if (mask)

@@ -232,6 +232,7 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
         }
     }
 
+    out.n_cand = n_cand;
     out.tile_start.ensure((size_t)n_keys * 4, s);
     out.tile_end.ensure((size_t)n_keys * 4, s);
     CSL_CUDA(cudaMemsetAsync(out.tile_start.get(), 0, (size_t)n_keys * 4, s));

@@ -28,6 +28,7 @@ struct SlabBins {
     DevBuf keys, vals;          // sorted pairs: key = slab * n_tiles + tile, val = record position
     DevBuf tile_start, tile_end;// uint32 [n_slabs * n_tiles]
     int64_t n_pairs = 0;
+    int64_t n_cand = 0;         // records examined: the slabs' z windows, summed
 };
 
 // Sizes that a chunk's pipeline discovers on the host (each needs a read
