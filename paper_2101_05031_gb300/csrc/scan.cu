@@ -1,6 +1,6 @@
 // Device-wide exclusive prefix sums (reduce, scan the block sums, scan again
-// with the block's offset). Blocks of 256 threads take 8 consecutive segments
-// of 256 elements each; every global load and store is coalesced.
+// with the block's offset). A block of 256 threads takes a tile of 2048
+// elements, 8 consecutive ones per thread, moved as 16-byte vectors.
 #include "common.cuh"
 
 namespace csl {
@@ -20,18 +20,69 @@ __device__ __forceinline__ U warp_inclusive(U v, int lane) {
     return v;
 }
 
+// Thread t of a block owns the kItems consecutive elements base + t * kItems ...
+// of the block's tile: loaded as 16-byte vectors when the tile is whole and
+// aligned (a warp then reads 32 consecutive 16-byte pieces per vector load).
+template <class T>
+__device__ __forceinline__ void load_items(const T* __restrict__ in, int64_t n, int64_t first,
+                                           T (&v)[kItems]) {
+    static_assert((kItems * sizeof(T)) % 16 == 0, "whole vectors per thread");
+    if (first + kItems <= n && (reinterpret_cast<uintptr_t>(in + first) & 15) == 0) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + first);
+#pragma unroll
+        for (int q = 0; q < (int)(kItems * sizeof(T) / 16); ++q)
+            reinterpret_cast<uint4*>(v)[q] = __ldg(p + q);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) v[i] = first + i < n ? in[first + i] : (T)0;
+    }
+}
+
+template <class U>
+__device__ __forceinline__ void store_items(U* __restrict__ out, int64_t n, int64_t first,
+                                            const U (&v)[kItems]) {
+    if (first + kItems <= n && (reinterpret_cast<uintptr_t>(out + first) & 15) == 0 &&
+        (kItems * sizeof(U)) % 16 == 0) {
+        uint4* p = reinterpret_cast<uint4*>(out + first);
+#pragma unroll
+        for (int q = 0; q < (int)(kItems * sizeof(U) / 16); ++q)
+            p[q] = reinterpret_cast<const uint4*>(v)[q];
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+            if (first + i < n) out[first + i] = v[i];
+    }
+}
+
+// Exclusive block-wide scan of one value per thread; the block total goes to
+// *total_s (shared), visible to every thread on return.
+template <class U>
+__device__ __forceinline__ U block_exclusive(U x, U* total_s) {
+    __shared__ U warp_tot[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const U inc = warp_inclusive(x, lane);
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const U t = lane < kThreads / 32 ? warp_tot[lane] : (U)0;
+        const U ti = warp_inclusive(t, lane);
+        if (lane < kThreads / 32) warp_tot[lane] = ti - t;   // exclusive warp offsets
+        if (lane == kThreads / 32 - 1) *total_s = ti;
+    }
+    __syncthreads();
+    return warp_tot[warp] + inc - x;
+}
+
 template <class T, class U>
 __global__ void __launch_bounds__(kThreads) k_block_sums(const T* __restrict__ in, int64_t n,
                                                          U* __restrict__ sums) {
     __shared__ U warp_tot[kThreads / 32];
-    int64_t base = (int64_t)blockIdx.x * kTile;
+    T v[kItems];
+    load_items(in, n, (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems, v);
     U acc = 0;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        int64_t idx = base + (int64_t)i * kThreads + threadIdx.x;
-        if (idx < n) acc += (U)in[idx];
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < kItems; ++i) acc += (U)v[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) warp_tot[warp] = acc;
@@ -48,31 +99,24 @@ template <class T, class U>
 __global__ void __launch_bounds__(kThreads) k_block_scan(const T* in, U* out, int64_t n,
                                                          const U* __restrict__ offsets,
                                                          U* total) {
-    __shared__ U warp_tot[kThreads / 32];
-    __shared__ U carry_s;
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t base = (int64_t)blockIdx.x * kTile;
-    U carry = offsets ? offsets[blockIdx.x] : (U)0;
+    __shared__ U block_total;
+    const int64_t first = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    T v[kItems];
+    load_items(in, n, first, v);
+    U mine = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) mine += (U)v[i];
+    const U off = block_exclusive<U>(mine, &block_total);
+    const U carry = offsets ? offsets[blockIdx.x] : (U)0;
+    U r[kItems];
+    U run = carry + off;
+#pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        int64_t idx = base + (int64_t)i * kThreads + threadIdx.x;
-        U v = idx < n ? (U)in[idx] : (U)0;
-        U inc = warp_inclusive(v, lane);
-        if (lane == 31) warp_tot[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            U t = lane < kThreads / 32 ? warp_tot[lane] : (U)0;
-            U ti = warp_inclusive(t, lane);
-            if (lane < kThreads / 32) warp_tot[lane] = ti - t;      // exclusive warp offsets
-            if (lane == kThreads / 32 - 1) carry_s = ti;             // tile segment total
-        }
-        __syncthreads();
-        U res = carry + warp_tot[warp] + inc - v;
-        U seg = carry_s;
-        __syncthreads();   // warp_tot / carry_s are rewritten next iteration
-        if (idx < n) out[idx] = res;
-        carry += seg;
+        r[i] = run;
+        run += (U)v[i];
     }
-    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = carry;
+    store_items(out, n, first, r);
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = carry + block_total;
 }
 
 template <class T, class U>
