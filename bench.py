@@ -540,6 +540,16 @@ def main():
                        "ms_per_step": e2e_ms}
 
     if world == 1 and not args.no_extra:
+        # self-support metrics (Eq. 11-14) of the same lattice, printing along z
+        res = {}
+
+        def support_step():
+            res["v"] = lat.support_metrics((0.0, 0.0, 1.0), math.pi / 4)
+
+        sms = _event_ms(support_step, args.steps, args.warmup, stream)
+        line["support_metrics"] = {"workload": cfg["name"], "gamma": res["v"][0],
+                                   "psi_percent": res["v"][1], "ms": sms,
+                                   "struts_per_s": cfg["edges"].shape[0] / (sms / 1e3)}
         del lat
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)

@@ -416,6 +416,21 @@ typedef struct csl_stats {
 csl_status csl_last_stats(csl_stats* out);
 
 /*
+ * csl_support_metrics -- self-support metrics of the lattice (Sec. 5.3):
+ * theta_j = arccos |u_j . t_P| per edge (Eq. 11); an edge with theta_j <= alpha
+ * is fully self-supported; g(theta) = sum_{i<6} a_i theta^i for theta > alpha,
+ * else 0 (Eq. 12); *gamma = sum over unsupported edges of r_j L_j g(theta_j) /
+ * sum over all edges of r_j L_j (Eq. 13); *psi = 100 x sum over supported edges
+ * of L_j / sum of L_j (Eq. 14). r_j is the edge's radius value as uploaded.
+ *   t_p     host double[3], the printing direction (any nonzero length)
+ *   alpha   the self-supporting angle in [0, pi/2] (the paper uses pi/4)
+ *   coeffs  host double[6] a_0..a_5, or NULL for the paper's quintic for pi/4
+ * Sums in double in a fixed order (deterministic). Synchronises the stream.
+ */
+csl_status csl_support_metrics(const csl_lattice* lat, const double* t_p, double alpha,
+                               const double* coeffs, double* gamma, double* psi, void* stream);
+
+/*
  * csl_measure_fp32_peak -- FP32 throughput of the device, measured with a
  * kernel of independent FFMA chains at full occupancy (best of 5 timed
  * launches after one warm-up). A measurement helper for the roofline of the

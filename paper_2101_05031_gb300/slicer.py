@@ -271,6 +271,16 @@ class Lattice:
                                            ctypes.byref(n), _stream_ptr(stream)))
         return off, ids[:n.value]
 
+    def support_metrics(self, t_p=(0.0, 0.0, 1.0), alpha=np.pi / 4, coeffs=None, stream=None):
+        """(Gamma, Psi) of Eq. 13-14 for printing direction t_p and angle alpha
+        (csl_support_metrics); coeffs: a_0..a_5 of g(theta), None for the paper's."""
+        t = (ctypes.c_double * 3)(*[float(v) for v in t_p])
+        a = (ctypes.c_double * 6)(*[float(v) for v in coeffs]) if coeffs is not None else None
+        g, p = ctypes.c_double(), ctypes.c_double()
+        _lib.check(_lib.load().csl_support_metrics(self._h, t, float(alpha), a, ctypes.byref(g),
+                                                   ctypes.byref(p), _stream_ptr(stream)))
+        return g.value, p.value
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().csl_lattice_free(self._h)
