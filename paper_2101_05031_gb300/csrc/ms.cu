@@ -107,7 +107,7 @@ __device__ __forceinline__ float value_at(const float* __restrict__ sg, const Ms
 }
 
 // grid: x over (row J <= ny, mask word k), y = layer
-__global__ void k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
+__global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
                        MsConst c, Dense D, Xing* __restrict__ rec, uint32_t n_cap,
                        uint32_t* flag) {
     const int layer = blockIdx.y;
