@@ -81,6 +81,16 @@ ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SliceP
     return g;
 }
 
+void check_lattice_status(const csl_lattice* L, cudaStream_t s) {
+    uint32_t st = 0;
+    read_to_host(&st, L->status.get(), 4, s);
+    if (st) {
+        CSL_CUDA(cudaMemsetAsync(L->status.get(), 0, 4, s));
+        CSL_CUDA(cudaStreamSynchronize(s));
+        fail(CSL_ERR_TIMEOUT, "a device wait (bulk copy of the field kernel) gave up");
+    }
+}
+
 void validate_desc(const csl_slice_desc* d) {
     require_arg(d != nullptr, "desc is NULL");
     require_arg(d->n_layers >= 0, "n_layers < 0");
@@ -194,6 +204,8 @@ csl_status csl_lattice_upload(const float* nodes_xyz, int64_t n_nodes, const int
             copy_in(L->nodes, nodes_xyz, (size_t)n_nodes * 12, dev, s);
             copy_in(L->edges, edges_ij, (size_t)n_edges * 8, dev, s);
             copy_in(L->radius, radius, (size_t)n_edges * 4, dev, s);
+            L->status.alloc_persistent(4);
+            CSL_CUDA(cudaMemsetAsync(L->status.get(), 0, 4, s));
             prepare_lattice(L, true, s);
             CSL_CUDA(cudaStreamSynchronize(s));
         } catch (...) {
@@ -461,6 +473,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         if (want_contours && prev >= 0) contour_stage(prev, g_prev);
         if (side.s2) CSL_CUDA(cudaStreamSynchronize(side.s2));
         CSL_CUDA(cudaStreamSynchronize(s));
+        check_lattice_status(L, s);
         if (count_pairs) {
             int64_t pc[2];
             read_to_host(pc, pair_count.get(), 16, s);
@@ -558,6 +571,7 @@ csl_status csl_volume_fraction(csl_lattice* L, const csl_cells* cells, float* vf
         launches_and_reset();
         vf_forward(L, *cells, vf_out, s);
         CSL_CUDA(cudaStreamSynchronize(s));
+        check_lattice_status(L, s);
         t_stats = csl_stats{};
         t_stats.kernel_launches = launches_and_reset();
     });

@@ -150,7 +150,8 @@ void plan_jobs(csl_batch* b, int S) {
     }
     CSL_CUDA(cudaMemsetAsync(b->mask_arena.get(), 0, (size_t)b->mask_arena_words * 4, b->st));
     std::vector<FieldBatchJob> fj;
-    for (auto& J : b->jobs) fj.push_back(FieldBatchJob{J.L, J.g, &J.bins, J.sigma, J.mask});
+    for (auto& J : b->jobs)
+        fj.push_back(FieldBatchJob{J.L, J.g, &J.bins, J.sigma, J.mask, b->flag_d.as<uint32_t>()});
     field_batch_prepare(fj, b->fb, b->st);
     field_batch_run(b->fb, b->n_sm * b->ctas, b->st);
     for (auto& J : b->jobs) {

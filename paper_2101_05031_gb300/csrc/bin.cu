@@ -176,6 +176,18 @@ __global__ void k_list_bounds(const uint32_t* __restrict__ keys, int64_t n,
     }
 }
 
+// recs[p] = rec[vals[p]] (32 bytes each; an index out of range copies record 0)
+__global__ void k_gather_records(const uint4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                 int64_t n, int64_t n_rec, uint4* __restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = vals[p];
+        if ((int64_t)v >= n_rec) v = 0;   // only in a replay whose sizes changed (flagged)
+        out[2 * p] = rec[2 * (int64_t)v];
+        out[2 * p + 1] = rec[2 * (int64_t)v + 1];
+    }
+}
+
 int bits_for(int64_t n) {
     int b = 0;
     while (b < 32 && ((int64_t)1 << b) < n) ++b;
@@ -276,6 +288,13 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
                                                         out.tile_start.as<uint32_t>(),
                                                         out.tile_end.as<uint32_t>());
     CSL_LAUNCH_CHECK("list bounds");
+    // the records themselves in entry order, so that the field kernel stages a
+    // tile's list with one bulk copy
+    out.recs.ensure((size_t)n_pairs * sizeof(csl_rec), s);
+    k_gather_records<<<grid_for(n_pairs, 256), 256, 0, s>>>(
+        reinterpret_cast<const uint4*>(L->rec.get()), out.vals.as<uint32_t>(), n_pairs,
+        L->n_edges, reinterpret_cast<uint4*>(out.recs.get()));
+    CSL_LAUNCH_CHECK("gather records");
 }
 
 }  // namespace csl

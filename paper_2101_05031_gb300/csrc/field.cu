@@ -18,12 +18,15 @@
 // the part (an ulp at 200 mm is 1.5e-5 mm, far above the 1e-5 relative field
 // tolerance at strut surfaces).
 //
-// Work per CTA: the tile's edge list is staged through shared memory in
-// chunks of 256 records; while staging, each thread computes for its record
-// and every layer of the slab whether the edge's support can reach each warp's
+// Work per CTA: the tile's edge list, which the binner stores contiguously (the
+// records themselves, in list order), is staged into shared memory in chunks of
+// 256 records by one bulk copy (TMA, cp.async.bulk) completed on an mbarrier;
+// each thread converts its record to tile-local coordinates, then computes for
+// every (record, layer) item whether the edge's support can reach each warp's
 // 8x4-pixel block (xy box of the edge clipped to |z - z_layer| <= R, grown by
-// R). Warps then walk only the records whose bit is set (ballot + ffs); the
-// per-pixel evaluation is branch-free.
+// R, and the block centre's distance to the line). Warps then walk only the
+// records whose bit is set (ballot + ffs); the per-pixel evaluation is
+// branch-free.
 #include <math.h>
 
 #include <vector>
@@ -48,20 +51,27 @@ struct FieldConst {
     const float2* org_z;   // per slab: z of its first layer
     int32_t mwr;        // mask words per row
     int64_t mask_wpl;   // mask words per layer
+    uint32_t* err;      // device status word: ST_TIMEOUT when a wait gave up
 };
 
 // One (tile, slab) of the field: called by the grid kernel (one CTA per
 // (tile, slab)) and by the persistent batch kernel (one item at a time).
+//
+// The tile's records are contiguous (the binner copies them in list order), so
+// each chunk of up to 256 records is staged by one bulk copy (TMA) issued by
+// thread 0 and completed on an mbarrier; every thread then converts its record
+// to tile-local coordinates in place. bar: the CTA's mbarrier (initialised
+// with one arrival), phase: its parity, kept by the caller across tiles.
+// Returns false (after setting ST_TIMEOUT in *c.err) when a copy never
+// completed; the caller must then stop using the barrier.
 template <int S, bool COUNT>
-__device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
-                                           const uint32_t* __restrict__ vals,
+__device__ __forceinline__ bool field_tile(const csl_rec* __restrict__ recs,
                                            const uint32_t* __restrict__ tstart,
                                            const uint32_t* __restrict__ tend, const FieldConst& c,
                                            float* __restrict__ sigma, uint32_t* __restrict__ mask,
                                            unsigned long long* __restrict__ n_pairs, int tile,
-                                           int slab) {
-    __shared__ float4 s_a[kFieldThreads];   // ax, ay, az (tile-local), ux
-    __shared__ float4 s_b[kFieldThreads];   // uy, uz, len, w / R^4
+                                           int slab, uint64_t* bar, uint32_t& phase) {
+    __shared__ __align__(16) float4 s_rec[kFieldThreads][2];   // raw, then tile-local
     __shared__ uint64_t s_mask[kFieldThreads];   // byte l: warps reached at layer l
 
     const int tx = tile % c.ntx, ty = tile / c.ntx;
@@ -88,12 +98,23 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
 
         for (uint32_t c0 = beg; c0 < end; c0 += kFieldThreads) {
             const int cnt = (int)min((uint32_t)kFieldThreads, end - c0);
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();   // the block's earlier reads of s_rec come first
+                bulk_load(s_rec, recs + c0, (uint32_t)cnt * (uint32_t)sizeof(csl_rec), bar);
+            }
+            // a copy that never completes: report it, wait once more (bounded)
+            // for the copy still in flight, and give the tile up
+            if (__syncthreads_or(!mbar_wait(bar, phase))) {
+                if (threadIdx.x == 0) atomicOr(c.err, ST_TIMEOUT);
+                mbar_wait(bar, phase);
+                return false;
+            }
+            phase ^= 1u;
             if ((int)threadIdx.x < cnt) {
-                float4 A, B;
-                load_record(rec + vals[c0 + threadIdx.x], oxh, oxl, oyh, oyl, ozh, ozl,
-                            cull.inv_R4, A, B);
-                s_a[threadIdx.x] = A;
-                s_b[threadIdx.x] = B;
+                const float4 r0 = s_rec[threadIdx.x][0], r1 = s_rec[threadIdx.x][1];
+                s_rec[threadIdx.x][0] =
+                    make_float4((r0.x - oxh) - oxl, (r0.y - oyh) - oyl, (r0.z - ozh) - ozl, r0.w);
+                s_rec[threadIdx.x][1] = make_float4(r1.x, r1.y, r1.z, r1.w * cull.inv_R4);
                 s_mask[threadIdx.x] = 0;
             }
             __syncthreads();
@@ -102,7 +123,7 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
             for (int item = threadIdx.x; item < cnt * nl; item += kFieldThreads) {
                 const int r = item % cnt, l = item / cnt;
                 reinterpret_cast<uint8_t*>(s_mask)[8 * r + l] =
-                    (uint8_t)cull_layer(s_a[r], s_b[r], l, cull);
+                    (uint8_t)cull_layer(s_rec[r][0], s_rec[r][1], l, cull);
             }
             __syncthreads();
             for (int i0 = 0; i0 < cnt; i0 += 32) {
@@ -113,7 +134,7 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
                     const int b = __ffs(ball) - 1;
                     ball &= ball - 1u;
                     const uint32_t lm = __shfl_sync(0xffffffffu, wm, b);
-                    const float4 A = s_a[i0 + b], B = s_b[i0 + b];
+                    const float4 A = s_rec[i0 + b][0], B = s_rec[i0 + b][1];
                     const float dx = pxl - A.x, dy = pyl - A.y;
                     const float txy = fmaf(dy, B.x, dx * A.w);
 #pragma unroll
@@ -139,7 +160,7 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
                     }
                 }
             }
-            if (c0 + kFieldThreads < end) __syncthreads();   // the next chunk reuses smem
+            __syncthreads();   // the next chunk (or tile) reuses s_rec and s_mask
         }
     }
     if (COUNT) {   // n_pairs[0]: nonzero terms, n_pairs[1]: evaluated terms
@@ -180,23 +201,29 @@ __device__ __forceinline__ void field_tile(const csl_rec* __restrict__ rec,
             }
         }
     }
+    return true;
 }
 
 template <int S, bool COUNT>
 __global__ void __launch_bounds__(kFieldThreads, 8)
-k_field(const csl_rec* __restrict__ rec, const uint32_t* __restrict__ vals,
-        const uint32_t* __restrict__ tstart, const uint32_t* __restrict__ tend, FieldConst c,
-        float* __restrict__ sigma, uint32_t* __restrict__ mask,
-        unsigned long long* __restrict__ n_pairs) {
-    field_tile<S, COUNT>(rec, vals, tstart, tend, c, sigma, mask, n_pairs, blockIdx.x,
-                         blockIdx.y);
+k_field(const csl_rec* __restrict__ recs, const uint32_t* __restrict__ tstart,
+        const uint32_t* __restrict__ tend, FieldConst c, float* __restrict__ sigma,
+        uint32_t* __restrict__ mask, unsigned long long* __restrict__ n_pairs) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    field_tile<S, COUNT>(recs, tstart, tend, c, sigma, mask, n_pairs, blockIdx.x, blockIdx.y,
+                         &bar, phase);
 }
 
 // One job of a batch, as the persistent kernel reads it.
 struct FieldJob {
     FieldConst c;
-    const csl_rec* rec;
-    const uint32_t* vals;
+    const csl_rec* recs;   // the binned records, in list order
     const uint32_t* tstart;
     const uint32_t* tend;
     float* sigma;
@@ -213,6 +240,13 @@ k_field_batch(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items
               const uint32_t* __restrict__ order, uint32_t n_items, uint32_t* counter) {
     __shared__ uint32_t s_item;
     __shared__ FieldJob s_job;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     uint32_t cur_job = 0xffffffffu;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
@@ -228,9 +262,10 @@ k_field_batch(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items
             __syncthreads();
         }
         const uint32_t n_tiles = (uint32_t)s_job.c.n_tiles;
-        field_tile<S, false>(s_job.rec, s_job.vals, s_job.tstart, s_job.tend, s_job.c,
-                             s_job.sigma, s_job.mask, nullptr, (int)(item.y % n_tiles),
-                             (int)(item.y / n_tiles));
+        if (!field_tile<S, false>(s_job.recs, s_job.tstart, s_job.tend, s_job.c, s_job.sigma,
+                                  s_job.mask, nullptr, (int)(item.y % n_tiles),
+                                  (int)(item.y / n_tiles), &bar, phase))
+            break;   // a bulk copy gave up (reported): this CTA takes no more items
         __syncthreads();   // shared memory is reused by the next item
     }
 }
@@ -334,20 +369,20 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     // tile and slab origins in double, each split into a (hi, lo) float pair
     DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
     launch_origins(g, org_d.as<float2>(), s);
-    const FieldConst c = make_field_const(g, C, org_d.as<float2>());
+    FieldConst c = make_field_const(g, C, org_d.as<float2>());
+    c.err = L->status.as<uint32_t>();
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
-    const csl_rec* rec = L->rec.as<csl_rec>();
-    const uint32_t* vals = bins.vals.as<uint32_t>();
+    const csl_rec* recs = bins.recs.as<csl_rec>();
     const uint32_t* ts = bins.tile_start.as<uint32_t>();
     const uint32_t* te = bins.tile_end.as<uint32_t>();
 #define CSL_FIELD_CASE(SV)                                                                    \
     case SV:                                                                                  \
         if (count_pairs)                                                                      \
-            k_field<SV, true><<<grid, kFieldThreads, 0, s>>>(rec, vals, ts, te, c, sigma, mask,\
+            k_field<SV, true><<<grid, kFieldThreads, 0, s>>>(recs, ts, te, c, sigma, mask,    \
                                                              count_pairs);                    \
         else                                                                                  \
-            k_field<SV, false><<<grid, kFieldThreads, 0, s>>>(rec, vals, ts, te, c, sigma,     \
-                                                              mask, nullptr);                 \
+            k_field<SV, false><<<grid, kFieldThreads, 0, s>>>(recs, ts, te, c, sigma, mask,   \
+                                                              nullptr);                       \
         break;
     switch (g.S) {
         CSL_FIELD_CASE(1)
@@ -384,8 +419,8 @@ void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb,
         launch_origins(J.g, org, s);
         o += (size_t)J.g.ntx + J.g.nty + J.g.n_slabs;
         hj[j].c = make_field_const(J.g, (float)J.L->C, org);
-        hj[j].rec = J.L->rec.as<csl_rec>();
-        hj[j].vals = J.bins->vals.as<uint32_t>();
+        hj[j].c.err = J.err;
+        hj[j].recs = J.bins->recs.as<csl_rec>();
         hj[j].tstart = J.bins->tile_start.as<uint32_t>();
         hj[j].tend = J.bins->tile_end.as<uint32_t>();
         hj[j].sigma = J.sigma;

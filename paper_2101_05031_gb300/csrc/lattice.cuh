@@ -27,6 +27,7 @@ struct csl_lattice {
     csl::DevBuf sid;      // uint32 [n_edges]: original edge id | (endpoints swapped) << 31
     csl::DevBuf node_csr_off;  // int32 [n_nodes + 1] (built on first backward)
     csl::DevBuf node_csr;      // uint32 [2 n_edges]: sorted position << 1 | end (0 = v_s)
+    csl::DevBuf status;        // uint32: ST_TIMEOUT when a device wait gave up
     float bbox_lo[3] = {0, 0, 0}, bbox_hi[3] = {0, 0, 0};
     float max_dz = 0, max_radius = 0;
 };

@@ -26,6 +26,7 @@ struct ChunkGeom {
 // Per-slab binning results (device).
 struct SlabBins {
     DevBuf keys, vals;          // sorted pairs: key = slab * n_tiles + tile, val = record position
+    DevBuf recs;                // csl_rec per entry, in entry order: each tile's list contiguous
     DevBuf tile_start, tile_end;// uint32 [n_slabs * n_tiles]
     int64_t n_pairs = 0;
     int64_t n_cand = 0;         // records examined: the slabs' z windows, summed
@@ -73,6 +74,7 @@ struct FieldBatchJob {
     const SlabBins* bins;   // must stay allocated (same buffers) while the batch lives
     float* sigma;
     uint32_t* mask;         // zero on entry of every run
+    uint32_t* err;          // device word OR-ed with ST_TIMEOUT when a wait gives up
 };
 struct FieldBatch {
     DevBuf jobs, origins, items, keys, vals, tmp_keys, tmp_vals, counter;
@@ -110,6 +112,10 @@ ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SliceP
                      int n);
 void validate_desc(const csl_slice_desc* d);
 void require_arg(bool ok, const char* msg);
+
+// Reads and clears the lattice's device status word; CSL_ERR_TIMEOUT when a
+// device wait of an earlier kernel gave up (synchronises s).
+void check_lattice_status(const csl_lattice* L, cudaStream_t s);
 
 // Volume fraction per density cell and its adjoint (vf.cu).
 void vf_forward(const csl_lattice* L, const csl_cells& cells, float* vf, cudaStream_t s);
