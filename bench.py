@@ -33,7 +33,7 @@ METRIC = "pixel-evals/s and layers/s at 10M and 100M struts; backward/forward ti
 F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the field kernel
 # FP32 instructions the field kernel executes per cycle as a fraction of the
 # FP32 peak (every evaluated lane), from an ncu capture of one launch
-NCU_FIELD_EXECUTED_FRAC = 8473.0 / (152 * 128 * 2)
+NCU_FIELD_EXECUTED_FRAC = 8422.3 / (152 * 128 * 2)
 HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
 # algorithmic bytes of the HBM-bound stages
 BIN_BYTES_PER_WINDOW_RECORD = 24   # xy box (16) + z range (8) of a record read per slab window
@@ -43,8 +43,8 @@ MS_BYTES_PER_CROSSING = 16         # two Sigma values read, the vertex (x, y) wr
 MS_BYTES_PER_LOOP = 8              # the loop's vertex offset written
 # DRAM bytes (read + write) per pixel-layer of one field-kernel launch, from an
 # ncu capture of the current field kernel on the 12.96M-strut graded lattice
-# (1.12 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
-FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.1262e9 / (64 * 2000 * 2000)
+# (1.28 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
+FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.2835e9 / (64 * 2000 * 2000)
 N_SM = 152
 FP32_LANES = 128
 MAX_SM_MHZ = 2070.0
