@@ -431,6 +431,15 @@ csl_status csl_support_metrics(const csl_lattice* lat, const double* t_p, double
                                const double* coeffs, double* gamma, double* psi, void* stream);
 
 /*
+ * csl_debug_wait_timeout -- test of the bounded device waits: launches one
+ * block that waits, with the field kernel's mbarrier wait, on a barrier that
+ * nothing arms, giving up after `polls` polls (1 .. 2^22). Returns
+ * CSL_ERR_TIMEOUT when the wait gave up and reported it (the expected result);
+ * the device stays usable. The paper has no counterpart.
+ */
+csl_status csl_debug_wait_timeout(uint32_t polls, void* stream);
+
+/*
  * csl_measure_fp32_peak -- FP32 throughput of the device, measured with a
  * kernel of independent FFMA chains at full occupancy (best of 5 timed
  * launches after one warm-up). A measurement helper for the roofline of the

@@ -121,6 +121,7 @@ SIGNATURES = [
     ("csl_hatches_free", None, [ctypes.POINTER(Hatches)]),
     ("csl_support_metrics", c_i32, [c_vp, ctypes.POINTER(c_f64), c_f64, ctypes.POINTER(c_f64),
                                     ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
+    ("csl_debug_wait_timeout", c_i32, [ctypes.c_uint32, c_vp]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),

@@ -270,6 +270,18 @@ k_field_batch(const FieldJob* __restrict__ jobs, const uint2* __restrict__ items
     }
 }
 
+// The field kernel's bounded mbarrier wait on a barrier that nothing arms: it
+// must give up after `polls` polls and report ST_TIMEOUT (test of the path).
+__global__ void k_wait_nothing(uint32_t polls, uint32_t* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (__syncthreads_or(!mbar_wait(&bar, 0, polls)) && threadIdx.x == 0) atomicOr(err, ST_TIMEOUT);
+}
+
 // items[i] = (job, slab * n_tiles + tile) for the jobs' item ranges off[j]..off[j+1].
 __global__ void k_make_items(const int64_t* __restrict__ off, int n_jobs, uint2* __restrict__ items) {
     const int64_t n = off[n_jobs];
@@ -470,3 +482,24 @@ void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s) {
 }
 
 }  // namespace csl
+
+extern "C" csl_status csl_debug_wait_timeout(uint32_t polls, void* stream) {
+    try {
+        if (polls == 0 || polls > csl::kWaitLimit) csl::fail(CSL_ERR_INVALID_ARG, "polls in [1, 2^22]");
+        cudaStream_t s = (cudaStream_t)stream;
+        csl::DevBuf err(4, s);
+        CSL_CUDA(cudaMemsetAsync(err.get(), 0, 4, s));
+        csl::k_wait_nothing<<<1, 64, 0, s>>>(polls, err.as<uint32_t>());
+        CSL_LAUNCH_CHECK("wait test");
+        uint32_t st = 0;
+        csl::read_to_host(&st, err.get(), 4, s);
+        if (st & csl::ST_TIMEOUT) csl::fail(CSL_ERR_TIMEOUT, "the wait gave up as it should");
+        return CSL_OK;
+    } catch (const csl::Error& e) {
+        csl::set_last_error(e.what());
+        return e.code;
+    } catch (...) {
+        csl::set_last_error("unknown error");
+        return CSL_ERR_CUDA;
+    }
+}

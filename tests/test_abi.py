@@ -87,6 +87,9 @@ def test_errors_cross_the_abi_as_codes():
     assert st == 1
     info = _lib.BatchInfo()
     assert lib.csl_batch_get_info(None, ctypes.byref(info)) == 1
+    # the wait test's poll count is checked before any device call
+    assert lib.csl_debug_wait_timeout(0, None) == 1
+    assert lib.csl_debug_wait_timeout(1 << 23, None) == 1
 
 
 def test_no_gpu_reports_not_ready():

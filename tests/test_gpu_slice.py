@@ -311,3 +311,18 @@ def test_isolated_strut_circle_on_gpu():
     assert np.max(np.abs(np.hypot(xy[:, 0], xy[:, 1]) - rho)) < 0.01 * 0.02
     area = 0.5 * np.sum(xy[:, 0] * np.roll(xy[:, 1], -1) - np.roll(xy[:, 0], -1) * xy[:, 1])
     assert area == pytest.approx(math.pi * rho * rho, rel=2e-3)
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable(c1):
+    """The field kernel's mbarrier wait, on a barrier that nothing arms, gives
+    up after its poll limit and reports CSL_ERR_TIMEOUT; the context is intact
+    and the next slice is unchanged."""
+    from paper_2101_05031_gb300 import _lib
+    cfg, lat = c1
+    before, _ = gpu_slice(lat, cfg, n_layers=3)
+    lib = _lib.load()
+    for polls in (1, 1000):
+        assert lib.csl_debug_wait_timeout(polls, None) == 4
+        assert b"gave up" in lib.csl_last_error()
+    after, _ = gpu_slice(lat, cfg, n_layers=3)
+    assert np.array_equal(before, after)
