@@ -19,3 +19,4 @@ from .lattices import (  # noqa: F401
     lattice_bbox,
     rng,
 )
+from .tets import density_config, graded_target_grid, kuhn_tet_mesh  # noqa: F401,E402
