@@ -449,6 +449,85 @@ csl_status csl_debug_wait_timeout(uint32_t polls, void* stream);
  */
 csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* stream);
 
+/* ---- density matching of a tetrahedral lattice (Sec. 5.5) ---------------- */
+
+/* Target densities on a voxel grid: voxel (i, j, k) is the box origin + h *
+ * ([i, i+1] x [j, j+1] x [k, k+1]); target is a HOST array [nz][ny][nx]. */
+typedef struct csl_voxels {
+    double origin[3];
+    double h;               /* > 0 */
+    int32_t dims[3];        /* nx, ny, nz >= 1, product < 2^31 */
+    const float* target;    /* finite */
+} csl_voxels;
+
+typedef struct csl_dm_params {
+    float r_min;        /* smallest printable radius (> 0); the base radius is r0 = 2 r_min */
+    float R;            /* support radius, > 4 r_min (the doubled base radius); 0: 6 r_min */
+    float C;            /* iso-value, > 0 */
+    float temperature;  /* T / C of the smoothed indicator, > 0 (0.01 in the volume fraction) */
+    int32_t tet_n;      /* n: n^3 samples per tetrahedron, 1..16 */
+    int32_t vox_m;      /* m: m^3 samples per voxel, 1..16 */
+    int32_t max_depth;  /* subdivision levels, 0..8 */
+    int32_t iters;      /* bisection halvings, 1..40 */
+} csl_dm_params;
+
+/* Result of csl_density_match, host memory owned by the library (free with
+ * csl_dm_result_free). Nodes: the input nodes, then the midpoints in creation
+ * order. Edges: the unsplit edges (both node ids, smaller first) in creation
+ * order, with their radii r0 * ratio. Tetrahedra: the leaves in creation order
+ * (children follow all tetrahedra of the previous level), with depth, target
+ * (Step 1), rho_star (density with the doubled radius) and ratio (Step 3). */
+typedef struct csl_dm_result {
+    int64_t n_nodes;
+    float* nodes;            /* [n_nodes][3] */
+    int64_t n_edges;
+    int32_t* edges;          /* [n_edges][2] */
+    float* radius;           /* [n_edges] */
+    float* step3_ratio;      /* [n_edges]: the ratio before the voxel check */
+    int64_t n_tets;
+    int32_t* tets;           /* [n_tets][4] */
+    int32_t* tet_depth;      /* [n_tets] */
+    double* tet_target;      /* [n_tets] */
+    float* tet_rho_star;     /* [n_tets] */
+    float* tet_ratio;        /* [n_tets] */
+    int64_t n_voxels;
+    float* voxel_ratio;      /* [nz][ny][nx]; NaN where no edge meets the voxel */
+    int64_t n_subdivided;    /* tetrahedra split over all levels */
+} csl_dm_result;
+
+/*
+ * csl_density_match -- builds a lattice matching target densities from a
+ * tetrahedral mesh (Sec. 5.5, the subdivision and radius-tuning operators and
+ * the four steps):
+ *   1. target of a tetrahedron = the largest target of the voxels whose
+ *      centres it contains (closed test, FP64 determinants); with none, the
+ *      trilinear interpolation of the voxel-centre values at its centroid;
+ *   2. rho* = its density with the doubled radius 2 r0 on its six edges; while
+ *      rho* < target (and depth < max_depth) it is cut 1:8 at its edges'
+ *      midpoints (float32), the inner octahedron along its shortest diagonal;
+ *      a split edge is replaced by its halves everywhere;
+ *   3. every leaf bisects the common ratio s in [1/2, 2] of its six edges'
+ *      radii r0 s for its target; an edge takes the smallest ratio of the
+ *      leaves containing it;
+ *   4. every voxel bisects a common ratio for the edges meeting it (closed
+ *      segment-box test, FP64), the other struts at their Step-3 radii; an
+ *      edge keeps the smaller of its ratio and the voxel's.
+ * A density is the mean of sigma((Sigma - C) / (temperature C)) at n^3
+ * equal-volume samples of the tetrahedron (centroids of its Kuhn subdivision)
+ * or m^3 stratified samples of the voxel (Eq. 9), Sigma with the PHYSICAL
+ * weights of radius r (Sec. 3.2); a tetrahedron's density uses its own six
+ * struts. nodes [n_nodes][3], tets [n_tets][4]: HOST arrays (copied). The
+ * densities, bisections and the voxel pass run on the device; the topology
+ * of the subdivision is edited on the host between levels. Errors:
+ * INVALID_ARG (index out of range, non-finite value, parameter out of range),
+ * CAPACITY (more than 2^27 tetrahedra or 2^31 voxel-edge pairs), OOM.
+ * Synchronises the stream.
+ */
+csl_status csl_density_match(const float* nodes, int64_t n_nodes, const int32_t* tets,
+                             int64_t n_tets, const csl_voxels* vox, const csl_dm_params* p,
+                             void* stream, csl_dm_result** out);
+void csl_dm_result_free(csl_dm_result* r);
+
 const char* csl_last_error(void);
 const char* csl_version(void);
 

@@ -226,13 +226,23 @@ def voxel_centre(grid, i, j, k):
 
 def tet_target(grid, v) -> float:
     """Step 1: the largest target of the voxels whose centres the tetrahedron
-    contains (D3), else the interpolated target at its centroid (D4)."""
+    contains (D3), else the interpolated target at its centroid (D4). Only
+    centres inside the tetrahedron's bounding box can be contained, so the
+    others are not tested."""
     dims = grid["dims"]
+    vv = np.asarray(v, dtype=np.float64)
+    lo, hi = vv.min(0), vv.max(0)
+    o = np.asarray(grid["origin"], dtype=np.float64)
+    h = float(grid["h"])
+    rng = []
+    for ax in range(3):
+        c = o[ax] + h * (np.arange(int(dims[ax])) + 0.5)
+        rng.append(np.nonzero((c >= lo[ax]) & (c <= hi[ax]))[0])
     best = None
-    for k in range(int(dims[2])):
-        for j in range(int(dims[1])):
-            for i in range(int(dims[0])):
-                if point_in_tet(voxel_centre(grid, i, j, k), v):
+    for k in rng[2]:
+        for j in rng[1]:
+            for i in rng[0]:
+                if point_in_tet(voxel_centre(grid, int(i), int(j), int(k)), v):
                     t = float(grid["target"][k, j, i])
                     best = t if best is None else max(best, t)
     if best is not None:
@@ -353,6 +363,31 @@ def tet_density_fn(v, A, r0: float, R: float, C: float, T: float):
     return lambda s: smooth_density(weight_R4(r0 * s, R, C) * J, C, T)
 
 
+def voxel_density_fn(grid, i, j, k, seg_a, seg_b, seg_ratio, r0: float, R: float, C: float,
+                     T: float, m: int):
+    """(rho_V(s), meets) of voxel (i, j, k) (reading D7): the struts meeting the
+    voxel at radius r0 s, the others at r0 * seg_ratio. Struts whose support
+    box misses the voxel contribute nothing at its samples and are skipped."""
+    o = [float(x) for x in grid["origin"]]
+    h = float(grid["h"])
+    lo = (o[0] + h * i, o[1] + h * j, o[2] + h * k)
+    hi = (o[0] + h * (i + 1), o[1] + h * (j + 1), o[2] + h * (k + 1))
+    seg_a = np.asarray(seg_a, dtype=np.float64).reshape(-1, 3)
+    seg_b = np.asarray(seg_b, dtype=np.float64).reshape(-1, 3)
+    near = np.all((np.minimum(seg_a, seg_b) - R <= np.array(hi))
+                  & (np.maximum(seg_a, seg_b) + R >= np.array(lo)), axis=1)
+    idx = np.nonzero(near)[0]
+    meets = np.zeros(seg_a.shape[0], dtype=bool)
+    for s in idx:
+        meets[s] = seg_meets_box(seg_a[s], seg_b[s], lo, hi)
+    pts = voxel_points(grid, i, j, k, m)
+    M = seg_R4I(pts, seg_a[idx], seg_b[idx], R)
+    mi = meets[idx]
+    F = (M[:, ~mi] * weight_R4(r0 * np.asarray(seg_ratio)[idx][~mi], R, C)[None, :]).sum(1)
+    J = M[:, mi].sum(1)
+    return (lambda s: smooth_density(F + weight_R4(r0 * s, R, C) * J, C, T)), meets
+
+
 def density_match(nodes, tets, grid, *, r_min: float, R: float | None = None, C: float = 1.0,
                   temperature: float = 0.01, tet_n: int = 8, vox_m: int = 8, max_depth: int = 3,
                   iters: int = 24):
@@ -405,26 +440,16 @@ def density_match(nodes, tets, grid, *, r_min: float, R: float | None = None, C:
 
     # step 4: the common ratio of each voxel, against the step-3 ratios
     dims = [int(x) for x in grid["dims"]]
-    o = [float(x) for x in grid["origin"]]
-    h = float(grid["h"])
     vox = np.full((dims[2], dims[1], dims[0]), np.nan)
     new_r = seg_r.copy()
     for k in range(dims[2]):
         for j in range(dims[1]):
             for i in range(dims[0]):
-                lo = (o[0] + h * i, o[1] + h * j, o[2] + h * k)
-                hi = (o[0] + h * (i + 1), o[1] + h * (j + 1), o[2] + h * (k + 1))
-                meets = np.array([seg_meets_box(seg_a[s], seg_b[s], lo, hi)
-                                  for s in range(len(segs))], dtype=bool)
+                rho, meets = voxel_density_fn(grid, i, j, k, seg_a, seg_b, seg_r, r0, R, C, T,
+                                              vox_m)
                 if not meets.any():
                     continue
-                pts = voxel_points(grid, i, j, k, vox_m)
-                M = seg_R4I(pts, seg_a, seg_b, R)
-                F = (M[:, ~meets] * weight_R4(r0 * seg_r[~meets], R, C)[None, :]).sum(1)
-                J = M[:, meets].sum(1)
-                tv = float(grid["target"][k, j, i])
-                s_v = bisect_ratio(
-                    lambda s: smooth_density(F + weight_R4(r0 * s, R, C) * J, C, T), tv, iters)
+                s_v = bisect_ratio(rho, float(grid["target"][k, j, i]), iters)
                 vox[k, j, i] = s_v
                 new_r[meets] = np.minimum(new_r[meets], s_v)
     nodes_out = np.array(lat.nodes, dtype=np.float32).reshape(-1, 3)

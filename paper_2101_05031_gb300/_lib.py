@@ -63,6 +63,24 @@ class Stats(ctypes.Structure):
                 ("evaluated_terms", c_i64), ("window_records", c_i64)]
 
 
+class Voxels(ctypes.Structure):
+    _fields_ = [("origin", c_f64 * 3), ("h", c_f64), ("dims", c_i32 * 3), ("target", c_vp)]
+
+
+class DmParams(ctypes.Structure):
+    _fields_ = [("r_min", ctypes.c_float), ("R", ctypes.c_float), ("C", ctypes.c_float),
+                ("temperature", ctypes.c_float), ("tet_n", c_i32), ("vox_m", c_i32),
+                ("max_depth", c_i32), ("iters", c_i32)]
+
+
+class DmResult(ctypes.Structure):
+    _fields_ = [("n_nodes", c_i64), ("nodes", c_vp), ("n_edges", c_i64), ("edges", c_vp),
+                ("radius", c_vp), ("step3_ratio", c_vp), ("n_tets", c_i64), ("tets", c_vp),
+                ("tet_depth", c_vp), ("tet_target", c_vp), ("tet_rho_star", c_vp),
+                ("tet_ratio", c_vp), ("n_voxels", c_i64), ("voxel_ratio", c_vp),
+                ("n_subdivided", c_i64)]
+
+
 class CellsDesc(ctypes.Structure):
     _fields_ = [("origin", c_f64 * 3), ("h", c_f64), ("dims", c_i32 * 3), ("m", c_i32),
                 ("temperature", c_f64)]
@@ -122,6 +140,10 @@ SIGNATURES = [
     ("csl_support_metrics", c_i32, [c_vp, ctypes.POINTER(c_f64), c_f64, ctypes.POINTER(c_f64),
                                     ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_debug_wait_timeout", c_i32, [ctypes.c_uint32, c_vp]),
+    ("csl_density_match", c_i32, [c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(Voxels),
+                                  ctypes.POINTER(DmParams), c_vp,
+                                  ctypes.POINTER(ctypes.POINTER(DmResult))]),
+    ("csl_dm_result_free", None, [ctypes.POINTER(DmResult)]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),

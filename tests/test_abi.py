@@ -42,7 +42,9 @@ def test_structs_match_header_layout(tmp_path):
     mirrors = {"csl_params": _lib.Params, "csl_lattice_info": _lib.LatticeInfo,
                "csl_slice_desc": _lib.SliceDesc, "csl_contours": _lib.Contours,
                "csl_stats": _lib.Stats, "csl_batch_opts": _lib.BatchOpts,
-               "csl_batch_info": _lib.BatchInfo, "csl_hatches": _lib.Hatches}
+               "csl_batch_info": _lib.BatchInfo, "csl_hatches": _lib.Hatches,
+               "csl_cells": _lib.CellsDesc, "csl_voxels": _lib.Voxels,
+               "csl_dm_params": _lib.DmParams, "csl_dm_result": _lib.DmResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -87,6 +89,28 @@ def test_errors_cross_the_abi_as_codes():
     assert st == 1
     info = _lib.BatchInfo()
     assert lib.csl_batch_get_info(None, ctypes.byref(info)) == 1
+    # density matching: parameters and indices are checked before any device call
+    vox = _lib.Voxels((ctypes.c_double * 3)(0, 0, 0), 1.0, (ctypes.c_int32 * 3)(1, 1, 1), None)
+    prm = _lib.DmParams(0.1, 0.0, 1.0, 0.01, 4, 4, 2, 24)
+    res = ctypes.POINTER(_lib.DmResult)()
+    st = lib.csl_density_match(None, 0, None, 0, ctypes.byref(vox), ctypes.byref(prm), None,
+                               ctypes.byref(res))
+    assert st == 1 and b"target" in lib.csl_last_error()
+    tgt = np.zeros(1, np.float32)
+    vox.target = tgt.ctypes.data_as(ctypes.c_void_p)
+    for field, bad, word in (("R", 0.3, b"R must"), ("tet_n", 17, b"tet_n"), ("max_depth", 9, b"max_depth"),
+                             ("iters", 0, b"iters"), ("r_min", -1.0, b"r_min")):
+        p2 = _lib.DmParams(0.1, 0.0, 1.0, 0.01, 4, 4, 2, 24)
+        setattr(p2, field, bad)
+        st = lib.csl_density_match(None, 0, None, 0, ctypes.byref(vox), ctypes.byref(p2), None,
+                                   ctypes.byref(res))
+        assert st == 1 and word in lib.csl_last_error(), field
+    nodes = np.zeros((4, 3), np.float32)
+    tets = np.array([[0, 1, 2, 4]], np.int32)
+    st = lib.csl_density_match(nodes.ctypes.data_as(ctypes.c_void_p), 4,
+                               tets.ctypes.data_as(ctypes.c_void_p), 1, ctypes.byref(vox),
+                               ctypes.byref(prm), None, ctypes.byref(res))
+    assert st == 1 and b"out of range" in lib.csl_last_error()
     # the wait test's poll count is checked before any device call
     assert lib.csl_debug_wait_timeout(0, None) == 1
     assert lib.csl_debug_wait_timeout(1 << 23, None) == 1

@@ -1,0 +1,178 @@
+"""Density matching on the GPU (csl_density_match) against the FP64 oracle:
+the subdivision (topology, bit-exact where no decision is a near tie), the
+targets, rho*, the bisected ratios (compared through the densities they
+reach, since a flat density leaves the ratio ill-conditioned), the voxel
+ratios and the per-edge minimum rule."""
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import density as D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C, TEMP = 1.0, 0.01
+
+
+def _run_gpu(cfg, **kw):
+    import paper_2101_05031_gb300 as cs
+    args = dict(r_min=cfg["r_min"], tet_n=cfg["tet_n"], vox_m=cfg["vox_m"],
+                max_depth=cfg["max_depth"], iters=cfg["iters"])
+    args.update(kw)
+    return cs.density_match(cfg["nodes"], cfg["tets"], cfg["grid"], **args)
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = synth.density_config(small=True)
+    ref = D.density_match(cfg["nodes"], cfg["tets"], cfg["grid"], r_min=cfg["r_min"],
+                          tet_n=cfg["tet_n"], vox_m=cfg["vox_m"], max_depth=cfg["max_depth"],
+                          iters=cfg["iters"])
+    got = _run_gpu(cfg)
+    return cfg, ref, got
+
+
+def _ratio_close(rho, s_gpu, s_ref, tol_s=1e-4, tol_rho=5e-5):
+    """Same ratio, or one the density cannot tell apart from it."""
+    if abs(float(s_gpu) - float(s_ref)) <= tol_s:
+        return True
+    return abs(rho(float(s_gpu)) - rho(float(s_ref))) <= tol_rho
+
+
+def test_subdivision_topology_matches(small):
+    cfg, ref, got = small
+    margins = np.array([abs(m) for _, m, _ in ref["decisions"]])
+    assert margins.min() > 1e-4          # no near tie in this seeded case
+    assert got["n_subdivided"] == sum(1 for *_, s in ref["decisions"] if s) > 0
+    assert np.array_equal(got["nodes"], ref["nodes"])
+    assert np.array_equal(got["edges"], ref["edges"])
+    assert np.array_equal(got["tets"], ref["tets"])
+    assert np.array_equal(got["depth"], ref["depth"])
+    assert len(set(ref["depth"].tolist())) == 3   # all three levels occur
+
+
+def test_targets_and_rho_star(small):
+    cfg, ref, got = small
+    assert np.max(np.abs(got["target"] - ref["target"])) <= 1e-12
+    assert np.max(np.abs(got["rho_star"] - ref["rho_star"])) <= 2e-5
+
+
+def test_tet_ratios_reach_the_same_densities(small):
+    cfg, ref, got = small
+    A = D.kuhn_coefficients(cfg["tet_n"])
+    r0, R = ref["r0"], ref["R"]
+    n_interior = 0
+    for k, t in enumerate(ref["tets"]):
+        rho = D.tet_density_fn(ref["nodes"][t].astype(np.float64), A, r0, R, C, TEMP * C)
+        assert _ratio_close(rho, got["tet_ratio"][k], ref["tet_ratio"][k]), k
+        n_interior += 0.5 < ref["tet_ratio"][k] < 2.0
+    assert n_interior >= 20
+
+
+def test_edge_ratios_take_the_smallest(small):
+    """Step 3 per edge: bounded by the tetrahedra's differences; Step 4: the
+    GPU's final ratio is exactly min(step-3 ratio, ratios of the voxels the
+    edge meets), with the meets decided by the oracle's FP64 test."""
+    cfg, ref, got = small
+    lat = ref["lattice"]
+    d_tet = np.abs(got["tet_ratio"].astype(np.float64) - ref["tet_ratio"])
+    # per edge: the largest ratio difference of the leaves containing it
+    seg_index = {e: i for i, e in enumerate(e for e in range(len(lat.edges))
+                                            if lat.children[e] is None)}
+    bound = np.zeros(len(seg_index))
+    leaves = [t for t in range(len(lat.tets)) if lat.leaf[t]]
+    for li, t in enumerate(leaves):
+        for e in lat.tet_edges[t]:
+            for s in lat.leaf_segments(e):
+                bound[seg_index[s]] = max(bound[seg_index[s]], d_tet[li])
+    assert np.all(np.abs(got["step3_ratio"] - ref["step3_ratio"]) <= bound + 1e-6)
+    # the minimum rule, bit-exact on the GPU's own values
+    grid = cfg["grid"]
+    a = got["nodes"][got["edges"][:, 0]].astype(np.float64)
+    b = got["nodes"][got["edges"][:, 1]].astype(np.float64)
+    expect = got["step3_ratio"].copy()
+    o, h = grid["origin"], grid["h"]
+    nx, ny, nz = grid["dims"]
+    for k, j, i in itertools.product(range(nz), range(ny), range(nx)):
+        lo = (o[0] + h * i, o[1] + h * j, o[2] + h * k)
+        hi = (o[0] + h * (i + 1), o[1] + h * (j + 1), o[2] + h * (k + 1))
+        meets = np.array([D.seg_meets_box(a[e], b[e], lo, hi) for e in range(len(a))])
+        assert np.isnan(got["voxel_ratio"][k, j, i]) == (not meets.any())
+        if meets.any():
+            expect[meets] = np.minimum(expect[meets], got["voxel_ratio"][k, j, i])
+    assert np.array_equal(got["radius"], (np.float32(ref["r0"]) * expect).astype(np.float32))
+
+
+def test_voxel_ratios_reach_the_same_densities(small):
+    cfg, ref, got = small
+    grid = cfg["grid"]
+    seg_a = ref["nodes"][ref["edges"][:, 0]].astype(np.float64)
+    seg_b = ref["nodes"][ref["edges"][:, 1]].astype(np.float64)
+    nx, ny, nz = grid["dims"]
+    n = 0
+    for k, j, i in itertools.product(range(nz), range(ny), range(nx)):
+        s_ref = ref["voxel_ratio"][k, j, i]
+        if np.isnan(s_ref):
+            assert np.isnan(got["voxel_ratio"][k, j, i])
+            continue
+        rho, _ = D.voxel_density_fn(grid, i, j, k, seg_a, seg_b, ref["step3_ratio"], ref["r0"],
+                                    ref["R"], C, TEMP * C, cfg["vox_m"])
+        # the GPU's fixed part uses its own step-3 ratios: allow their spread
+        assert _ratio_close(rho, got["voxel_ratio"][k, j, i], s_ref, tol_s=2e-3, tol_rho=2e-4)
+        n += 1
+    assert n >= 10
+
+
+def test_no_subdivision_and_flat_targets():
+    """max_depth = 0 keeps the mesh; a target beyond reach takes the end points."""
+    cfg = synth.density_config(small=True)
+    grid = dict(cfg["grid"])
+    for value, ratio in ((5.0, 2.0), (0.0, 0.5)):
+        grid["target"] = np.full_like(cfg["grid"]["target"], value)
+        got = _run_gpu(dict(cfg, grid=grid), max_depth=0)
+        assert got["n_subdivided"] == 0 and got["tets"].shape == cfg["tets"].shape
+        assert np.all(got["tet_ratio"] == ratio)
+        assert np.all(got["voxel_ratio"][~np.isnan(got["voxel_ratio"])] == ratio)
+        assert np.allclose(got["radius"], 2 * cfg["r_min"] * ratio)
+
+
+def test_empty_mesh():
+    cfg = synth.density_config(small=True)
+    got = _run_gpu(dict(cfg, nodes=np.zeros((0, 3), np.float32), tets=np.zeros((0, 4), np.int32)))
+    assert got["edges"].shape == (0, 2) and got["tets"].shape == (0, 4)
+    assert np.all(np.isnan(got["voxel_ratio"]))
+
+
+def test_full_workload_sampled_against_the_oracle():
+    """The 93,750-tetrahedron workload: sampled leaves' targets, rho* and ratios
+    and sampled voxels' ratios recomputed by the oracle one by one."""
+    cfg = synth.density_config()
+    got = _run_gpu(cfg)
+    assert got["n_subdivided"] > 0 and got["tets"].shape[0] > cfg["tets"].shape[0]
+    r0 = 2 * cfg["r_min"]
+    R = 3 * r0
+    A = D.kuhn_coefficients(cfg["tet_n"])
+    r = synth.rng(17)
+    for k in r.choice(got["tets"].shape[0], 24, replace=False):
+        v = got["nodes"][got["tets"][k]].astype(np.float64)
+        assert abs(D.tet_target(cfg["grid"], v) - got["target"][k]) <= 1e-12
+        rho = D.tet_density_fn(v, A, r0, R, C, TEMP * C)
+        assert abs(rho(2.0) - got["rho_star"][k]) <= 2e-5
+        s_ref = D.bisect_ratio(rho, got["target"][k], cfg["iters"])
+        assert _ratio_close(rho, got["tet_ratio"][k], s_ref)
+    grid = cfg["grid"]
+    seg_a = got["nodes"][got["edges"][:, 0]].astype(np.float64)
+    seg_b = got["nodes"][got["edges"][:, 1]].astype(np.float64)
+    nx, ny, nz = grid["dims"]
+    for flat in r.choice(nx * ny * nz, 12, replace=False):
+        i, j, k = flat % nx, (flat // nx) % ny, flat // (nx * ny)
+        rho, meets = D.voxel_density_fn(grid, i, j, k, seg_a, seg_b, got["step3_ratio"], r0, R, C,
+                                        TEMP * C, cfg["vox_m"])
+        s_gpu = got["voxel_ratio"][k, j, i]
+        assert np.isnan(s_gpu) == (not meets.any())
+        if meets.any():
+            s_ref = D.bisect_ratio(rho, float(grid["target"][k, j, i]), cfg["iters"])
+            assert _ratio_close(rho, s_gpu, s_ref, tol_s=1e-3, tol_rho=1e-4)
