@@ -317,6 +317,75 @@ def run_hatch(steps, warmup):
             "d2h_bytes_per_step": out["segments"] * 12 + (cfg["n_layers"] + 1) * 8}
 
 
+def run_density(steps, warmup):
+    """Density matching (Sec. 5.5) of a 93,750-tetrahedron Kuhn mesh of a
+    100 mm box against graded targets on 50^3 voxels of 2 mm: wall time of
+    csl_density_match (host mesh in, host lattice out), the lattice it builds,
+    and how well the result's volume fraction (Eq. 9, the same 8^3 smoothed
+    samples per voxel) matches the targets. The oracle's time on the 48-
+    tetrahedron case stands beside the GPU's on the same case."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    import synth
+    from paper_2101_05031_gb300 import volume_fraction
+
+    def call(cfg):
+        return cs.density_match(cfg["nodes"], cfg["tets"], cfg["grid"], r_min=cfg["r_min"],
+                                tet_n=cfg["tet_n"], vox_m=cfg["vox_m"],
+                                max_depth=cfg["max_depth"], iters=cfg["iters"])
+
+    def wall(cfg, n_steps, n_warm):
+        for _ in range(n_warm):
+            call(cfg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_steps):
+            res = call(cfg)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n_steps * 1e3, res
+
+    cfg = synth.density_config()
+    ms, res = wall(cfg, steps, warmup)
+    grid = cfg["grid"]
+    r_min = cfg["r_min"]
+    d = grid["dims"]
+    cells = dict(origin=grid["origin"], h=grid["h"], dims=d, m=8, T=0.01)
+    tgt = grid["target"]
+
+    def error(radius):
+        lat = cs.Lattice(res["nodes"], res["edges"], radius, R=6.0 * r_min, C=1.0)
+        vf = torch.empty((d[2], d[1], d[0]), device="cuda")
+        volume_fraction(lat, cells, out=vf)
+        err = vf.cpu().numpy() - tgt
+        return {"mean_signed": float(np.mean(err)), "mean_abs": float(np.mean(np.abs(err))),
+                "median_rel": float(np.median(np.abs(err) / tgt)),
+                "within_10pct": float(np.mean(np.abs(err) <= 0.1 * tgt))}
+
+    small = synth.density_config(small=True)
+    gpu_small_ms, _ = wall(small, 3, 1)
+    from oracle import density as D
+    t0 = time.perf_counter()
+    D.density_match(small["nodes"], small["tets"], small["grid"], r_min=small["r_min"],
+                    tet_n=small["tet_n"], vox_m=small["vox_m"], max_depth=small["max_depth"],
+                    iters=small["iters"])
+    oracle_small_s = time.perf_counter() - t0
+    n_in = int(cfg["tets"].shape[0])
+    return {"workload": cfg["name"], "ms_per_step": ms,
+            "input_tets_per_s": n_in / (ms / 1e3),
+            "leaf_tets": int(res["tets"].shape[0]), "struts": int(res["edges"].shape[0]),
+            "subdivided": int(res["n_subdivided"]),
+            "depth_counts": np.bincount(res["depth"]).tolist(),
+            "density_error": {"final": error(res["radius"]),
+                              "after_step3": error(2 * r_min * res["step3_ratio"]),
+                              "basis": "volume fraction of the lattice on the voxels (Eq. 9, "
+                                       "8^3 samples, T = 0.01 C) minus the target"},
+            "host_topology_ms": float(res["host_ms"]), "call_ms": float(res["wall_ms"]),
+            "small_case": {"workload": small["name"], "gpu_ms": gpu_small_ms,
+                           "cpu_baseline": {"seconds": oracle_small_s, "cores": 1,
+                                            "kind": "oracle", "sample": "the whole small case"}}}
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args, cfg, rank, world):
@@ -356,13 +425,14 @@ def main():
                     help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
-    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch"],
+    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density"],
                     help="run only one of the extra lines and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
-        fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch, "hatch": run_hatch}[args.only]
+        fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch, "hatch": run_hatch,
+              "density": run_density}[args.only]
         print(json.dumps(fn(args.steps, args.warmup)), flush=True)
         return
 
@@ -555,6 +625,7 @@ def main():
         line["volume_fraction"] = run_vf(args.steps, args.warmup)
         line["batched_64"] = run_batch(args.steps, args.warmup)
         line["zigzag_infill_10M"] = run_hatch(args.steps, args.warmup)
+        line["density_matching"] = run_density(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:

@@ -493,6 +493,8 @@ typedef struct csl_dm_result {
     int64_t n_voxels;
     float* voxel_ratio;      /* [nz][ny][nx]; NaN where no edge meets the voxel */
     int64_t n_subdivided;    /* tetrahedra split over all levels */
+    double host_ms;          /* time in the host-side topology edits and bookkeeping */
+    double wall_ms;          /* time of the whole call */
 } csl_dm_result;
 
 /*

@@ -78,7 +78,7 @@ class DmResult(ctypes.Structure):
                 ("radius", c_vp), ("step3_ratio", c_vp), ("n_tets", c_i64), ("tets", c_vp),
                 ("tet_depth", c_vp), ("tet_target", c_vp), ("tet_rho_star", c_vp),
                 ("tet_ratio", c_vp), ("n_voxels", c_i64), ("voxel_ratio", c_vp),
-                ("n_subdivided", c_i64)]
+                ("n_subdivided", c_i64), ("host_ms", c_f64), ("wall_ms", c_f64)]
 
 
 class CellsDesc(ctypes.Structure):

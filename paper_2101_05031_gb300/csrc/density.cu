@@ -21,7 +21,7 @@
 
 #include <algorithm>
 #include <array>
-#include <unordered_map>
+#include <chrono>
 #include <vector>
 
 #include "common.cuh"
@@ -63,44 +63,35 @@ __device__ __forceinline__ float strut_R4I(float px, float py, float pz, float4 
     return segment_term_R4(t0, h2, u.w);
 }
 
-// Sum over the block, the same fixed order in every call; every thread gets it.
-__device__ __forceinline__ float block_sum(float v, float* s_part) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float t = 0.0f;
-#pragma unroll
-    for (int w = 0; w < kDmThreads / 32; ++w) t += s_part[w];
-    __syncthreads();
-    return t;
-}
-
 // Mean of sigma((F + W J - C) / T) over the n samples held in shared memory.
-__device__ __forceinline__ float mean_density(const float* F, const float* J, int n, float W,
-                                              const DmConst& c, float* s_part) {
+// The same mean by one warp (lane-strided samples, butterfly sum: every lane
+// gets the same value, in a fixed order).
+__device__ __forceinline__ float warp_mean_density(const float* F, const float* J, int n, float W,
+                                                   const DmConst& c) {
     float acc = 0.0f;
-    for (int k = threadIdx.x; k < n; k += kDmThreads) {
+    for (int k = threadIdx.x & 31; k < n; k += 32) {
         const float f = F ? F[k] : 0.0f;
         const float x = (f + W * J[k] - c.Cf) * c.inv_T;
         acc += 1.0f / (1.0f + expf(-x));
     }
-    return block_sum(acc, s_part) / (float)n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc / (float)n;
 }
 
 // The ratio s in [1/2, 2] at which the density reaches `target` (the end
-// points when it is out of reach, else `iters` halvings); *rho_hi = density at
-// s = 2.
-__device__ float bisect_ratio(const float* F, const float* J, int n, float target,
-                              const DmConst& c, float* s_part, float* rho_hi) {
-    const float r_hi = mean_density(F, J, n, weight_R4(c.r0 * 2.0, c), c, s_part);
+// points when it is out of reach, else `iters` halvings), by one warp;
+// *rho_hi = density at s = 2.
+__device__ float warp_bisect_ratio(const float* F, const float* J, int n, float target,
+                                   const DmConst& c, float* rho_hi) {
+    const float r_hi = warp_mean_density(F, J, n, weight_R4(c.r0 * 2.0, c), c);
     *rho_hi = r_hi;
     if (r_hi <= target) return 2.0f;
-    if (mean_density(F, J, n, weight_R4(c.r0 * 0.5, c), c, s_part) >= target) return 0.5f;
+    if (warp_mean_density(F, J, n, weight_R4(c.r0 * 0.5, c), c) >= target) return 0.5f;
     float lo = 0.5f, hi = 2.0f;
     for (int it = 0; it < c.iters; ++it) {
         const float mid = 0.5f * (lo + hi);
-        if (mean_density(F, J, n, weight_R4(c.r0 * (double)mid, c), c, s_part) < target)
+        if (warp_mean_density(F, J, n, weight_R4(c.r0 * (double)mid, c), c) < target)
             lo = mid;
         else
             hi = mid;
@@ -204,7 +195,10 @@ __global__ void k_dm_target(const float4* __restrict__ tv, int64_t n_tets, GridC
             const double3 p = make_double3(g.ox + g.h * ((double)i + 0.5),
                                            g.oy + g.h * ((double)j + 0.5),
                                            g.oz + g.h * ((double)k + 0.5));
-            if (contains(v, D, p)) {
+            // a centre outside the bounding box cannot be contained
+            const bool in_box = p.x >= xmin && p.x <= xmax && p.y >= ymin && p.y <= ymax &&
+                                p.z >= zmin && p.z <= zmax;
+            if (in_box && contains(v, D, p)) {
                 found = true;
                 best = fmax(best, (double)tgt[((int64_t)k * g.ny + j) * g.nx + i]);
             }
@@ -227,15 +221,20 @@ __global__ void k_dm_target(const float4* __restrict__ tv, int64_t n_tets, GridC
 
 // ---- Steps 2 and 3: density of a tetrahedron, rho* and the bisection -----
 
-// One block per tetrahedron. coef: the n^3 Kuhn-centroid coefficients; the
-// sample is a1 (v1 - v0) + a2 (v2 - v1) + a3 (v3 - v2) relative to v0.
+// One warp per tetrahedron, J(p) of its six struts in the warp's slice of
+// dynamic shared memory (n_samples floats). coef: the n^3 Kuhn-centroid
+// coefficients; the sample is a1 (v1 - v0) + a2 (v2 - v1) + a3 (v3 - v2)
+// relative to v0.
 __global__ void __launch_bounds__(kDmThreads)
 k_dm_tet(const float4* __restrict__ tv, const double* __restrict__ target, int64_t n_tets,
          const float4* __restrict__ coef, int n_samples, DmConst c, float* __restrict__ rho_star,
          float* __restrict__ ratio) {
-    __shared__ float s_J[kDmMaxSamples];
-    __shared__ float s_part[kDmThreads / 32];
-    for (int64_t t = blockIdx.x; t < n_tets; t += gridDim.x) {
+    extern __shared__ float s_dyn[];
+    const int lane = threadIdx.x & 31;
+    float* s_J = s_dyn + (size_t)(threadIdx.x >> 5) * n_samples;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tets;
+         t += warps) {
         const float4 v0 = tv[4 * t];
         float3 w[4];
         w[0] = make_float3(0.0f, 0.0f, 0.0f);
@@ -257,7 +256,7 @@ k_dm_tet(const float4* __restrict__ tv, const double* __restrict__ target, int64
         const float3 d1 = w[1];
         const float3 d2 = make_float3(w[2].x - w[1].x, w[2].y - w[1].y, w[2].z - w[1].z);
         const float3 d3 = make_float3(w[3].x - w[2].x, w[3].y - w[2].y, w[3].z - w[2].z);
-        for (int k = threadIdx.x; k < n_samples; k += kDmThreads) {
+        for (int k = lane; k < n_samples; k += 32) {
             const float4 a = coef[k];
             const float px = a.x * d1.x + a.y * d2.x + a.z * d3.x;
             const float py = a.x * d1.y + a.y * d2.y + a.z * d3.y;
@@ -267,14 +266,14 @@ k_dm_tet(const float4* __restrict__ tv, const double* __restrict__ target, int64
             for (int e = 0; e < 6; ++e) J += strut_R4I(px, py, pz, ea[e], eu[e], c.R2);
             s_J[k] = J;
         }
-        __syncthreads();
+        __syncwarp();
         float r_hi;
-        const float s = bisect_ratio(nullptr, s_J, n_samples, (float)target[t], c, s_part, &r_hi);
-        if (threadIdx.x == 0) {
+        const float s = warp_bisect_ratio(nullptr, s_J, n_samples, (float)target[t], c, &r_hi);
+        if (lane == 0) {
             rho_star[t] = r_hi;
             ratio[t] = s;
         }
-        __syncthreads();   // s_J is rewritten by the next tetrahedron
+        __syncwarp();   // s_J is rewritten by the next tetrahedron
     }
 }
 
@@ -401,7 +400,6 @@ k_dm_voxel(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ vbeg,
            float* __restrict__ vox_ratio) {
     __shared__ float s_F[kDmMaxSamples], s_J[kDmMaxSamples];
     __shared__ float4 s_a[kDmThreads], s_u[kDmThreads];
-    __shared__ float s_part[kDmThreads / 32];
     const int n = m * m * m;
     const int64_t n_vox = (int64_t)g.nx * g.ny * g.nz;
     const float hf = (float)g.h, inv_m = 1.0f / (float)m;
@@ -460,10 +458,12 @@ k_dm_voxel(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ vbeg,
             if (threadIdx.x == 0) vox_ratio[v] = __int_as_float(0x7fc00000);
             continue;
         }
-        float r_hi;
-        const float s = bisect_ratio(s_F, s_J, n, tgt[v], c, s_part, &r_hi);
-        if (threadIdx.x == 0) vox_ratio[v] = s;
-        __syncthreads();
+        if (threadIdx.x < 32) {   // one warp bisects; no block barrier per step
+            float r_hi;
+            const float s = warp_bisect_ratio(s_F, s_J, n, tgt[v], c, &r_hi);
+            if (threadIdx.x == 0) vox_ratio[v] = s;
+        }
+        __syncthreads();   // s_F, s_J are rewritten by the next voxel
     }
 }
 
@@ -486,12 +486,61 @@ __global__ void k_dm_radii(const float* __restrict__ ratio, int64_t n, float r0,
 
 // ---- host: the tetrahedral lattice and its subdivision --------------------
 
+// Edge key (smaller node id << 32 | larger) -> edge id, open addressing with
+// linear probing (node ids < 2^30, so no key equals the empty marker).
+class EdgeMap {
+  public:
+    void reserve(size_t n) {
+        size_t cap = 64;
+        while (cap < 2 * n) cap <<= 1;
+        if (cap > keys_.size()) rehash(cap);
+    }
+    int32_t find(uint64_t k) const {
+        for (size_t i = slot(k);; i = (i + 1) & mask_) {
+            if (keys_[i] == k) return vals_[i];
+            if (keys_[i] == kEmpty) return -1;
+        }
+    }
+    void insert(uint64_t k, int32_t v) {   // k must be absent
+        if (2 * (n_ + 1) > keys_.size()) rehash(keys_.size() * 2);
+        size_t i = slot(k);
+        while (keys_[i] != kEmpty) i = (i + 1) & mask_;
+        keys_[i] = k;
+        vals_[i] = v;
+        ++n_;
+    }
+
+  private:
+    static constexpr uint64_t kEmpty = ~0ull;
+    size_t slot(uint64_t k) const {
+        k ^= k >> 33;   // a 64-bit finaliser mix before masking
+        k *= 0xff51afd7ed558ccdull;
+        k ^= k >> 33;
+        return (size_t)k & mask_;
+    }
+    void rehash(size_t cap) {
+        std::vector<uint64_t> ok;
+        std::vector<int32_t> ov;
+        ok.swap(keys_);
+        ov.swap(vals_);
+        keys_.assign(cap, kEmpty);
+        vals_.assign(cap, -1);
+        mask_ = cap - 1;
+        n_ = 0;
+        for (size_t i = 0; i < ok.size(); ++i)
+            if (ok[i] != kEmpty) insert(ok[i], ov[i]);
+    }
+    std::vector<uint64_t> keys_ = std::vector<uint64_t>(64, kEmpty);
+    std::vector<int32_t> vals_ = std::vector<int32_t>(64, -1);
+    size_t mask_ = 63, n_ = 0;
+};
+
 struct TetLattice {
     std::vector<float> xyz;                 // 3 per node
     std::vector<int2> edges;                // (smaller, larger) node id
     std::vector<int32_t> mid;               // midpoint node once split, else -1
     std::vector<int2> halves;               // the two halves once split
-    std::unordered_map<uint64_t, int32_t> ids;
+    EdgeMap ids;
     std::vector<int4> tets;
     std::vector<std::array<int32_t, 6>> tet_edges;
     std::vector<int32_t> depth;
@@ -503,13 +552,13 @@ struct TetLattice {
     }
     int32_t add_edge(int32_t a, int32_t b) {
         const uint64_t k = key(a, b);
-        auto it = ids.find(k);
-        if (it != ids.end()) return it->second;
+        const int32_t found = ids.find(k);
+        if (found >= 0) return found;
         const int32_t e = (int32_t)edges.size();
         edges.push_back(make_int2(std::min(a, b), std::max(a, b)));
         mid.push_back(-1);
         halves.push_back(make_int2(-1, -1));
-        ids.emplace(k, e);
+        ids.insert(k, e);
         return e;
     }
     std::array<int32_t, 6> edges_of(const int4& t) {
@@ -609,6 +658,15 @@ std::vector<float4> kuhn_table(int n) {
     return out;
 }
 
+// Accumulates the time spent between start() and stop() calls.
+struct HostClock {
+    using clock = std::chrono::steady_clock;
+    double ms = 0.0;
+    clock::time_point t0;
+    void start() { t0 = clock::now(); }
+    void stop() { ms += std::chrono::duration<double, std::milli>(clock::now() - t0).count(); }
+};
+
 template <class T>
 void upload(DevBuf& d, const std::vector<T>& h, cudaStream_t s) {
     d.ensure(std::max<size_t>(h.size() * sizeof(T), 16), s);
@@ -639,6 +697,9 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
                                         const csl_dm_params* p, void* stream,
                                         csl_dm_result** out) {
     try {
+        HostClock wall, host;
+        wall.start();
+        host.start();
         if (!out || !vox || !p) fail(CSL_ERR_INVALID_ARG, "NULL argument");
         *out = nullptr;
         if (n_nodes < 0 || n_tets < 0) fail(CSL_ERR_INVALID_ARG, "negative count");
@@ -690,6 +751,10 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         g.ny = vox->dims[1];
         g.nz = vox->dims[2];
         const int n_samples = p->tet_n * p->tet_n * p->tet_n;
+        // warps per block of the tetrahedron kernel: their J slices fit 48 KB
+        const int tet_warps = std::max(1, std::min(kDmThreads / 32, 12288 / n_samples));
+        const int tet_threads = 32 * tet_warps;
+        const size_t tet_smem = (size_t)tet_warps * n_samples * sizeof(float);
 
         // the mesh and its edges, numbered in (smaller, larger) node-id order
         TetLattice lat;
@@ -704,6 +769,10 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
             }
             std::sort(keys.begin(), keys.end());
             keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+            lat.ids.reserve(keys.size() * 4);
+            lat.edges.reserve(keys.size() * 4);
+            lat.mid.reserve(keys.size() * 4);
+            lat.halves.reserve(keys.size() * 4);
             for (uint64_t k : keys) lat.add_edge((int32_t)(k >> 32), (int32_t)(k & 0xffffffffu));
             for (int64_t t = 0; t < n_tets; ++t) {
                 const int32_t* v = tets + 4 * t;
@@ -711,6 +780,7 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
             }
         }
 
+        host.stop();
         DevBuf d_tgt((size_t)n_vox * sizeof(float), s);
         CSL_CUDA(cudaMemcpyAsync(d_tgt.get(), vox->target, (size_t)n_vox * sizeof(float),
                                  cudaMemcpyHostToDevice, s));
@@ -729,6 +799,7 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         std::vector<double> h_target;
         std::vector<float> h_rho, h_ratio;
         for (int d = 0; d <= p->max_depth && !cand.empty(); ++d) {
+            host.start();
             const int64_t nc = (int64_t)cand.size();
             h_tv.resize((size_t)nc * 4);
             for (int64_t i = 0; i < nc; ++i) {
@@ -738,6 +809,7 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
                     h_tv[4 * i + k] = make_float4(lat.xyz[3 * v[k]], lat.xyz[3 * v[k] + 1],
                                                   lat.xyz[3 * v[k] + 2], 0.0f);
             }
+            host.stop();
             upload(d_tv, h_tv, s);
             d_target.ensure((size_t)nc * sizeof(double), s);
             d_rho.ensure((size_t)nc * sizeof(float), s);
@@ -746,13 +818,14 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
                                                                d_tgt.as<float>(),
                                                                d_target.as<double>());
             CSL_LAUNCH_CHECK("density targets");
-            k_dm_tet<<<(unsigned)std::min<int64_t>(nc, 152 * 8), kDmThreads, 0, s>>>(
+            k_dm_tet<<<grid_for(nc * 32, tet_threads), tet_threads, tet_smem, s>>>(
                 d_tv.as<float4>(), d_target.as<double>(), nc, d_coef.as<float4>(), n_samples, c,
                 d_rho.as<float>(), d_ratio.as<float>());
             CSL_LAUNCH_CHECK("tetrahedron densities");
             download(h_target, d_target, nc, s);
             download(h_rho, d_rho, nc, s);
             download(h_ratio, d_ratio, nc, s);
+            host.start();
             std::vector<int32_t> next;
             for (int64_t i = 0; i < nc; ++i) {
                 const int32_t t = cand[i];
@@ -770,7 +843,9 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
             rho_star.resize(lat.tets.size());
             tet_ratio.resize(lat.tets.size());
             cand.swap(next);
+            host.stop();
         }
+        host.start();
 
         // the final edges (unsplit, in creation order) and the leaves
         const int64_t n_e = (int64_t)lat.edges.size();
@@ -802,6 +877,7 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
                 }
             }
         }
+        host.stop();
         DevBuf d_pt, d_ps, d_lr, d_r3((size_t)std::max<int64_t>(n_seg, 1) * 4, s);
         upload(d_pt, pair_tet, s);
         upload(d_ps, pair_seg, s);
@@ -824,12 +900,14 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         }
 
         // Step 4: voxel-edge pairs, the per-voxel ratio, the per-edge minimum
+        host.start();
         std::vector<float4> h_sa(n_seg), h_sb(n_seg);
         for (int64_t i = 0; i < n_seg; ++i) {
             const int2 ab = lat.edges[segs[i]];
             h_sa[i] = make_float4(lat.xyz[3 * ab.x], lat.xyz[3 * ab.x + 1], lat.xyz[3 * ab.x + 2], 0.f);
             h_sb[i] = make_float4(lat.xyz[3 * ab.y], lat.xyz[3 * ab.y + 1], lat.xyz[3 * ab.y + 2], 0.f);
         }
+        host.stop();
         DevBuf d_sa, d_sb;
         upload(d_sa, h_sa, s);
         upload(d_sb, h_sb, s);
@@ -892,6 +970,7 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         download(h_vr, d_vr, n_vox, s);
 
         // the result, in page-locked host blocks
+        host.start();
         std::vector<int32_t> h_edges((size_t)n_seg * 2), h_tets((size_t)n_leaf * 4), h_depth(n_leaf);
         std::vector<double> h_tt(n_leaf);
         std::vector<float> h_rs(n_leaf);
@@ -927,6 +1006,10 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         r->n_voxels = n_vox;
         r->voxel_ratio = (float*)host_copy(h_vr.data(), h_vr.size() * 4);
         r->n_subdivided = n_split;
+        host.stop();
+        wall.stop();
+        r->host_ms = host.ms;
+        r->wall_ms = wall.ms;
         *out = r;
         return CSL_OK;
     } catch (const Error& e) {

@@ -18,7 +18,7 @@ def density_match(nodes, tets, grid, *, r_min: float, R: float = 0.0, C: float =
     (3,), h, dims (nx, ny, nz) and target float32 [nz, ny, nx]. R = 0 takes
     1.5 x the doubled base radius (6 r_min). Returns numpy arrays: nodes,
     edges, radius, step3_ratio, tets, depth, target, rho_star, tet_ratio,
-    voxel_ratio [nz, ny, nx], and n_subdivided."""
+    voxel_ratio [nz, ny, nx], n_subdivided, host_ms and wall_ms."""
     nodes = np.ascontiguousarray(nodes, dtype=np.float32).reshape(-1, 3)
     tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     dims = tuple(int(v) for v in grid["dims"])
@@ -58,6 +58,7 @@ def density_match(nodes, tets, grid, *, r_min: float, R: float = 0.0, C: float =
             rho_star=arr(r.tet_rho_star, f32, r.n_tets),
             tet_ratio=arr(r.tet_ratio, f32, r.n_tets),
             voxel_ratio=arr(r.voxel_ratio, f32, r.n_voxels, (dims[2], dims[1], dims[0])),
-            n_subdivided=int(r.n_subdivided))
+            n_subdivided=int(r.n_subdivided), host_ms=float(r.host_ms),
+            wall_ms=float(r.wall_ms))
     finally:
         lib.csl_dm_result_free(out)

@@ -67,8 +67,9 @@ def graded_target_grid(lo, hi, h: float, scale=(0.05, 0.35), period: float = 50.
 
 def density_config(small: bool = False):
     """Density-matching workload. Full: a 100 mm box of 4 mm cubes (25^3 x 6 =
-    93,750 tetrahedra) with 2 mm voxels (50^3); small: 2^3 cubes (48
-    tetrahedra) with 3^3 voxels. r_min = 0.1 mm (base radius 0.2 mm)."""
+    93,750 tetrahedra) with 5 mm voxels (20^3), the designer's grid coarser
+    than the lattice; small: 2^3 cubes (48 tetrahedra) with 3^3 voxels.
+    r_min = 0.1 mm (base radius 0.2 mm)."""
     if small:
         nodes, tets = kuhn_tet_mesh((2, 2, 2), 4.0, 0.1, seed=SEED_BASE + 6)
         grid = graded_target_grid((0.0, 0.0, 0.0), (8.0, 8.0, 8.0), 8.0 / 3.0,
@@ -77,8 +78,8 @@ def density_config(small: bool = False):
                     nodes=nodes, tets=tets, grid=grid, r_min=0.1, tet_n=4, vox_m=4,
                     max_depth=2, iters=24)
     nodes, tets = kuhn_tet_mesh((25, 25, 25), 4.0, 0.1, seed=SEED_BASE + 6)
-    grid = graded_target_grid((0.0, 0.0, 0.0), (100.0, 100.0, 100.0), 2.0)
+    grid = graded_target_grid((0.0, 0.0, 0.0), (100.0, 100.0, 100.0), 5.0)
     return dict(name="Kuhn tetrahedral mesh 25^3 cubes of 4 mm (93,750 tetrahedra), "
-                     "50^3 voxels of 2 mm",
+                     "20^3 voxels of 5 mm",
                 nodes=nodes, tets=tets, grid=grid, r_min=0.1, tet_n=8, vox_m=8, max_depth=3,
                 iters=24)
