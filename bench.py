@@ -386,6 +386,47 @@ def run_density(steps, warmup):
                                             "kind": "oracle", "sample": "the whole small case"}}}
 
 
+def run_support_opt(steps, warmup):
+    """Vertex re-positioning for self-support (Eq. 16-17) on a 50^3-cube Kuhn
+    mesh of 2 mm cubes (750,000 tetrahedra, 132,651 nodes), printing along z,
+    up to 100 rounds: wall time of csl_support_optimize (host mesh in, host
+    nodes out) and Gamma / Psi before and after; the oracle's time on the
+    6^3-cube mesh beside the GPU's."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    import synth
+    nodes, tets = synth.kuhn_tet_mesh((50, 50, 50), 2.0, 0.15, seed=synth.SEED_BASE + 7)
+
+    def wall(nd, tt, n_steps, n_warm):
+        for _ in range(n_warm):
+            cs.support_optimize(nd, tt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_steps):
+            res = cs.support_optimize(nd, tt)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / n_steps * 1e3, res
+
+    ms, res = wall(nodes, tets, steps, warmup)
+    small_n, small_t = synth.kuhn_tet_mesh((6, 6, 6), 4.0, 0.15, seed=synth.SEED_BASE + 7)
+    small_ms, _ = wall(small_n, small_t, 3, 1)
+    from oracle import support_opt as P
+    t0 = time.perf_counter()
+    P.optimize(small_n, small_t)
+    oracle_s = time.perf_counter() - t0
+    return {"workload": "Kuhn tetrahedral mesh 50^3 cubes of 2 mm (750,000 tetrahedra), t_P = z",
+            "ms_per_step": ms, "rounds": res["rounds"], "moves": res["moves"],
+            "colours": res["n_colours"],
+            "ms_per_round": ms / max(res["rounds"], 1),
+            "gamma": [res["gamma_before"], res["gamma_after"]],
+            "psi_percent": [res["psi_before"], res["psi_after"]],
+            "small_case": {"workload": "Kuhn mesh 6^3 cubes of 4 mm (1,296 tetrahedra)",
+                           "gpu_ms": small_ms,
+                           "cpu_baseline": {"seconds": oracle_s, "cores": 1, "kind": "oracle",
+                                            "sample": "the whole small case"}}}
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args, cfg, rank, world):
@@ -425,14 +466,14 @@ def main():
                     help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
-    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density"],
+    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density", "support"],
                     help="run only one of the extra lines and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
         fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch, "hatch": run_hatch,
-              "density": run_density}[args.only]
+              "density": run_density, "support": run_support_opt}[args.only]
         print(json.dumps(fn(args.steps, args.warmup)), flush=True)
         return
 
@@ -626,6 +667,7 @@ def main():
         line["batched_64"] = run_batch(args.steps, args.warmup)
         line["zigzag_infill_10M"] = run_hatch(args.steps, args.warmup)
         line["density_matching"] = run_density(args.steps, args.warmup)
+        line["support_optimisation"] = run_support_opt(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:

@@ -449,6 +449,50 @@ csl_status csl_debug_wait_timeout(uint32_t polls, void* stream);
  */
 csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* stream);
 
+/* ---- vertex position optimisation for self-support (Sec. 5.3.2) ---------- */
+
+typedef struct csl_po_params {
+    double t_p[3];        /* printing direction (nonzero; normalised here) */
+    double alpha;         /* self-supporting angle in [0, pi/2] (pi/4 in the paper) */
+    double a[6];          /* g(theta) = sum_i a_i theta^i for theta > alpha (Eq. 12) */
+    double step;          /* first trial step, in units of tau0 (> 0) */
+    double ball;          /* radius of the allowed ball around the initial position, in tau0 */
+    double min_volume;    /* an incident tetrahedron keeps this share of its volume, [0, 1) */
+    int32_t backtracks;   /* step halvings per visit, 0..60 */
+    int32_t max_rounds;   /* 0..100000 */
+} csl_po_params;
+
+typedef struct csl_po_result {
+    int32_t rounds;        /* rounds run (the last one moved nothing, unless max_rounds) */
+    int32_t n_colours;     /* colours of the greedy colouring */
+    int64_t moves;         /* accepted moves over all rounds */
+    double gamma_before, psi_before, gamma_after, psi_after;   /* Eq. 13-14 of the mesh's edges */
+} csl_po_result;
+
+/*
+ * csl_support_optimize -- vertex re-positioning for self-support (Sec. 5.3.2,
+ * Eq. 16-17). Every interior vertex of the tetrahedral mesh moves along
+ * -grad J(v), J(v) = sum_{e at v} r_e L_e g(theta_e) / sum_{e at v} r_e L_e,
+ * theta_e = arccos |u_e . t_P| (Eq. 11), by step * tau0 halved up to
+ * `backtracks` times until the new position lies within ball * tau0 of the
+ * initial one (tau0: the initial distance to the faces opposite the vertex, the
+ * inscribed sphere of Eq. 17), keeps every incident tetrahedron's orientation
+ * and min_volume of its volume, and lowers J. Vertices on the mesh boundary
+ * stay. The paper's one-by-one order is a greedy colouring (vertex order,
+ * smallest free colour): colour by colour, vertices by index; each colour is
+ * one parallel step with the result of the sequential sweep. Rounds repeat
+ * until none moves or max_rounds. FP64 throughout.
+ * nodes: HOST float [n_nodes][3], updated in place; tets: HOST int32
+ * [n_tets][4]; radius: HOST float per edge of the distinct tetrahedron edges
+ * sorted by (smaller, larger) node id, or NULL for equal radii;
+ * moves_per_round: HOST int32 [max_rounds] or NULL. Errors: INVALID_ARG
+ * (index out of range, non-finite value, parameter out of range), CAPACITY.
+ * Synchronises the stream.
+ */
+csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                                const float* radius, const csl_po_params* p, void* stream,
+                                csl_po_result* out, int32_t* moves_per_round);
+
 /* ---- density matching of a tetrahedral lattice (Sec. 5.5) ---------------- */
 
 /* Target densities on a voxel grid: voxel (i, j, k) is the box origin + h *

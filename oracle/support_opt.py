@@ -153,71 +153,91 @@ def plane_distance(p, a, b, c) -> float:
     return abs(px * nx + py * ny + pz * nz) / nn
 
 
-def optimize(nodes, tets, radius=None, *, t_p=(0.0, 0.0, 1.0), alpha=math.pi / 4, a=PAPER_A,
-             step=0.25, ball=0.5, min_volume=0.1, backtracks=8, max_rounds=100):
-    """Returns dict(nodes float64 [N, 3], rounds, moves per round, colours)."""
-    x = np.asarray(nodes, dtype=np.float32).astype(np.float64).copy()
-    tets = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
-    n = x.shape[0]
-    edges = mesh_edges(tets)
-    r = np.ones(edges.shape[0]) if radius is None else np.asarray(radius, np.float32).astype(np.float64)
-    t0 = [float(v) for v in t_p]
-    tn = math.sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2])
-    t = (t0[0] / tn, t0[1] / tn, t0[2] / tn)
-    inc = [[] for _ in range(n)]          # (other vertex, radius)
-    for (p, q), rr in zip(edges, r):
-        inc[p].append((int(q), rr))
-        inc[q].append((int(p), rr))
-    vt = [[] for _ in range(n)]           # (tetrahedron, local index)
-    for ti, tt in enumerate(tets):
-        for k in range(4):
-            vt[int(tt[k])].append((ti, k))
-    fixed = boundary_vertices(tets, n)
-    col = greedy_colours(edges, n)
-    order = [v for c in range(int(col.max()) + 1 if n else 0) for v in range(n)
-             if col[v] == c and not fixed[v]]
-    vol0 = [orient(*(x[int(i)] for i in tt)) for tt in tets]
-    o = x.copy()
-    tau0 = np.zeros(n)
-    for v in order:
-        tau0[v] = min(plane_distance(x[v], *(x[tets[ti][k2]] for k2 in FACES[k]))
-                      for ti, k in vt[v])
+class Star:
+    """The per-vertex data of the optimisation on the mesh as given: incident
+    edges (in edge order) with radii, incident tetrahedra, boundary flags,
+    colours, the initial positions o, tau0 and the tetrahedra's volumes."""
 
-    def allowed(v, p):
-        dx, dy, dz = p[0] - o[v][0], p[1] - o[v][1], p[2] - o[v][2]
-        if math.sqrt(dx * dx + dy * dy + dz * dz) > ball * tau0[v]:
+    def __init__(self, nodes, tets, radius=None, *, t_p=(0.0, 0.0, 1.0), alpha=math.pi / 4,
+                 a=PAPER_A, step=0.25, ball=0.5, min_volume=0.1, backtracks=8):
+        x = np.asarray(nodes, dtype=np.float32).astype(np.float64).copy()
+        self.tets = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
+        n = x.shape[0]
+        self.edges = mesh_edges(self.tets)
+        r = (np.ones(self.edges.shape[0]) if radius is None
+             else np.asarray(radius, np.float32).astype(np.float64))
+        t0 = [float(v) for v in t_p]
+        tn = math.sqrt(t0[0] * t0[0] + t0[1] * t0[1] + t0[2] * t0[2])
+        self.t = (t0[0] / tn, t0[1] / tn, t0[2] / tn)
+        self.alpha, self.a = alpha, a
+        self.step, self.ball, self.min_volume, self.backtracks = step, ball, min_volume, backtracks
+        self.inc = [[] for _ in range(n)]          # (other vertex, radius)
+        for (p, q), rr in zip(self.edges, r):
+            self.inc[p].append((int(q), rr))
+            self.inc[q].append((int(p), rr))
+        self.vt = [[] for _ in range(n)]           # (tetrahedron, local index)
+        for ti, tt in enumerate(self.tets):
+            for k in range(4):
+                self.vt[int(tt[k])].append((ti, k))
+        self.fixed = boundary_vertices(self.tets, n)
+        self.colours = greedy_colours(self.edges, n)
+        self.order = [v for c in range(int(self.colours.max()) + 1 if n else 0) for v in range(n)
+                      if self.colours[v] == c and not self.fixed[v]]
+        self.vol0 = [orient(*(x[int(i)] for i in tt)) for tt in self.tets]
+        self.o = x
+        self.tau0 = np.zeros(n)
+        for v in self.order:
+            self.tau0[v] = min(plane_distance(x[v], *(x[self.tets[ti][k2]] for k2 in FACES[k]))
+                               for ti, k in self.vt[v])
+
+    def allowed(self, v, p, x):
+        o = self.o[v]
+        dx, dy, dz = p[0] - o[0], p[1] - o[1], p[2] - o[2]
+        if math.sqrt(dx * dx + dy * dy + dz * dz) > self.ball * self.tau0[v]:
             return False
-        for ti, k in vt[v]:
-            q = [p if j == k else x[int(tets[ti][j])] for j in range(4)]
+        for ti, k in self.vt[v]:
+            q = [p if j == k else x[int(self.tets[ti][j])] for j in range(4)]
             vol = orient(*q)
-            if not (vol * vol0[ti] > 0.0 and abs(vol) >= min_volume * abs(vol0[ti])):
+            if not (vol * self.vol0[ti] > 0.0 and abs(vol) >= self.min_volume * abs(self.vol0[ti])):
                 return False
         return True
 
+    def move(self, v, x):
+        """The new position of vertex v given the positions x, or None."""
+        others = [x[w] for w, _ in self.inc[v]]
+        radii = [rr for _, rr in self.inc[v]]
+        J0, grad = local_J(x[v], others, radii, self.t, self.alpha, self.a)
+        gn = math.sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2])
+        if gn == 0.0:
+            return None
+        u = [grad[k] / gn for k in range(3)]
+        s = self.step * self.tau0[v]
+        for _ in range(self.backtracks + 1):
+            cand = np.array([x[v][k] - s * u[k] for k in range(3)])
+            if self.allowed(v, cand, x):
+                J1, _ = local_J(cand, others, radii, self.t, self.alpha, self.a)
+                if J1 < J0:
+                    return cand
+            s *= 0.5
+        return None
+
+
+def optimize(nodes, tets, radius=None, *, t_p=(0.0, 0.0, 1.0), alpha=math.pi / 4, a=PAPER_A,
+             step=0.25, ball=0.5, min_volume=0.1, backtracks=8, max_rounds=100):
+    """Returns dict(nodes float64 [N, 3], rounds, moves per round, colours, fixed, edges)."""
+    st = Star(nodes, tets, radius, t_p=t_p, alpha=alpha, a=a, step=step, ball=ball,
+              min_volume=min_volume, backtracks=backtracks)
+    x = st.o.copy()
     moves = []
     for _ in range(max_rounds):
         moved = 0
-        for v in order:
-            others = [x[w] for w, _ in inc[v]]
-            radii = [rr for _, rr in inc[v]]
-            J0, grad = local_J(x[v], others, radii, t, alpha, a)
-            gn = math.sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2])
-            if gn == 0.0:
-                continue
-            u = [grad[k] / gn for k in range(3)]
-            s = step * tau0[v]
-            for _ in range(backtracks + 1):
-                cand = np.array([x[v][k] - s * u[k] for k in range(3)])
-                if not allowed(v, cand):
-                    s *= 0.5
-                    continue
-                J1, _ = local_J(cand, others, radii, t, alpha, a)
-                if J1 < J0:
-                    x[v] = cand
-                    moved += 1
-                    break
-                s *= 0.5
+        for v in st.order:
+            p = st.move(v, x)
+            if p is not None:
+                x[v] = p
+                moved += 1
         moves.append(moved)
         if moved == 0:
             break
-    return dict(nodes=x, rounds=len(moves), moves=moves, colours=col, fixed=fixed, edges=edges)
+    return dict(nodes=x, rounds=len(moves), moves=moves, colours=st.colours, fixed=st.fixed,
+                edges=st.edges)

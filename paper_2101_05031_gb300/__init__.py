@@ -5,10 +5,10 @@ include/cslice.h). This package only marshals arguments to it.
 """
 from ._lib import CslError, load  # noqa: F401
 from .batch import Batch  # noqa: F401
-from .density import density_match  # noqa: F401
+from .density import density_match, support_optimize  # noqa: F401
 from .slicer import ContourSet, DeviceContours, Lattice, last_stats, measure_fp32_peak  # noqa: F401
 
-__all__ = ["Lattice", "Batch", "density_match", "ContourSet", "DeviceContours", "CslError", "load", "last_stats",
+__all__ = ["Lattice", "Batch", "density_match", "support_optimize", "ContourSet", "DeviceContours", "CslError", "load", "last_stats",
            "volume_fraction", "volume_fraction_backward", "VolumeFraction"]
 
 

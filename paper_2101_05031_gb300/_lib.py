@@ -73,6 +73,18 @@ class DmParams(ctypes.Structure):
                 ("max_depth", c_i32), ("iters", c_i32)]
 
 
+class PoParams(ctypes.Structure):
+    _fields_ = [("t_p", c_f64 * 3), ("alpha", c_f64), ("a", c_f64 * 6), ("step", c_f64),
+                ("ball", c_f64), ("min_volume", c_f64), ("backtracks", c_i32),
+                ("max_rounds", c_i32)]
+
+
+class PoResult(ctypes.Structure):
+    _fields_ = [("rounds", c_i32), ("n_colours", c_i32), ("moves", c_i64),
+                ("gamma_before", c_f64), ("psi_before", c_f64), ("gamma_after", c_f64),
+                ("psi_after", c_f64)]
+
+
 class DmResult(ctypes.Structure):
     _fields_ = [("n_nodes", c_i64), ("nodes", c_vp), ("n_edges", c_i64), ("edges", c_vp),
                 ("radius", c_vp), ("step3_ratio", c_vp), ("n_tets", c_i64), ("tets", c_vp),
@@ -144,6 +156,8 @@ SIGNATURES = [
                                   ctypes.POINTER(DmParams), c_vp,
                                   ctypes.POINTER(ctypes.POINTER(DmResult))]),
     ("csl_dm_result_free", None, [ctypes.POINTER(DmResult)]),
+    ("csl_support_optimize", c_i32, [c_vp, c_i64, c_vp, c_i64, c_vp, ctypes.POINTER(PoParams),
+                                     c_vp, ctypes.POINTER(PoResult), c_vp]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),
     ("csl_field_layers_static", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, c_f64, c_f64, c_i32,
                                         ctypes.POINTER(SliceDesc), c_vp, c_vp]),

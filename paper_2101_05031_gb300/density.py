@@ -1,9 +1,11 @@
-"""Density matching of a tetrahedral lattice (csl_density_match, Sec. 5.5):
-argument marshalling only; the densities, bisections and the voxel pass run
+"""Lattice design steps on tetrahedral meshes: density matching
+(csl_density_match, Sec. 5.5) and vertex re-positioning for self-support
+(csl_support_optimize, Sec. 5.3.2). Argument marshalling only; the work runs
 in libcslice.so."""
 from __future__ import annotations
 
 import ctypes
+import math
 
 import numpy as np
 
@@ -62,3 +64,32 @@ def density_match(nodes, tets, grid, *, r_min: float, R: float = 0.0, C: float =
             wall_ms=float(r.wall_ms))
     finally:
         lib.csl_dm_result_free(out)
+
+
+PAPER_A = (-0.02, -0.31, 1.44, -1.11, 0.58, -0.16)   # Eq. 12 for alpha = pi / 4
+
+
+def support_optimize(nodes, tets, radius=None, *, t_p=(0.0, 0.0, 1.0), alpha=math.pi / 4,
+                     coeffs=PAPER_A, step=0.25, ball=0.5, min_volume=0.1, backtracks=8,
+                     max_rounds=100, stream=None) -> dict:
+    """Vertex re-positioning (Eq. 16-17). nodes float32 [N, 3], tets int32
+    [T, 4] (host); radius: float per distinct edge in (smaller, larger) order,
+    or None. Returns nodes (new float32 array), rounds, moves_per_round,
+    n_colours and Gamma / Psi before and after."""
+    x = np.array(nodes, dtype=np.float32, copy=True).reshape(-1, 3)
+    tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    r = None if radius is None else np.ascontiguousarray(radius, dtype=np.float32)
+    prm = _lib.PoParams((ctypes.c_double * 3)(*[float(v) for v in t_p]), float(alpha),
+                        (ctypes.c_double * 6)(*[float(v) for v in coeffs]), float(step),
+                        float(ball), float(min_volume), int(backtracks), int(max_rounds))
+    per_round = np.zeros(max(int(max_rounds), 1), dtype=np.int32)
+    res = _lib.PoResult()
+    _lib.check(_lib.load().csl_support_optimize(
+        x.ctypes.data_as(ctypes.c_void_p), x.shape[0], tets.ctypes.data_as(ctypes.c_void_p),
+        tets.shape[0], r.ctypes.data_as(ctypes.c_void_p) if r is not None else None,
+        ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(res),
+        per_round.ctypes.data_as(ctypes.c_void_p)))
+    return dict(nodes=x, rounds=int(res.rounds), moves_per_round=per_round[:res.rounds].tolist(),
+                moves=int(res.moves), n_colours=int(res.n_colours),
+                gamma_before=res.gamma_before, psi_before=res.psi_before,
+                gamma_after=res.gamma_after, psi_after=res.psi_after)

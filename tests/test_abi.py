@@ -44,7 +44,8 @@ def test_structs_match_header_layout(tmp_path):
                "csl_stats": _lib.Stats, "csl_batch_opts": _lib.BatchOpts,
                "csl_batch_info": _lib.BatchInfo, "csl_hatches": _lib.Hatches,
                "csl_cells": _lib.CellsDesc, "csl_voxels": _lib.Voxels,
-               "csl_dm_params": _lib.DmParams, "csl_dm_result": _lib.DmResult}
+               "csl_dm_params": _lib.DmParams, "csl_dm_result": _lib.DmResult,
+               "csl_po_params": _lib.PoParams, "csl_po_result": _lib.PoResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
@@ -110,6 +111,21 @@ def test_errors_cross_the_abi_as_codes():
     st = lib.csl_density_match(nodes.ctypes.data_as(ctypes.c_void_p), 4,
                                tets.ctypes.data_as(ctypes.c_void_p), 1, ctypes.byref(vox),
                                ctypes.byref(prm), None, ctypes.byref(res))
+    assert st == 1 and b"out of range" in lib.csl_last_error()
+    # vertex re-positioning: parameters and indices before any device call
+    po = _lib.PoParams((ctypes.c_double * 3)(0, 0, 1), 0.785, (ctypes.c_double * 6)(), 0.25, 0.5,
+                       0.1, 8, 10)
+    pr = _lib.PoResult()
+    for field, bad, word in (("step", 0.0, b"step"), ("min_volume", 1.0, b"min_volume"),
+                             ("backtracks", -1, b"backtracks"), ("alpha", 2.0, b"alpha")):
+        p2 = _lib.PoParams.from_buffer_copy(po)
+        setattr(p2, field, bad)
+        st = lib.csl_support_optimize(None, 0, None, 0, None, ctypes.byref(p2), None,
+                                      ctypes.byref(pr), None)
+        assert st == 1 and word in lib.csl_last_error(), field
+    st = lib.csl_support_optimize(nodes.ctypes.data_as(ctypes.c_void_p), 4,
+                                  tets.ctypes.data_as(ctypes.c_void_p), 1, None, ctypes.byref(po),
+                                  None, ctypes.byref(pr), None)
     assert st == 1 and b"out of range" in lib.csl_last_error()
     # the wait test's poll count is checked before any device call
     assert lib.csl_debug_wait_timeout(0, None) == 1
