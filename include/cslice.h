@@ -467,6 +467,8 @@ typedef struct csl_po_result {
     int32_t n_colours;     /* colours of the greedy colouring */
     int64_t moves;         /* accepted moves over all rounds */
     double gamma_before, psi_before, gamma_after, psi_after;   /* Eq. 13-14 of the mesh's edges */
+    double host_ms;        /* time in the host-side setup (edges, adjacency, boundary, colouring) */
+    double wall_ms;        /* time of the whole call */
 } csl_po_result;
 
 /*

@@ -82,7 +82,7 @@ class PoParams(ctypes.Structure):
 class PoResult(ctypes.Structure):
     _fields_ = [("rounds", c_i32), ("n_colours", c_i32), ("moves", c_i64),
                 ("gamma_before", c_f64), ("psi_before", c_f64), ("gamma_after", c_f64),
-                ("psi_after", c_f64)]
+                ("psi_after", c_f64), ("host_ms", c_f64), ("wall_ms", c_f64)]
 
 
 class DmResult(ctypes.Structure):

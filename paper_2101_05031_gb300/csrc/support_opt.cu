@@ -6,7 +6,7 @@
 // inside the inscribed sphere of its star (Eq. 17). The paper visits the
 // vertices one by one; here a greedy colouring (vertex order, smallest colour
 // free among the neighbours) orders them colour by colour. Vertices of one
-// colour share no edge, so each colour is one kernel launch with a thread per
+// colour share no edge, so each colour is one kernel launch with a warp per
 // vertex, and the result equals the sequential sweep in that order.
 //
 // A move goes along -grad J by step * tau0 (tau0: the smallest distance from
@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <vector>
 
 #include "common.cuh"
@@ -47,39 +48,71 @@ __device__ __forceinline__ void g_dg(double th, const PoConst& c, double& g, dou
     }
 }
 
-// J(v) at position (vx, vy, vz) over the vertex's edges [b, e) of the CSR;
-// with grad != nullptr also its gradient.
-__device__ double local_J(double vx, double vy, double vz, const int32_t* __restrict__ nbr,
-                          const double* __restrict__ rad, int64_t b, int64_t e,
-                          const double* __restrict__ pos, const PoConst& c, double* grad) {
+// One warp evaluates J(v) at (vx, vy, vz) over the vertex's edges [b, e) of
+// the CSR: each lane computes the terms of its edges, then the sums are taken
+// in edge order (lane by lane through shuffles), the order of the sequential
+// definition. With grad != nullptr also the gradient. Every lane returns the
+// same values.
+__device__ double warp_J(double vx, double vy, double vz, const int32_t* __restrict__ nbr,
+                         const double* __restrict__ rad, int64_t b, int64_t e,
+                         const double* __restrict__ pos, const PoConst& c, double* grad) {
+    const int lane = threadIdx.x & 31;
     double N = 0.0, D = 0.0;
     double dN[3] = {0.0, 0.0, 0.0}, dD[3] = {0.0, 0.0, 0.0};
     const double tk[3] = {c.tx, c.ty, c.tz};
-    for (int64_t i = b; i < e; ++i) {
-        const int32_t w = nbr[i];
-        const double r = rad[i];
-        const double d[3] = {vx - pos[3 * (int64_t)w], vy - pos[3 * (int64_t)w + 1],
-                             vz - pos[3 * (int64_t)w + 2]};
-        const double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        if (L == 0.0) continue;
-        const double s = d[0] * c.tx + d[1] * c.ty + d[2] * c.tz;
-        const double cs = fmin(fabs(s) / L, 1.0);
-        const double th = acos(cs);
-        double g, dg;
-        g_dg(th, c, g, dg);
-        const double dL[3] = {d[0] / L, d[1] / L, d[2] / L};
-        N += r * L * g;
-        D += r * L;
-        if (!grad) continue;
-        for (int k = 0; k < 3; ++k) dD[k] += r * dL[k];
-        if (g != 0.0 || dg != 0.0) {
-            const double sg = copysign(1.0, s);
-            const double s2 = sqrt(fmax(1.0 - cs * cs, 1e-300));
-            for (int k = 0; k < 3; ++k) {
-                const double dc = (sg * tk[k] - cs * dL[k]) / L;
-                const double dth = -dc / s2;
-                dN[k] += r * (dL[k] * g + L * dg * dth);
+    for (int64_t base = b; base < e; base += 32) {
+        const int64_t i = base + lane;
+        double tN = 0.0, tD = 0.0, tdN[3] = {0.0, 0.0, 0.0}, tdD[3] = {0.0, 0.0, 0.0};
+        bool live = false;
+        if (i < e) {
+            const int32_t w = nbr[i];
+            const double r = rad[i];
+            const double d[3] = {vx - pos[3 * (int64_t)w], vy - pos[3 * (int64_t)w + 1],
+                                 vz - pos[3 * (int64_t)w + 2]};
+            const double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (L != 0.0) {
+                live = true;
+                const double s = d[0] * c.tx + d[1] * c.ty + d[2] * c.tz;
+                const double cs = fmin(fabs(s) / L, 1.0);
+                const double th = acos(cs);
+                double g, dg;
+                g_dg(th, c, g, dg);
+                const double dL[3] = {d[0] / L, d[1] / L, d[2] / L};
+                tN = r * L * g;
+                tD = r * L;
+                if (grad) {
+                    for (int k = 0; k < 3; ++k) tdD[k] = r * dL[k];
+                    if (g != 0.0 || dg != 0.0) {
+                        const double sg = copysign(1.0, s);
+                        const double s2 = sqrt(fmax(1.0 - cs * cs, 1e-300));
+                        for (int k = 0; k < 3; ++k) {
+                            const double dc = (sg * tk[k] - cs * dL[k]) / L;
+                            const double dth = -dc / s2;
+                            tdN[k] = r * (dL[k] * g + L * dg * dth);
+                        }
+                    }
+                }
             }
+        }
+        const int n = (int)min((int64_t)32, e - base);
+        const unsigned live_mask = __ballot_sync(0xffffffffu, live);
+        for (int j = 0; j < n; ++j) {   // edge order
+            const double xN = __shfl_sync(0xffffffffu, tN, j);
+            const double xD = __shfl_sync(0xffffffffu, tD, j);
+            double xdN[3], xdD[3];
+            if (grad)
+                for (int k = 0; k < 3; ++k) {
+                    xdN[k] = __shfl_sync(0xffffffffu, tdN[k], j);
+                    xdD[k] = __shfl_sync(0xffffffffu, tdD[k], j);
+                }
+            if (!((live_mask >> j) & 1u)) continue;   // a zero-length edge adds nothing
+            N += xN;
+            D += xD;
+            if (grad)
+                for (int k = 0; k < 3; ++k) {
+                    dD[k] += xdD[k];
+                    dN[k] += xdN[k];
+                }
         }
     }
     if (D == 0.0) {
@@ -144,7 +177,9 @@ __global__ void k_po_vol0(const int4* __restrict__ tets, int64_t n, const double
     }
 }
 
-// One colour: a thread per vertex of the list (no two share an edge).
+// One colour: a warp per vertex of the list (no two share an edge). The
+// lanes share the edge terms and the incident tetrahedra's checks; the trials
+// of the backtracking run in order.
 __global__ void __launch_bounds__(kPoThreads)
 k_po_move(const int32_t* __restrict__ list, int64_t n, double* __restrict__ pos,
           const double* __restrict__ o, const double* __restrict__ tau0,
@@ -152,40 +187,46 @@ k_po_move(const int32_t* __restrict__ list, int64_t n, double* __restrict__ pos,
           const double* __restrict__ rad, const int64_t* __restrict__ vt_off,
           const int32_t* __restrict__ vt, const int4* __restrict__ tets,
           const double* __restrict__ vol0, PoConst c, unsigned int* moves) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const int32_t v = list[i];
         const int64_t eb = e_off[v], ee = e_off[v + 1];
         double* pv = pos + 3 * (int64_t)v;
+        const double p0 = pv[0], p1 = pv[1], p2 = pv[2];
         double grad[3];
-        const double J0 = local_J(pv[0], pv[1], pv[2], nbr, rad, eb, ee, pos, c, grad);
+        const double J0 = warp_J(p0, p1, p2, nbr, rad, eb, ee, pos, c, grad);
         const double gn = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
         if (gn == 0.0) continue;
         const double u[3] = {grad[0] / gn, grad[1] / gn, grad[2] / gn};
         const double* ov = o + 3 * (int64_t)v;
         const double rb = c.ball * tau0[v];
+        const int64_t tb = vt_off[v], te = vt_off[v + 1];
         double s = c.step * tau0[v];
         for (int it = 0; it <= c.backtracks; ++it, s *= 0.5) {
-            const double cand[3] = {pv[0] - s * u[0], pv[1] - s * u[1], pv[2] - s * u[2]};
+            const double cand[3] = {p0 - s * u[0], p1 - s * u[1], p2 - s * u[2]};
             const double dx = cand[0] - ov[0], dy = cand[1] - ov[1], dz = cand[2] - ov[2];
             if (sqrt(dx * dx + dy * dy + dz * dz) > rb) continue;
             bool ok = true;
-            for (int64_t q = vt_off[v]; q < vt_off[v + 1] && ok; ++q) {
+            for (int64_t q = tb + lane; q < te; q += 32) {
                 const int32_t ti = vt[q] >> 2, k = vt[q] & 3;
                 const int4 t = tets[ti];
                 const int32_t id[4] = {t.x, t.y, t.z, t.w};
                 const double* P[4];
                 for (int j = 0; j < 4; ++j) P[j] = j == k ? cand : pos + 3 * (int64_t)id[j];
                 const double vol = orient(P[0], P[1], P[2], P[3]);
-                ok = vol * vol0[ti] > 0.0 && fabs(vol) >= c.min_volume * fabs(vol0[ti]);
+                ok = ok && vol * vol0[ti] > 0.0 && fabs(vol) >= c.min_volume * fabs(vol0[ti]);
             }
-            if (!ok) continue;
-            const double J1 = local_J(cand[0], cand[1], cand[2], nbr, rad, eb, ee, pos, c, nullptr);
+            if (!__all_sync(0xffffffffu, ok)) continue;
+            const double J1 = warp_J(cand[0], cand[1], cand[2], nbr, rad, eb, ee, pos, c, nullptr);
             if (J1 < J0) {
-                pv[0] = cand[0];
-                pv[1] = cand[1];
-                pv[2] = cand[2];
-                atomicAdd(moves, 1u);
+                __syncwarp();   // every lane has read pv before lane 0 writes it
+                if (lane == 0) {
+                    pv[0] = cand[0];
+                    pv[1] = cand[1];
+                    pv[2] = cand[2];
+                    atomicAdd(moves, 1u);
+                }
                 break;
             }
         }
@@ -268,6 +309,8 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
                                            const csl_po_params* p, void* stream,
                                            csl_po_result* out, int32_t* moves_per_round) {
     try {
+        using clk = std::chrono::steady_clock;
+        const auto t_start = clk::now();
         if (!p || !out) fail(CSL_ERR_INVALID_ARG, "NULL argument");
         if (n_nodes < 0 || n_tets < 0) fail(CSL_ERR_INVALID_ARG, "negative count");
         if ((n_nodes && !nodes) || (n_tets && !tets)) fail(CSL_ERR_INVALID_ARG, "NULL array");
@@ -301,44 +344,8 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
         c.backtracks = p->backtracks;
         cudaStream_t s = (cudaStream_t)stream;
 
-        // edges: the distinct tetrahedron edges in (smaller, larger) order
-        std::vector<uint64_t> keys;
-        keys.reserve((size_t)n_tets * 6);
-        const int le[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-        for (int64_t t = 0; t < n_tets; ++t)
-            for (int e = 0; e < 6; ++e) {
-                const uint32_t a = (uint32_t)tets[4 * t + le[e][0]], b = (uint32_t)tets[4 * t + le[e][1]];
-                keys.push_back(((uint64_t)std::min(a, b) << 32) | std::max(a, b));
-            }
-        std::sort(keys.begin(), keys.end());
-        keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-        const int64_t n_e = (int64_t)keys.size();
-        std::vector<int2> h_edges(n_e);
-        std::vector<double> h_er(n_e);
-        for (int64_t i = 0; i < n_e; ++i) {
-            h_edges[i] = make_int2((int32_t)(keys[i] >> 32), (int32_t)(keys[i] & 0xffffffffu));
-            h_er[i] = radius ? (double)radius[i] : 1.0;
-            if (!(h_er[i] > 0.0) || !isfinite(h_er[i])) fail(CSL_ERR_INVALID_ARG, "radius must be > 0");
-        }
-        // vertex -> (neighbour, radius) in edge order; vertex -> (tetrahedron, corner)
-        std::vector<int64_t> e_off(n_nodes + 1, 0), vt_off(n_nodes + 1, 0);
-        for (const int2& e : h_edges) {
-            ++e_off[e.x + 1];
-            ++e_off[e.y + 1];
-        }
-        for (int64_t v = 0; v < n_nodes; ++v) e_off[v + 1] += e_off[v];
-        std::vector<int32_t> nbr(e_off[n_nodes]);
-        std::vector<double> rad(e_off[n_nodes]);
-        {
-            std::vector<int64_t> fill(e_off.begin(), e_off.end() - 1);
-            for (int64_t i = 0; i < n_e; ++i) {
-                const int2 e = h_edges[i];
-                nbr[fill[e.x]] = e.y;
-                rad[fill[e.x]++] = h_er[i];
-                nbr[fill[e.y]] = e.x;
-                rad[fill[e.y]++] = h_er[i];
-            }
-        }
+        // vertex -> (tetrahedron, corner)
+        std::vector<int64_t> vt_off(n_nodes + 1, 0);
         for (int64_t i = 0; i < 4 * n_tets; ++i) ++vt_off[tets[i] + 1];
         for (int64_t v = 0; v < n_nodes; ++v) vt_off[v + 1] += vt_off[v];
         std::vector<int32_t> vt(vt_off[n_nodes]);
@@ -347,28 +354,87 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
             for (int64_t t = 0; t < n_tets; ++t)
                 for (int k = 0; k < 4; ++k) vt[fill[tets[4 * t + k]]++] = (int32_t)(t * 4 + k);
         }
-        // boundary vertices: on a face that belongs to one tetrahedron
+        // per vertex, its distinct neighbours in ascending order (the edges are
+        // then the pairs (v, w > v) in (v, w) order), and its boundary faces:
+        // a face (v < b < c) is on the boundary when one tetrahedron has it
+        std::vector<int64_t> e_off(n_nodes + 1, 0);
+        std::vector<int32_t> nbr;
+        nbr.reserve((size_t)n_tets * 4);
         std::vector<uint8_t> fixed(n_nodes, 0);
+        std::vector<int64_t> up_off(n_nodes + 1, 0);   // edges (v, w > v) start at up_off[v]
         {
-            const int fc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
-            std::vector<std::array<int32_t, 3>> faces;
-            faces.reserve((size_t)n_tets * 4);
-            for (int64_t t = 0; t < n_tets; ++t)
-                for (int f = 0; f < 4; ++f) {
-                    std::array<int32_t, 3> q = {tets[4 * t + fc[f][0]], tets[4 * t + fc[f][1]],
-                                                tets[4 * t + fc[f][2]]};
-                    std::sort(q.begin(), q.end());
-                    faces.push_back(q);
+            std::vector<int32_t> tmp;
+            std::vector<uint64_t> faces;
+            std::vector<int64_t> stamp(n_nodes, -1);   // stamp[w] == v: w already listed for v
+            for (int64_t v = 0; v < n_nodes; ++v) {
+                tmp.clear();
+                faces.clear();
+                for (int64_t q = vt_off[v]; q < vt_off[v + 1]; ++q) {
+                    const int32_t* tv = tets + 4 * (int64_t)(vt[q] >> 2);
+                    const int k = vt[q] & 3;
+                    for (int j = 0; j < 4; ++j)
+                        if (j != k && tv[j] != v && stamp[tv[j]] != v) {
+                            stamp[tv[j]] = v;
+                            tmp.push_back(tv[j]);
+                        }
+                    for (int f = 0; f < 4; ++f) {   // faces containing v as their smallest id
+                        if (f == k) continue;
+                        int32_t o[2];
+                        int m = 0;
+                        bool smallest = true;
+                        for (int j = 0; j < 4; ++j) {
+                            if (j == f || j == k) continue;
+                            o[m++] = tv[j];
+                            smallest = smallest && tv[j] > v;
+                        }
+                        if (smallest)
+                            faces.push_back(((uint64_t)(uint32_t)std::min(o[0], o[1]) << 32) |
+                                            (uint32_t)std::max(o[0], o[1]));
+                    }
                 }
-            std::sort(faces.begin(), faces.end());
-            for (size_t i = 0; i < faces.size();) {
-                size_t j = i;
-                while (j < faces.size() && faces[j] == faces[i]) ++j;
-                if (j - i == 1)
-                    for (int32_t v : faces[i]) fixed[v] = 1;
-                i = j;
+                std::sort(tmp.begin(), tmp.end());
+                nbr.insert(nbr.end(), tmp.begin(), tmp.end());
+                e_off[v + 1] = (int64_t)nbr.size();
+                up_off[v + 1] = up_off[v] + (int64_t)(tmp.end() - std::upper_bound(tmp.begin(), tmp.end(), (int32_t)v));
+                std::sort(faces.begin(), faces.end());
+                for (size_t i = 0; i < faces.size();) {
+                    size_t j = i;
+                    while (j < faces.size() && faces[j] == faces[i]) ++j;
+                    if (j - i == 1) {
+                        fixed[v] = 1;
+                        fixed[(int32_t)(faces[i] >> 32)] = 1;
+                        fixed[(int32_t)(faces[i] & 0xffffffffu)] = 1;
+                    }
+                    i = j;
+                }
             }
         }
+        const int64_t n_e = up_off[n_nodes];
+        std::vector<int2> h_edges(n_e);
+        std::vector<double> h_er(n_e);
+        for (int64_t v = 0; v < n_nodes; ++v) {
+            int64_t id = up_off[v];
+            for (int64_t q = e_off[v]; q < e_off[v + 1]; ++q)
+                if (nbr[q] > v) {
+                    h_edges[id] = make_int2((int32_t)v, nbr[q]);
+                    h_er[id] = radius ? (double)radius[id] : 1.0;
+                    if (!(h_er[id] > 0.0) || !isfinite(h_er[id]))
+                        fail(CSL_ERR_INVALID_ARG, "radius must be > 0");
+                    ++id;
+                }
+        }
+        // the radius of every (vertex, neighbour) entry: its edge is (min, max)
+        std::vector<double> rad(nbr.size());
+        for (int64_t v = 0; v < n_nodes; ++v)
+            for (int64_t q = e_off[v]; q < e_off[v + 1]; ++q) {
+                const int32_t w = nbr[q];
+                const int32_t a = std::min((int32_t)v, w), b = std::max((int32_t)v, w);
+                const int32_t* lo = nbr.data() + e_off[a];
+                const int32_t* hi = nbr.data() + e_off[a + 1];
+                const int32_t* first_up = std::upper_bound(lo, hi, a);
+                const int64_t rank = std::lower_bound(first_up, hi, b) - first_up;
+                rad[q] = h_er[up_off[a] + rank];
+            }
         // greedy colouring in vertex order
         std::vector<int32_t> col(n_nodes, -1);
         int32_t n_col = 0;
@@ -399,6 +465,8 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
                 if (!fixed[v]) list[fill[col[v]]++] = (int32_t)v;
         }
 
+        const double host_ms =
+            std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
         std::vector<double> h_pos(3 * n_nodes);
         for (int64_t i = 0; i < 3 * n_nodes; ++i) h_pos[i] = (double)nodes[i];
         std::vector<int4> h_tets(n_tets);
@@ -440,7 +508,7 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
             for (int32_t k = 0; k < n_col; ++k) {
                 const int64_t b = col_off[k], n = col_off[k + 1] - b;
                 if (!n) continue;
-                k_po_move<<<grid_for(n, kPoThreads), kPoThreads, 0, s>>>(
+                k_po_move<<<grid_for(n * 32, kPoThreads), kPoThreads, 0, s>>>(
                     d_list.as<int32_t>() + b, n, d_pos.as<double>(), d_o.as<double>(),
                     d_tau.as<double>(), d_eoff.as<int64_t>(), d_nbr.as<int32_t>(),
                     d_rad.as<double>(), d_vtoff.as<int64_t>(), d_vt.as<int32_t>(),
@@ -457,6 +525,8 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
         metrics(d_edges, d_er, n_e, d_pos, c, d_part, d_tot, s, &r.gamma_after, &r.psi_after);
         if (n_nodes) read_to_host(h_pos.data(), d_pos.get(), h_pos.size() * 8, s);
         for (int64_t i = 0; i < 3 * n_nodes; ++i) nodes[i] = (float)h_pos[i];
+        r.host_ms = host_ms;
+        r.wall_ms = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
         *out = r;
         return CSL_OK;
     } catch (const Error& e) {

@@ -92,4 +92,5 @@ def support_optimize(nodes, tets, radius=None, *, t_p=(0.0, 0.0, 1.0), alpha=mat
     return dict(nodes=x, rounds=int(res.rounds), moves_per_round=per_round[:res.rounds].tolist(),
                 moves=int(res.moves), n_colours=int(res.n_colours),
                 gamma_before=res.gamma_before, psi_before=res.psi_before,
-                gamma_after=res.gamma_after, psi_after=res.psi_after)
+                gamma_after=res.gamma_after, psi_after=res.psi_after, host_ms=res.host_ms,
+                wall_ms=res.wall_ms)
