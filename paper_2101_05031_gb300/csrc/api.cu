@@ -32,8 +32,11 @@ SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
     const int64_t plane = (int64_t)d.nx * d.ny;
     int chunk = d.chunk_layers;
     if (chunk == 0) {
-        // about 1 GiB of Sigma per chunk, whole slabs, at least one slab
-        int64_t c = ((int64_t)1 << 30) / (4 * plane);
+        // about 4 GiB of Sigma per chunk (fewer launches and read-backs per
+        // layer), but at least four chunks when the layers allow, so that two
+        // chunks are in flight; whole slabs, at least one slab
+        int64_t c = ((int64_t)4 << 30) / (4 * plane);
+        c = std::min<int64_t>(c, std::max<int64_t>(d.n_layers / 4, 1));
         c = std::max<int64_t>(S, c - c % S);
         c = std::min<int64_t>(c, std::max(d.n_layers, 1));
         chunk = (int)c;
