@@ -639,8 +639,11 @@ def main():
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         d2h = 0
+        wall = []
         for _ in range(args.e2e_steps):
+            t_step = time.perf_counter()
             d2h = e2e_step()
+            wall.append((time.perf_counter() - t_step) * 1e3)
         a1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -648,7 +651,7 @@ def main():
         line["e2e"] = {"value": whole_job_rate(px_per_step, 1, world, e2e_ms),
                        "unit": "pixel-evals/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "ms_per_step": e2e_ms}
+                       "ms_per_step": e2e_ms, "wall_ms_each_step": wall}
 
     if world == 1 and not args.no_extra:
         # self-support metrics (Eq. 11-14) of the same lattice, printing along z
