@@ -33,10 +33,8 @@ SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
     int chunk = d.chunk_layers;
     if (chunk == 0) {
         // about 4 GiB of Sigma per chunk (fewer launches and read-backs per
-        // layer), but at least four chunks when the layers allow, so that two
-        // chunks are in flight; whole slabs, at least one slab
+        // layer than smaller chunks); whole slabs, at least one slab
         int64_t c = ((int64_t)4 << 30) / (4 * plane);
-        c = std::min<int64_t>(c, std::max<int64_t>(d.n_layers / 4, 1));
         c = std::max<int64_t>(S, c - c % S);
         c = std::min<int64_t>(c, std::max(d.n_layers, 1));
         chunk = (int)c;
