@@ -664,6 +664,26 @@ def main():
         line["support_metrics"] = {"workload": cfg["name"], "gamma": res["v"][0],
                                    "psi_percent": res["v"][1], "ms": sms,
                                    "struts_per_s": cfg["edges"].shape[0] / (sms / 1e3)}
+        # the binary images alone (what a DLP printer takes, Sec. 4): no contours and no
+        # Sigma plane; then the same with the bit-packed images copied to pinned host memory
+        wpr = (cfg["nx"] + 31) // 32
+        mask = torch.empty((cfg["n_layers"], cfg["ny"], wpr), dtype=torch.int32, device="cuda")
+        host_mask = torch.empty(mask.shape, dtype=torch.int32, pin_memory=True)
+        dms = _event_ms(lambda: lat.slice(**kw, contours=False, mask_out=mask), args.steps,
+                        args.warmup, stream)
+
+        def dlp_to_host():
+            lat.slice(**kw, contours=False, mask_out=mask)
+            host_mask.copy_(mask)
+
+        hms = _event_ms(dlp_to_host, args.steps, args.warmup, stream)
+        px = cfg["nx"] * cfg["ny"] * cfg["n_layers"]
+        line["binary_images"] = {"workload": cfg["name"], "ms_per_step": dms,
+                                 "pixel_evals_per_s": px / (dms / 1e3),
+                                 "s_per_slice": dms / 1e3 / cfg["n_layers"],
+                                 "to_host_ms_per_step": hms,
+                                 "d2h_bytes_per_step": int(mask.numel() * 4)}
+        del mask, host_mask
         del lat
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)

@@ -363,7 +363,9 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         const int chunk_alloc = std::min(p.chunk, std::max(d.n_layers, 1));
         const int64_t mask_layer = mask_words_per_layer(d.nx, d.ny);
         for (int b = 0; b < n_par; ++b) {
-            if (!d.sigma_out && d.n_layers > 0)
+            // without contours nothing reads the Sigma plane: the field kernel
+            // then writes only the mask (the binary image) unless sigma_out is set
+            if (!d.sigma_out && want_contours && d.n_layers > 0)
                 sigma_ws[b].alloc((size_t)chunk_alloc * plane * 4, streams[b]);
             if ((want_contours || d.mask_out) && d.n_layers > 0)
                 mask_ws[b].alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
@@ -437,7 +439,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             ChunkGeom g = chunk_geom(L, d, p, first, n);
             cudaStream_t ks = streams[k % n_par];
             float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane
-                                       : sigma_ws[k % n_par].as<float>();
+                                       : sigma_ws[k % n_par].as<float>();   // null: mask only
             {
                 SlabBins bins;
                 timed(st.bin_ms, [&] { bin_chunk(L, g, bins, ks); });

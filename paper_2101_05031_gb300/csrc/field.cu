@@ -175,7 +175,7 @@ __device__ __forceinline__ bool field_tile(const csl_rec* __restrict__ recs,
     }
     const int gi = tx * kTile + il, gj = ty * kTile + jl;
     const bool in_grid = gi < c.nx && gj < c.ny;
-    if (in_grid) {
+    if (in_grid && sigma) {   // no Sigma plane when only the mask is wanted
 #pragma unroll
         for (int l = 0; l < S; ++l)
             if (l < nl) sigma[((int64_t)(l0 + l) * c.ny + gj) * c.nx + gi] = acc[l];

@@ -298,6 +298,23 @@ def test_mask_out_is_the_thresholded_field(c1, nx, contours, chunk):
     assert np.array_equal(bits[:, :, :nx].astype(bool)[far], (ref >= cfg["C"])[far])
 
 
+def test_mask_only_slice_gives_the_same_image(c1):
+    """Without contours and without sigma_out no Sigma plane is written; the
+    binary image is the one of the slice that also returns Sigma."""
+    cfg, lat = c1
+    n, nx, ny = 10, 200, 120
+    wpr = (nx + 31) // 32
+    kw = dict(z0=cfg["z0"], dz=cfg["dz"], n_layers=n, x0=cfg["x0"], y0=cfg["y0"], nx=nx, ny=ny,
+              pixel=cfg["pixel"], contours=False)
+    sig = torch.empty((n, ny, nx), dtype=torch.float32, device="cuda")
+    mk1 = torch.full((n, ny, wpr), -1, dtype=torch.int32, device="cuda")
+    mk2 = torch.full((n, ny, wpr), -1, dtype=torch.int32, device="cuda")
+    lat.slice(**kw, sigma_out=sig, mask_out=mk1)
+    lat.slice(**kw, mask_out=mk2)
+    torch.cuda.synchronize()
+    assert torch.equal(mk1, mk2) and int(mk1.count_nonzero()) > 0
+
+
 def test_isolated_strut_circle_on_gpu():
     """The cross-section of an isolated long strut is the circle of its radius."""
     cs = _cslice()
