@@ -427,6 +427,47 @@ def run_support_opt(steps, warmup):
                                             "sample": "the whole small case"}}}
 
 
+def run_render(steps, warmup):
+    """Depth image of the implicit solid (csl_render_depth) of the 430k-strut
+    Freudenthal lattice at 1920 x 1080, samples every R/8 along the rays; the
+    oracle's time for a 32 x 24 image of the cubic+BCC lattice beside the
+    GPU's for the same image."""
+    import torch
+
+    import paper_2101_05031_gb300 as cs
+    import synth
+    cfg = synth.config(2)
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    lo, hi = synth.lattice_bbox(cfg["nodes"])
+    c = 0.5 * (lo + hi)
+    ext = float(np.max(hi - lo))
+    cam = dict(eye=(float(c[0] + 1.1 * ext), float(c[1] - 0.8 * ext), float(c[2] + 0.7 * ext)),
+               target=(float(c[0]), float(c[1]), float(c[2])), up=(0.0, 0.0, 1.0), fov_y=0.6,
+               width=1920, height=1080)
+    step = cfg["R"] / 8
+    out = torch.empty((1080, 1920), dtype=torch.float32, device="cuda")
+    ms = _event_ms(lambda: lat.render_depth(**cam, step=step, refine=20, out=out), steps, warmup,
+                   torch.cuda.current_stream())
+    hits = int(torch.isfinite(out).sum())
+    small = synth.config(1)
+    lat1 = cs.Lattice(small["nodes"], small["edges"], small["radius"], R=small["R"])
+    cam1 = dict(eye=(31.0, -17.0, 24.0), target=(10.0, 10.0, 9.0), up=(0.0, 0.0, 1.0), fov_y=0.9,
+                width=32, height=24)
+    small_ms = _event_ms(lambda: lat1.render_depth(**cam1, step=0.05, refine=20), 3, 1,
+                         torch.cuda.current_stream())
+    from oracle import render as V
+    t0 = time.perf_counter()
+    V.render(small["nodes"], small["edges"], small["radius"], R=small["R"], C=1.0, step=0.05,
+             refine=20, **cam1)
+    oracle_s = time.perf_counter() - t0
+    return {"workload": cfg["name"].split(",")[0] + ", 1920 x 1080 depth image, step R/8",
+            "ms_per_step": ms, "rays_per_s": 1920 * 1080 / (ms / 1e3), "hits": hits,
+            "small_case": {"workload": "cubic+BCC 812 struts, 32 x 24 image, step 0.05 mm",
+                           "gpu_ms": small_ms,
+                           "cpu_baseline": {"seconds": oracle_s, "cores": 1, "kind": "oracle",
+                                            "sample": "the whole small image"}}}
+
+
 # --------------------------------------------------------------------------- main
 
 def run_reference(args, cfg, rank, world):
@@ -466,14 +507,16 @@ def main():
                     help="skip the 10M-strut and volume-fraction lines")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
-    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density", "support"],
+    ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density", "support",
+                                       "render"],
                     help="run only one of the extra lines and print it (profiling runs)")
     args = ap.parse_args()
     if args.only:
         import torch
         torch.cuda.set_device(0)
         fn = {"10M": run_10m, "vf": run_vf, "batched": run_batch, "hatch": run_hatch,
-              "density": run_density, "support": run_support_opt}[args.only]
+              "density": run_density, "support": run_support_opt,
+              "render": run_render}[args.only]
         print(json.dumps(fn(args.steps, args.warmup)), flush=True)
         return
 
@@ -691,6 +734,7 @@ def main():
         line["zigzag_infill_10M"] = run_hatch(args.steps, args.warmup)
         line["density_matching"] = run_density(args.steps, args.warmup)
         line["support_optimisation"] = run_support_opt(args.steps, args.warmup)
+        line["depth_image"] = run_render(args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(cfg)
     if rank == 0:

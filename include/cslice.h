@@ -449,6 +449,31 @@ csl_status csl_debug_wait_timeout(uint32_t polls, void* stream);
  */
 csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* stream);
 
+/* ---- ray casting of the implicit solid (a depth image, no mesh) --------- */
+
+typedef struct csl_camera {
+    double eye[3], target[3], up[3];   /* pinhole camera; up fixes the roll */
+    double fov_y;          /* vertical field of view, radians, in (0, pi) */
+    int32_t width, height; /* pixels; pixel (i, j), j the row from the top */
+    double step;           /* sample spacing along a ray (mm), > 0 */
+    int32_t refine;        /* halvings of the step that holds the surface, 0..60 */
+    int32_t reserved;
+} csl_camera;
+
+/*
+ * csl_render_depth -- the distance along each pixel's unit ray to the solid
+ * {Sigma >= C} (Sec. 3; the paper shows its lattices by ray tracing the
+ * implicit function directly). A ray is sampled at t_in + k * step from where
+ * it enters the lattice's box grown by R; the first sample with Sigma >= C is
+ * refined by `refine` halvings of the preceding step; no such sample: +inf.
+ * Features thinner than a step can be missed. The struts are binned into a
+ * uniform grid of cells of edge >= 2R (empty cells are skipped). depth: DEVICE
+ * float [height][width]. Errors: INVALID_ARG (camera, sizes), CAPACITY (more
+ * than 2^31 strut-cell pairs), OOM. Synchronises the stream.
+ */
+csl_status csl_render_depth(const csl_lattice* lat, const csl_camera* cam, float* depth,
+                            void* stream);
+
 /* ---- vertex position optimisation for self-support (Sec. 5.3.2) ---------- */
 
 typedef struct csl_po_params {

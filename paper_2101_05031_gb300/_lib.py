@@ -73,6 +73,12 @@ class DmParams(ctypes.Structure):
                 ("max_depth", c_i32), ("iters", c_i32)]
 
 
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", c_f64 * 3), ("target", c_f64 * 3), ("up", c_f64 * 3), ("fov_y", c_f64),
+                ("width", c_i32), ("height", c_i32), ("step", c_f64), ("refine", c_i32),
+                ("reserved", c_i32)]
+
+
 class PoParams(ctypes.Structure):
     _fields_ = [("t_p", c_f64 * 3), ("alpha", c_f64), ("a", c_f64 * 6), ("step", c_f64),
                 ("ball", c_f64), ("min_volume", c_f64), ("backtracks", c_i32),
@@ -156,6 +162,7 @@ SIGNATURES = [
                                   ctypes.POINTER(DmParams), c_vp,
                                   ctypes.POINTER(ctypes.POINTER(DmResult))]),
     ("csl_dm_result_free", None, [ctypes.POINTER(DmResult)]),
+    ("csl_render_depth", c_i32, [c_vp, ctypes.POINTER(Camera), c_vp, c_vp]),
     ("csl_support_optimize", c_i32, [c_vp, c_i64, c_vp, c_i64, c_vp, ctypes.POINTER(PoParams),
                                      c_vp, ctypes.POINTER(PoResult), c_vp]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),

@@ -281,6 +281,24 @@ class Lattice:
                                                    ctypes.byref(p), _stream_ptr(stream)))
         return g.value, p.value
 
+    def render_depth(self, *, eye, target, up=(0.0, 0.0, 1.0), fov_y=0.7, width, height,
+                     step, refine=24, out=None, stream=None):
+        """csl_render_depth: distances along the pixels' rays to the solid, a
+        CUDA float32 tensor [height, width] (+inf where a ray misses)."""
+        if out is None:
+            out = torch.empty((int(height), int(width)), dtype=torch.float32, device="cuda")
+        if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+                and out.numel() >= int(width) * int(height)):
+            raise ValueError("out must be a contiguous CUDA float32 tensor of width * height")
+        cam = _lib.Camera((ctypes.c_double * 3)(*[float(v) for v in eye]),
+                          (ctypes.c_double * 3)(*[float(v) for v in target]),
+                          (ctypes.c_double * 3)(*[float(v) for v in up]), float(fov_y),
+                          int(width), int(height), float(step), int(refine), 0)
+        _lib.check(_lib.load().csl_render_depth(self._h, ctypes.byref(cam),
+                                                ctypes.c_void_p(out.data_ptr()),
+                                                _stream_ptr(stream)))
+        return out
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().csl_lattice_free(self._h)

@@ -45,7 +45,8 @@ def test_structs_match_header_layout(tmp_path):
                "csl_batch_info": _lib.BatchInfo, "csl_hatches": _lib.Hatches,
                "csl_cells": _lib.CellsDesc, "csl_voxels": _lib.Voxels,
                "csl_dm_params": _lib.DmParams, "csl_dm_result": _lib.DmResult,
-               "csl_po_params": _lib.PoParams, "csl_po_result": _lib.PoResult}
+               "csl_po_params": _lib.PoParams, "csl_po_result": _lib.PoResult,
+               "csl_camera": _lib.Camera}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cslice.h"', 'int main(void){']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
