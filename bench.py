@@ -300,7 +300,7 @@ def run_hatch(steps, warmup):
     import paper_2101_05031_gb300 as cs
     cfg = workload("graded-10M")
     lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
-    dev = lat.slice(**slice_kwargs(cfg, 0, 1), on_device=True)
+    dev = lat.slice(**slice_kwargs(cfg, 0, 1), on_device=True, edge_ids=True)
     n_lines = int(round(cfg["ny"] * cfg["pixel"] / 0.1))
     y0 = cfg["y0"] + 0.05
     out = {}
@@ -310,7 +310,20 @@ def run_hatch(steps, warmup):
         out["segments"] = int(seg.shape[0])
 
     ms = _event_ms(step, steps, warmup, torch.cuda.current_stream())
-    return {"workload": cfg["name"] + ", scan lines every 0.1 mm", "layers": cfg["n_layers"],
+    # topology-preserving simplification of the same contours (tolerance 0.25 px)
+    simp = {}
+
+    def simplify_step():
+        simp["c"] = dev.simplify(cfg["nx"], cfg["ny"], 0.25 * cfg["pixel"])
+        simp["n"] = simp["c"].n_verts
+        simp["c"].free()
+
+    sms = _event_ms(simplify_step, steps, warmup, torch.cuda.current_stream())
+    out_simplify = {"ms_per_step": sms, "vertices_in": int(dev.n_verts),
+                    "vertices_out": int(simp["n"]), "vertices_per_s": dev.n_verts / (sms / 1e3),
+                    "tolerance_px": 0.25}
+    return {"simplify": out_simplify,
+            "workload": cfg["name"] + ", scan lines every 0.1 mm", "layers": cfg["n_layers"],
             "contour_vertices": int(dev.n_verts), "segments": out["segments"],
             "ms_per_step": ms, "segments_per_s": out["segments"] / (ms / 1e3),
             "vertices_per_s": dev.n_verts / (ms / 1e3),

@@ -449,6 +449,24 @@ csl_status csl_debug_wait_timeout(uint32_t polls, void* stream);
  */
 csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* stream);
 
+/*
+ * csl_simplify_contours -- topology-preserving simplification of device
+ * contours (the paper simplifies its marching-squares boundaries without
+ * creating intersections, Sec. 4). A vertex on grid edge e, at an odd
+ * position of a loop of >= 5 vertices, is dropped when neither grid cell
+ * beside e has a crossing on an edge other than the loop's own (so both cells
+ * hold only this loop, and the chord joining its neighbours stays in their
+ * convex 1 x 2 block) and it lies within tol (mm) of that chord (FP64). Loops,
+ * their order and their heads are kept; every loop keeps >= 3 vertices; no two
+ * segments of a layer cross if none did. in: device contours with edge ids
+ * (CSL_SLICE_CONTOURS_ON_DEVICE | CSL_SLICE_EDGE_IDS) of an nx x ny grid;
+ * out: new device contours with edge ids (csl_contours_free). Errors:
+ * INVALID_ARG (host contours, no edge ids, nx/ny out of range, tol < 0),
+ * CAPACITY (the per-layer edge bitmaps above 16 GiB), OOM. Synchronises.
+ */
+csl_status csl_simplify_contours(const csl_contours* in, int32_t nx, int32_t ny, double tol,
+                                 void* stream, csl_contours** out);
+
 /* ---- ray casting of the implicit solid (a depth image, no mesh) --------- */
 
 typedef struct csl_camera {

@@ -103,6 +103,14 @@ class DeviceContours:
             lib.csl_hatches_free(h)
         return off, seg
 
+    def simplify(self, nx, ny, tol, stream=None):
+        """csl_simplify_contours: new DeviceContours with vertices dropped where
+        that cannot create an intersection (needs edge ids; tol in mm)."""
+        out = ctypes.POINTER(_lib.Contours)()
+        _lib.check(_lib.load().csl_simplify_contours(self._ptr, int(nx), int(ny), float(tol),
+                                                     _stream_ptr(stream), ctypes.byref(out)))
+        return DeviceContours(out)
+
     def free(self):
         if self._ptr is not None:
             _lib.load().csl_contours_free(self._ptr)
