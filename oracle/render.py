@@ -62,10 +62,30 @@ def box_interval(o, d, lo, hi):
     return t0, t1
 
 
+def near_ray(nodes, edges, o, d, R):
+    """Indices of the struts that can reach the ray's line: a strut whose
+    midpoint lies farther than R + half its length from the line contributes
+    nothing anywhere on it."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    a = nodes[edges[:, 0]]
+    b = nodes[edges[:, 1]]
+    m = 0.5 * (a + b)
+    half = 0.5 * np.linalg.norm(b - a, axis=1)
+    q = m - o[None, :]
+    t = q @ d
+    dist = np.linalg.norm(q - t[:, None] * d[None, :], axis=1)
+    return np.nonzero(dist <= R + half)[0]
+
+
 def cast(nodes, edges, radius, o, d, *, R, C=1.0, step, refine=24, lo, hi):
     """Depth of the first hit of one ray (V2), +inf for a miss."""
     iv = box_interval(o, d, lo, hi)
     if iv is None:
+        return math.inf
+    keep = near_ray(nodes, np.asarray(edges), o, d, R)
+    edges = np.asarray(edges)[keep]
+    radius = np.asarray(radius)[keep]
+    if edges.shape[0] == 0:
         return math.inf
     t_in, t_out = iv
     n = int(math.floor((t_out - t_in) / step)) + 1

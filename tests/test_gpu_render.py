@@ -59,3 +59,32 @@ def test_cubic_bcc_against_the_oracle():
             n_bad += 1
     assert n_hit > 100
     assert n_bad <= 0.01 * len(ref), n_bad
+
+
+def test_full_workload_sampled_rays():
+    """The bench's image (430k-strut Freudenthal lattice, 1920 x 1080, step
+    R/8): 40 sampled pixels against the oracle, ray by ray."""
+    import paper_2101_05031_gb300 as cs
+    cfg = synth.config(2)
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    lo, hi = synth.lattice_bbox(cfg["nodes"])
+    c = 0.5 * (lo + hi)
+    ext = float(np.max(hi - lo))
+    cam = dict(eye=(float(c[0] + 1.1 * ext), float(c[1] - 0.8 * ext), float(c[2] + 0.7 * ext)),
+               target=(float(c[0]), float(c[1]), float(c[2])), up=(0.0, 0.0, 1.0), fov_y=0.6,
+               width=1920, height=1080)
+    step = cfg["R"] / 8
+    depth = lat.render_depth(**cam, step=step, refine=20).cpu().numpy()
+    r = synth.rng(29)
+    pix = [(int(r.integers(1080)), int(r.integers(1920))) for _ in range(40)]
+    ref = V.render(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], step=step, refine=20,
+                   pixels=pix, **cam)
+    n_hit = n_bad = 0
+    for (j, i), t in ref.items():
+        g = depth[j, i]
+        if np.isinf(t) and np.isinf(g):
+            continue
+        n_hit += 1
+        n_bad += not (abs(g - t) <= 2e-3)
+    assert n_hit >= 20
+    assert n_bad <= 1, n_bad

@@ -56,3 +56,25 @@ def test_simplify_arguments_and_empty_input():
     empty = lat.slice(n_layers=0, edge_ids=True, **kw)
     out = empty.simplify(cfg["nx"], cfg["ny"], 0.01)
     assert out.n_loops == 0 and out.n_verts == 0
+
+
+def test_full_grid_layers_of_the_10M_workload():
+    """20 layers of the 10M-strut graded lattice at its full 2000 x 2000 grid,
+    simplified as the benchmark does (0.25 px): two sampled layers against the
+    oracle's rule, one of them checked for crossings."""
+    import paper_2101_05031_gb300 as cs
+    nodes, edges, radius, r_ref = synth.adaptive_graded(box=100.0, level_min=4, level_max=7)
+    lat = cs.Lattice(nodes, edges, radius, R=1.5 * r_ref, C=1.0)
+    nx = ny = 2000
+    pixel = 0.05
+    dev = lat.slice(z0=40.1, dz=0.2, n_layers=20, x0=0.0, y0=0.0, nx=nx, ny=ny, pixel=pixel,
+                    on_device=True, edge_ids=True)
+    src = dev.to_host()
+    out = dev.simplify(nx, ny, 0.25 * pixel).to_host()
+    for k in (4, 17):
+        off, eid, xy = _layer_arrays(src, k)
+        goff, geid, gxy = _layer_arrays(out, k)
+        roff, reid, rxy, _ = Z.simplify_layer(off, eid, xy, nx, 0.25 * pixel)
+        assert np.array_equal(goff, roff) and np.array_equal(geid, reid)
+        assert np.array_equal(gxy, rxy)
+        assert len(reid) < 0.8 * len(eid)
