@@ -740,6 +740,30 @@ def main():
                                  "to_host_ms_per_step": hms,
                                  "d2h_bytes_per_step": int(mask.numel() * 4)}
         del mask, host_mask
+        # the same slicing from a host-resident lattice: records in page-locked host
+        # memory, each chunk's z window copied to the device (the out-of-core sweep)
+        t_up = time.perf_counter()
+        lat_h = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"],
+                           host_resident=True)
+        up_s = time.perf_counter() - t_up
+        hr = {}
+
+        def host_resident_step():
+            lat_h.slice(**kw, on_device=True).free()
+            hr["peak"] = cs.last_stats().device_bytes_peak
+
+        hr_ms = _event_ms(host_resident_step, args.steps, args.warmup, stream)
+        ne, nn = int(cfg["edges"].shape[0]), int(cfg["nodes"].shape[0])
+        line["host_resident"] = {
+            "workload": cfg["name"], "ms_per_step": hr_ms,
+            "pixel_evals_per_s": px / (hr_ms / 1e3), "upload_and_prepare_s": up_s,
+            "lattice_device_bytes": nn * 12,
+            "lattice_device_bytes_resident": nn * 12 + ne * (8 + 4 + 32 + 16 + 4 + 4 + 4),
+            "slice_workspace_peak_bytes": int(hr.get("peak", 0)),
+            "basis": "lattice bytes by layout (nodes only when host-resident; nodes, edges, "
+                     "radii and the prepared arrays when resident); the workspace peak from "
+                     "csl_last_stats"}
+        del lat_h
         del lat
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)

@@ -94,6 +94,26 @@ csl_status csl_lattice_upload(const float* nodes_xyz, int64_t n_nodes, const int
                               void* stream, csl_lattice** out);
 
 /*
+ * csl_lattice_upload_streamed -- the same lattice, kept in host memory (the
+ * GPU form of the paper's out-of-core sweep, Sec. 4: only the edges near the
+ * planes being sliced need to be in memory). The inputs are HOST arrays
+ * (params->input_on_device must be 0). The nodes are copied to the device;
+ * the edges are prepared in batches of at most batch_edges (0: 2^24) on the
+ * device, each batch sorted by v_s^z there, and the sorted batches are merged
+ * on the host into the order of one stable sort; the records stay in
+ * page-locked host memory. csl_slice_layers then copies each chunk's z window
+ * of the records to the device, so device memory holds the nodes and two
+ * windows instead of the whole lattice; its results equal those of
+ * csl_lattice_upload bit for bit. Such a lattice serves csl_slice_layers and
+ * csl_lattice_get_info only; the other calls return NOT_READY. Errors as
+ * csl_lattice_upload, plus INVALID_ARG for device inputs or batch_edges < 0.
+ */
+csl_status csl_lattice_upload_streamed(const float* nodes_xyz, int64_t n_nodes,
+                                       const int32_t* edges_ij, const float* radius,
+                                       int64_t n_edges, const csl_params* params,
+                                       int64_t batch_edges, void* stream, csl_lattice** out);
+
+/*
  * csl_lattice_update -- replace node positions and/or radii of an uploaded
  * lattice (same edges), e.g. inside a radius-tuning loop (Sec. 5.4).
  * nodes_xyz (float[n_nodes][3]) and radius (float[n_edges]) are device

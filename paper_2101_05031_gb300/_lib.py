@@ -133,6 +133,8 @@ SIGNATURES = [
     ("csl_last_stats", c_i32, [ctypes.POINTER(Stats)]),
     ("csl_lattice_upload", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, ctypes.POINTER(Params), c_vp,
                                    ctypes.POINTER(c_vp)]),
+    ("csl_lattice_upload_streamed", c_i32, [c_vp, c_i64, c_vp, c_vp, c_i64, ctypes.POINTER(Params),
+                                            c_i64, c_vp, ctypes.POINTER(c_vp)]),
     ("csl_lattice_update", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("csl_lattice_get_info", c_i32, [c_vp, ctypes.POINTER(LatticeInfo)]),
     ("csl_lattice_free", None, [c_vp]),

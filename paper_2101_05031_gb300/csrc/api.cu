@@ -15,6 +15,12 @@ using namespace csl;
 
 namespace csl {
 
+void require_device_resident(const csl_lattice* L) {
+    if (L && L->host_resident)
+        fail(CSL_ERR_NOT_READY,
+             "the lattice is host-resident (csl_lattice_upload_streamed): only slicing streams it");
+}
+
 void require_arg(bool ok, const char* msg) {
     if (!ok) fail(CSL_ERR_INVALID_ARG, msg);
 }
@@ -217,10 +223,53 @@ csl_status csl_lattice_upload(const float* nodes_xyz, int64_t n_nodes, const int
     });
 }
 
+csl_status csl_lattice_upload_streamed(const float* nodes_xyz, int64_t n_nodes,
+                                       const int32_t* edges_ij, const float* radius,
+                                       int64_t n_edges, const csl_params* params,
+                                       int64_t batch_edges, void* stream, csl_lattice** out) {
+    return guard([&] {
+        require(out != nullptr, "out is NULL");
+        *out = nullptr;
+        require(n_nodes >= 0 && n_edges >= 0, "negative size");
+        require(n_edges <= 0x7fffffffLL && n_nodes <= 0x7fffffffLL, "more than 2^31 - 1 items");
+        require(n_nodes == 0 || nodes_xyz != nullptr, "nodes_xyz is NULL");
+        require(n_edges == 0 || (edges_ij != nullptr && radius != nullptr),
+                "edges_ij or radius is NULL");
+        require(batch_edges >= 0, "batch_edges must be >= 0");
+        csl_params p = {0.0, 1.0, CSL_MODE_PHYSICAL, 0};
+        if (params) p = *params;
+        require(p.input_on_device == 0, "a streamed lattice takes host arrays");
+        if (p.C == 0.0) p.C = 1.0;
+        require(isfinite(p.C) && p.C > 0, "C must be > 0");
+        require(p.mode == CSL_MODE_PHYSICAL || p.mode == CSL_MODE_RAW, "unknown mode");
+        require(isfinite(p.R), "R must be finite");
+        cudaStream_t s = (cudaStream_t)stream;
+        csl_lattice* L = new csl_lattice();
+        try {
+            L->n_nodes = n_nodes;
+            L->n_edges = n_edges;
+            L->R = p.R;
+            L->C = p.C;
+            L->mode = p.mode;
+            copy_in(L->nodes, nodes_xyz, (size_t)n_nodes * 12, false, s);
+            L->status.alloc_persistent(4);
+            CSL_CUDA(cudaMemsetAsync(L->status.get(), 0, 4, s));
+            prepare_lattice_streamed(L, edges_ij, radius,
+                                     batch_edges > 0 ? batch_edges : ((int64_t)1 << 24), s);
+            CSL_CUDA(cudaStreamSynchronize(s));
+        } catch (...) {
+            delete L;
+            throw;
+        }
+        *out = L;
+    });
+}
+
 csl_status csl_lattice_update(csl_lattice* L, const float* nodes_xyz, const float* radius,
                               void* stream) {
     return guard([&] {
         require(L != nullptr, "lattice is NULL");
+        require_device_resident(L);
         cudaStream_t s = (cudaStream_t)stream;
         if (nodes_xyz && L->n_nodes > 0)
             CSL_CUDA(cudaMemcpyAsync(L->nodes.get(), nodes_xyz, (size_t)L->n_nodes * 12,
@@ -431,6 +480,37 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             }
             dev_chunks.push_back(std::move(cc));
         };
+        // A host-resident lattice: each chunk's z window of the sorted records
+        // (every record the chunk's slabs can select, with slack) is copied to
+        // one of two device windows, and the binner and field kernel see a view
+        // of the lattice made of that window.
+        std::vector<std::pair<int64_t, int64_t>> wins;
+        DevBuf w_rec[2], w_bxy[2], w_zlo[2], w_zhi[2];
+        if (L->host_resident) {
+            int64_t max_w = 1;
+            for (int k = 0; k < n_chunks; ++k) {
+                const int first = k * p.chunk;
+                const int n = std::min(p.chunk, d.n_layers - first);
+                const ChunkGeom g = chunk_geom(L, d, p, first, n);
+                const double zf = g.z0 + (double)g.first_layer * g.dz;
+                const double zl = g.z0 + (double)(g.first_layer + g.n_layers - 1) * g.dz;
+                const double lo_key = zf - g.margin_z - L->max_dz - 2e-3 * (1.0 + fabs(zf)) - fabs(g.dz);
+                const double hi_key = zl + g.margin_z + 2e-3 * (1.0 + fabs(zl)) + fabs(g.dz);
+                const float* z = L->h_zlo;
+                const int64_t a = std::lower_bound(z, z + L->n_edges, lo_key,
+                                                   [](float v, double key) { return (double)v < key; }) - z;
+                const int64_t b = std::upper_bound(z + a, z + L->n_edges, hi_key,
+                                                   [](double key, float v) { return key < (double)v; }) - z;
+                wins.emplace_back(a, b);
+                max_w = std::max<int64_t>(max_w, b - a);
+            }
+            for (int b = 0; b < n_par; ++b) {
+                w_rec[b].alloc((size_t)max_w * sizeof(csl_rec), streams[b]);
+                w_bxy[b].alloc((size_t)max_w * 16, streams[b]);
+                w_zlo[b].alloc((size_t)max_w * 4, streams[b]);
+                w_zhi[b].alloc((size_t)max_w * 4, streams[b]);
+            }
+        }
         int prev = -1;
         ChunkGeom g_prev{};
         for (int k = 0; k < n_chunks; ++k) {
@@ -438,11 +518,44 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             const int n = std::min(p.chunk, d.n_layers - first);
             ChunkGeom g = chunk_geom(L, d, p, first, n);
             cudaStream_t ks = streams[k % n_par];
+            csl_lattice view;              // the window of a host-resident lattice
+            const csl_lattice* LB = L;     // what the binner and field kernel see
+            if (L->host_resident) {
+                const int64_t a = wins[k].first, nw = wins[k].second - wins[k].first;
+                const int b = k % n_par;
+                if (nw > 0) {
+                    CSL_CUDA(cudaMemcpyAsync(w_rec[b].get(), L->h_rec + a, (size_t)nw * sizeof(csl_rec),
+                                             cudaMemcpyHostToDevice, ks));
+                    CSL_CUDA(cudaMemcpyAsync(w_bxy[b].get(), L->h_bxy + a, (size_t)nw * 16,
+                                             cudaMemcpyHostToDevice, ks));
+                    CSL_CUDA(cudaMemcpyAsync(w_zlo[b].get(), L->h_zlo + a, (size_t)nw * 4,
+                                             cudaMemcpyHostToDevice, ks));
+                    CSL_CUDA(cudaMemcpyAsync(w_zhi[b].get(), L->h_zhi + a, (size_t)nw * 4,
+                                             cudaMemcpyHostToDevice, ks));
+                }
+                view.n_nodes = L->n_nodes;
+                view.n_edges = nw;
+                view.R = L->R;
+                view.C = L->C;
+                view.mode = L->mode;
+                for (int c3 = 0; c3 < 3; ++c3) {
+                    view.bbox_lo[c3] = L->bbox_lo[c3];
+                    view.bbox_hi[c3] = L->bbox_hi[c3];
+                }
+                view.max_dz = L->max_dz;
+                view.max_radius = L->max_radius;
+                view.rec.view(w_rec[b].get(), w_rec[b].size());
+                view.bxy.view(w_bxy[b].get(), w_bxy[b].size());
+                view.zlo.view(w_zlo[b].get(), w_zlo[b].size());
+                view.zhi.view(w_zhi[b].get(), w_zhi[b].size());
+                view.status.view(L->status.get(), 4);
+                LB = &view;
+            }
             float* sigma = d.sigma_out ? d.sigma_out + (int64_t)first * plane
                                        : sigma_ws[k % n_par].as<float>();   // null: mask only
             {
                 SlabBins bins;
-                timed(st.bin_ms, [&] { bin_chunk(L, g, bins, ks); });
+                timed(st.bin_ms, [&] { bin_chunk(LB, g, bins, ks); });
                 st.candidate_pairs += bins.n_pairs;
                 st.window_records += bins.n_cand;
                 uint32_t* mask = (want_contours || d.mask_out) ? mask_ws[k % n_par].as<uint32_t>()
@@ -450,7 +563,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 if (mask)
                     CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, ks));
                 timed(st.field_ms, [&] {
-                    field_chunk(L, g, bins, (float)L->C, sigma, mask,
+                    field_chunk(LB, g, bins, (float)L->C, sigma, mask,
                                 count_pairs ? pair_count.as<unsigned long long>() : nullptr, ks);
                 });
                 ++st.field_launches;
@@ -568,6 +681,7 @@ csl_status csl_volume_fraction(csl_lattice* L, const csl_cells* cells, float* vf
                                void* stream) {
     return guard([&] {
         require(L != nullptr, "lattice is NULL");
+        require_device_resident(L);
         validate_cells_or_fail(cells);
         require(vf_out != nullptr, "vf_out is NULL");
         cudaStream_t s = (cudaStream_t)stream;
@@ -585,6 +699,7 @@ csl_status csl_volume_fraction_backward(csl_lattice* L, const csl_cells* cells,
                                         float* grad_nodes, void* stream) {
     return guard([&] {
         require(L != nullptr, "lattice is NULL");
+        require_device_resident(L);
         validate_cells_or_fail(cells);
         require(grad_vf != nullptr, "grad_vf is NULL");
         require(L->n_edges == 0 || grad_radius != nullptr, "grad_radius is NULL");
@@ -603,6 +718,7 @@ csl_status csl_debug_slab_bins(csl_lattice* L, const csl_slice_desc* desc, int32
                                int64_t capacity, int64_t* n_ids, void* stream) {
     return guard([&] {
         require(L != nullptr && tile_off != nullptr && n_ids != nullptr, "NULL argument");
+        require_device_resident(L);
         validate_desc(desc);
         require(n_slab_layers >= 1 && first_layer >= 0, "bad slab");
         cudaStream_t s = (cudaStream_t)stream;

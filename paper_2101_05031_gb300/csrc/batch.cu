@@ -309,6 +309,7 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
             for (int j = 0; j < n_jobs; ++j) {
                 auto& J = b->jobs[j];
                 require_arg(lats[j] != nullptr, "a job's lattice is NULL");
+                require_device_resident(lats[j]);
                 validate_desc(&descs[j]);
                 require_arg(descs[j].n_layers >= 1, "a batch job needs n_layers >= 1");
                 J.L = lats[j];

@@ -36,12 +36,14 @@ class DevBuf {
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     DevBuf(DevBuf&& o) noexcept
-        : p_(o.p_), n_(o.n_), s_(o.s_), persistent_(o.persistent_) { o.p_ = nullptr; o.n_ = 0; }
+        : p_(o.p_), n_(o.n_), s_(o.s_), persistent_(o.persistent_), owned_(o.owned_) {
+        o.p_ = nullptr; o.n_ = 0; o.owned_ = true;
+    }
     DevBuf& operator=(DevBuf&& o) noexcept {
         if (this != &o) {
             release();
-            p_ = o.p_; n_ = o.n_; s_ = o.s_; persistent_ = o.persistent_;
-            o.p_ = nullptr; o.n_ = 0;
+            p_ = o.p_; n_ = o.n_; s_ = o.s_; persistent_ = o.persistent_; owned_ = o.owned_;
+            o.p_ = nullptr; o.n_ = 0; o.owned_ = true;
         }
         return *this;
     }
@@ -52,6 +54,8 @@ class DevBuf {
     void alloc_persistent(size_t bytes);
     void ensure_persistent(size_t bytes) { if (bytes > n_) alloc_persistent(bytes); }
     void release();
+    // a view of `bytes` of device memory owned elsewhere (never freed here)
+    void view(void* p, size_t bytes);
     template <class T> T* as() const { return reinterpret_cast<T*>(p_); }
     size_t size() const { return n_; }
     void* get() const { return p_; }
@@ -61,6 +65,7 @@ class DevBuf {
     size_t n_ = 0;
     cudaStream_t s_ = nullptr;
     bool persistent_ = false;
+    bool owned_ = true;
 };
 
 // Workspace accounting for csl_last_stats.

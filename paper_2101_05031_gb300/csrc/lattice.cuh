@@ -30,9 +30,30 @@ struct csl_lattice {
     csl::DevBuf status;        // uint32: ST_TIMEOUT when a device wait gave up
     float bbox_lo[3] = {0, 0, 0}, bbox_hi[3] = {0, 0, 0};
     float max_dz = 0, max_radius = 0;
+    // A host-resident lattice (csl_lattice_upload_streamed) keeps the prepared
+    // arrays below in page-locked host memory, in the order rec/zlo give; only
+    // nodes and status live on the device, and slicing copies each chunk's
+    // z window of them to the device.
+    bool host_resident = false;
+    csl_rec* h_rec = nullptr;
+    float4* h_bxy = nullptr;
+    float* h_zlo = nullptr;
+    float* h_zhi = nullptr;
+    uint32_t* h_sid = nullptr;
+    ~csl_lattice() {
+        void* blocks[] = {h_rec, h_bxy, h_zlo, h_zhi, h_sid};
+        for (void* b : blocks)
+            if (b) csl::host_block_free(b);
+    }
 };
 
 namespace csl {
 // (Re)builds rec/zlo/zhi/sid from nodes/edges/radius; validates the input.
 void prepare_lattice(csl_lattice* L, bool recompute_R, cudaStream_t s);
+// The same preparation for a host-resident lattice: L->nodes on the device,
+// the edges and radii in host memory, at most `batch` edges on the device at
+// a time; every batch is sorted on the device and the sorted batches are
+// merged on the host in the order of the single sort.
+void prepare_lattice_streamed(csl_lattice* L, const int32_t* edges, const float* radius,
+                              int64_t batch, cudaStream_t s);
 }  // namespace csl

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "field_tile.cuh"
+#include "slice.cuh"
 
 namespace csl {
 namespace {
@@ -212,6 +213,7 @@ extern "C" csl_status csl_render_depth(const csl_lattice* L, const csl_camera* c
                                        void* stream) {
     try {
         if (!L || !cam || !depth) fail(CSL_ERR_INVALID_ARG, "NULL argument");
+        require_device_resident(L);
         if (cam->width < 1 || cam->height < 1 || (int64_t)cam->width * cam->height >= (1ll << 31))
             fail(CSL_ERR_INVALID_ARG, "width and height must be >= 1");
         if (!(cam->fov_y > 0.0 && cam->fov_y < M_PI)) fail(CSL_ERR_INVALID_ARG, "fov_y in (0, pi)");

@@ -111,11 +111,24 @@ void DevBuf::alloc_persistent(size_t bytes) {
 
 void DevBuf::release() {
     if (!p_) return;
+    if (!owned_) {   // a view of memory owned elsewhere
+        p_ = nullptr;
+        n_ = 0;
+        owned_ = true;
+        return;
+    }
     if (persistent_) cudaFree(p_);
     else cudaFreeAsync(p_, s_);
     note_device_bytes(-(int64_t)n_);
     p_ = nullptr;
     n_ = 0;
+}
+
+void DevBuf::view(void* p, size_t bytes) {
+    release();
+    p_ = p;
+    n_ = bytes;
+    owned_ = false;
 }
 
 namespace {

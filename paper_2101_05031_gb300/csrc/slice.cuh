@@ -112,6 +112,8 @@ ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SliceP
                      int n);
 void validate_desc(const csl_slice_desc* d);
 void require_arg(bool ok, const char* msg);
+// Fails with NOT_READY for a host-resident lattice (slicing is its only use).
+void require_device_resident(const csl_lattice* L);
 
 // Reads and clears the lattice's device status word; CSL_ERR_TIMEOUT when a
 // device wait of an earlier kernel gave up (synchronises s).

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "lattice.cuh"
+#include "slice.cuh"
 
 namespace csl {
 namespace {
@@ -92,6 +93,7 @@ extern "C" csl_status csl_support_metrics(const csl_lattice* L, const double* t_
                                           void* stream) {
     try {
         if (!L || !t_p || !gamma || !psi) fail(CSL_ERR_INVALID_ARG, "NULL argument");
+        require_device_resident(L);
         const double n = sqrt(t_p[0] * t_p[0] + t_p[1] * t_p[1] + t_p[2] * t_p[2]);
         if (!(n > 0.0) || !isfinite(n)) fail(CSL_ERR_INVALID_ARG, "t_p must be a nonzero vector");
         if (!(alpha >= 0.0 && alpha <= M_PI / 2)) fail(CSL_ERR_INVALID_ARG, "alpha in [0, pi/2]");

@@ -162,7 +162,12 @@ class Lattice:
     nodes float[Nn, 3] (mm), edges int32[Ne, 2], radius float[Ne] (PHYSICAL:
     strut radius; RAW: the paper's r_i weight). R None -> 1.5 x max radius."""
 
-    def __init__(self, nodes, edges, radius, R=None, C=1.0, mode="physical", stream=None):
+    def __init__(self, nodes, edges, radius, R=None, C=1.0, mode="physical", stream=None,
+                 host_resident=False, batch_edges=0):
+        """host_resident=True: csl_lattice_upload_streamed (host arrays; the
+        prepared records stay in page-locked host memory, at most batch_edges
+        edges on the device while preparing, and slicing streams each chunk's
+        window; the lattice then serves slicing only)."""
         lib = _lib.load()
         pn, nn, dn, kn = _as_buffer(nodes, np.float32, 3)
         pe, ne, de, ke = _as_buffer(edges, np.int32, 2)
@@ -174,8 +179,13 @@ class Lattice:
         params = _lib.Params(float(R) if R else 0.0, float(C),
                              _lib.MODE_RAW if mode == "raw" else _lib.MODE_PHYSICAL, int(dn))
         h = ctypes.c_void_p()
-        _lib.check(lib.csl_lattice_upload(pn, nn, pe, pr, ne, ctypes.byref(params),
-                                          _stream_ptr(stream), ctypes.byref(h)))
+        if host_resident:
+            _lib.check(lib.csl_lattice_upload_streamed(pn, nn, pe, pr, ne, ctypes.byref(params),
+                                                       int(batch_edges), _stream_ptr(stream),
+                                                       ctypes.byref(h)))
+        else:
+            _lib.check(lib.csl_lattice_upload(pn, nn, pe, pr, ne, ctypes.byref(params),
+                                              _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
         del kn, ke, kr
         info = self.info()
