@@ -135,7 +135,7 @@ def test_autograd_function_and_radius_tuning():
     gr, gn = volume_fraction_backward(lat, cells, (vf - target).detach())
     assert torch.allclose(radius.grad, gr, rtol=1e-6, atol=1e-12)
     assert torch.allclose(nodes.grad, gn, rtol=1e-6, atol=1e-12)
-    losses = [float(loss)]
+    losses = [float(loss.detach())]
     with torch.no_grad():
         r = radius.detach().clone()
     lr = 0.05 / max(float(gr.abs().max()), 1e-12)
