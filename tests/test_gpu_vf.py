@@ -146,5 +146,5 @@ def test_autograd_function_and_radius_tuning():
         loss.backward()
         with torch.no_grad():
             r = (r - lr * r.grad).clamp(0.05, 0.9 * R)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < losses[0]
