@@ -224,9 +224,25 @@ def run_vf(steps, warmup):
     fwd = _event_ms(lambda: volume_fraction(lat, cells, out=vf), steps, warmup, stream)
     bwd = _event_ms(lambda: volume_fraction_backward(lat, cells, g), steps, warmup, stream)
     samples = d[0] * d[1] * d[2] * cells["m"] ** 3
+    # the FP64 oracle on a sample of 2 cells in the middle of the grid (one host core)
+    import oracle
+    n_cells = d[0] * d[1] * d[2]
+    mid = (d[2] // 2 * d[1] + d[1] // 2) * d[0] + d[0] // 2
+    ids = np.arange(mid, mid + 2, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.volume_fraction(cfg["nodes"], cfg["edges"], cfg["radius"], cells, R=cfg["R"], ids=ids)
+    of = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.vf_backward(cfg["nodes"], cfg["edges"], cfg["radius"], cells, np.ones(2), R=cfg["R"],
+                       ids=ids)
+    ob = time.perf_counter() - t0
     return {"workload": cfg["name"], "forward_ms": fwd, "backward_ms": bwd,
             "backward_forward_ratio": bwd / fwd, "samples_per_s_forward": samples / (fwd / 1e3),
-            "samples_per_s_backward": samples / (bwd / 1e3)}
+            "samples_per_s_backward": samples / (bwd / 1e3),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "2 cells of the 64^3 grid",
+                             "forward_s_per_cell": of / 2, "backward_s_per_cell": ob / 2,
+                             "forward_full_grid_s_extrapolated": of / 2 * n_cells,
+                             "backward_full_grid_s_extrapolated": ob / 2 * n_cells}}
 
 
 def run_10m(steps, warmup):
@@ -287,6 +303,10 @@ def run_batch(steps, warmup):
                        "candidates": cands},
            "per_job": {"ms_per_step": plain_ms, "pixel_evals_per_s": px / (plain_ms / 1e3)},
            "batched_over_per_job": plain_ms / batch_ms}
+    # the FP64 oracle on a 128^2 window of the middle layer of the largest lattice
+    big = max(cfg["jobs"], key=lambda jb: jb["edges"].shape[0])
+    ob = oracle_sample(big, window=128, min_seconds=3.0)
+    out["cpu_baseline"] = dict(ob, full_batch_s_extrapolated=px / ob["value"])
     b.close()
     return out
 
