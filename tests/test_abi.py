@@ -128,6 +128,25 @@ def test_errors_cross_the_abi_as_codes():
                                   tets.ctypes.data_as(ctypes.c_void_p), 1, None, ctypes.byref(po),
                                   None, ctypes.byref(pr), None)
     assert st == 1 and b"out of range" in lib.csl_last_error()
+    # depth images, simplification and streamed uploads check their arguments first
+    cam = _lib.Camera((ctypes.c_double * 3)(0, 0, 10), (ctypes.c_double * 3)(0, 0, 0),
+                      (ctypes.c_double * 3)(0, 1, 0), 0.5, 16, 16, 0.1, 10, 0)
+    assert lib.csl_render_depth(None, ctypes.byref(cam), None, None) == 1
+    host = _lib.Contours()
+    res_c = ctypes.POINTER(_lib.Contours)()
+    st = lib.csl_simplify_contours(ctypes.byref(host), 10, 10, 0.1, None, ctypes.byref(res_c))
+    assert st == 1 and b"device" in lib.csl_last_error()
+    host.on_device = 1
+    st = lib.csl_simplify_contours(ctypes.byref(host), 10, 10, 0.1, None, ctypes.byref(res_c))
+    assert st == 1 and b"edge ids" in lib.csl_last_error()
+    prm_dev = _lib.Params(0.0, 1.0, 0, 1)
+    lat_out = ctypes.c_void_p()
+    st = lib.csl_lattice_upload_streamed(nodes.ctypes.data_as(ctypes.c_void_p), 4, None, None, 0,
+                                         ctypes.byref(prm_dev), 0, None, ctypes.byref(lat_out))
+    assert st == 1 and b"host arrays" in lib.csl_last_error()
+    st = lib.csl_lattice_upload_streamed(nodes.ctypes.data_as(ctypes.c_void_p), 4, None, None, 0,
+                                         None, -1, None, ctypes.byref(lat_out))
+    assert st == 1 and b"batch_edges" in lib.csl_last_error()
     # the wait test's poll count is checked before any device call
     assert lib.csl_debug_wait_timeout(0, None) == 1
     assert lib.csl_debug_wait_timeout(1 << 23, None) == 1
