@@ -506,8 +506,9 @@ typedef struct csl_camera {
  * refined by `refine` halvings of the preceding step; no such sample: +inf.
  * Features thinner than a step can be missed. The struts are binned into a
  * uniform grid of cells of edge >= 2R (empty cells are skipped). depth: DEVICE
- * float [height][width]. Errors: INVALID_ARG (camera, sizes), CAPACITY (more
- * than 2^31 strut-cell pairs), OOM. Synchronises the stream.
+ * float [height][width]. Errors: INVALID_ARG (camera, sizes, a step giving
+ * more than 2^24 samples across the grown box), CAPACITY (more than 2^31
+ * strut-cell pairs), OOM. Synchronises the stream.
  */
 csl_status csl_render_depth(const csl_lattice* lat, const csl_camera* cam, float* depth,
                             void* stream);

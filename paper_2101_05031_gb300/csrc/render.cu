@@ -269,6 +269,17 @@ extern "C" csl_status csl_render_depth(const csl_lattice* L, const csl_camera* c
             CSL_CUDA(cudaStreamSynchronize(s));
             return CSL_OK;
         }
+        // at most 2^24 samples along any ray through the box, so that the
+        // sample index k is exact in float and every march ends in bounded time
+        {
+            double diag2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double e = (double)c.bhi[k] - (double)c.blo[k];
+                diag2 += e * e;
+            }
+            if (sqrt(diag2) / cam->step > (double)(1 << 24))
+                fail(CSL_ERR_INVALID_ARG, "step too small: more than 2^24 samples across the box");
+        }
         // the grid: cells of edge >= 2R, at most 2^24 of them
         RvGrid g;
         double h = std::max(2.0 * R, 1e-6);

@@ -88,3 +88,32 @@ def test_full_workload_sampled_rays():
         n_bad += not (abs(g - t) <= 2e-3)
     assert n_hit >= 20
     assert n_bad <= 1, n_bad
+
+
+def test_edge_cases_of_the_ray_march():
+    """Rays that point away from the lattice miss; rays that start inside the
+    solid stop at their first sample (depth 0, reading V2 with t_in = 0); a
+    lattice without struts gives +inf everywhere; a step that would need more
+    than 2^24 samples across the box is rejected before any launch."""
+    import paper_2101_05031_gb300 as cs
+    rho, R = 0.3, 0.45
+    nodes = np.array([[0, 0, -20], [0, 0, 20]], np.float32)
+    lat = cs.Lattice(nodes, np.array([[0, 1]], np.int32), np.array([rho], np.float32), R=R)
+    away = lat.render_depth(eye=(0.0, 5.0, 1.0), target=(0.0, 10.0, 1.0), up=(0.0, 0.0, 1.0),
+                            fov_y=0.2, width=5, height=3, step=0.01).cpu().numpy()
+    assert np.all(np.isinf(away))
+    inside = lat.render_depth(eye=(0.0, 0.0, 1.0), target=(1.0, 0.0, 1.0), up=(0.0, 0.0, 1.0),
+                              fov_y=0.5, width=4, height=4, step=0.01).cpu().numpy()
+    assert np.all(inside == 0.0)
+    ref = V.render(nodes, np.array([[0, 1]], np.int32), np.array([rho], np.float32), R=R,
+                   eye=(0.0, 0.0, 1.0), target=(1.0, 0.0, 1.0), up=(0.0, 0.0, 1.0), fov_y=0.5,
+                   width=4, height=4, step=0.01, pixels=[(0, 0), (2, 1)])
+    assert all(t == 0.0 for t in ref.values())
+    empty = cs.Lattice(nodes, np.zeros((0, 2), np.int32), np.zeros(0, np.float32), R=R)
+    e = empty.render_depth(eye=(0.0, 5.0, 1.0), target=(0.0, 0.0, 1.0), width=3, height=2,
+                           step=0.01).cpu().numpy()
+    assert np.all(np.isinf(e))
+    with pytest.raises(cs.CslError) as err:
+        lat.render_depth(eye=(0.0, 5.0, 1.0), target=(0.0, 0.0, 1.0), width=3, height=2,
+                         step=1e-7)
+    assert err.value.code == 1

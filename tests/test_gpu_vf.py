@@ -148,3 +148,19 @@ def test_autograd_function_and_radius_tuning():
             r = (r - lr * r.grad).clamp(0.05, 0.9 * R)
         losses.append(float(loss.detach()))
     assert losses[-1] < losses[0]
+
+
+def test_cells_beyond_every_strut_support(c5):
+    """Cells farther than R from every strut: Sigma = 0 at every sample, so
+    each cell's volume fraction is sigma(-C/T) (below 1e-30 at T = 0.01 C) and
+    no strut or node receives any gradient."""
+    from paper_2101_05031_gb300 import volume_fraction, volume_fraction_backward
+    cfg, lat = c5
+    lo, hi = synth.lattice_bbox(cfg["nodes"])
+    cells = dict(origin=(float(hi[0]) + 5.0, float(lo[1]), float(lo[2])), h=1.0, dims=(4, 3, 2),
+                 m=2, T=0.01)
+    vf = volume_fraction(lat, cells)
+    assert vf.shape == (2, 3, 4)
+    assert float(vf.abs().max()) <= 1e-30
+    gr, gn = volume_fraction_backward(lat, cells, torch.ones((2, 3, 4), device="cuda"))
+    assert int(torch.count_nonzero(gr)) == 0 and int(torch.count_nonzero(gn)) == 0
