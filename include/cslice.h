@@ -207,6 +207,21 @@ csl_status csl_contours_copy(const csl_contours* c, int64_t* layer_loop_off, int
                              float* xy, int32_t* edge_id, int32_t dst_on_device, void* stream);
 
 /*
+ * csl_contours_create -- device contours from HOST arrays in the layout of
+ * csl_contours (for post-processing contours made elsewhere: simplification,
+ * smoothing, zigzag infill). layer_loop_off [n_layers + 1] from 0 to n_loops
+ * and loop_vert_off [n_loops + 1] from 0 to n_verts, both non-decreasing;
+ * xy [2 n_verts] in mm (finite); edge_id [n_verts] grid-edge ids (>= 0) or
+ * NULL. The library copies the arrays and owns the result (free with
+ * csl_contours_free). Errors: INVALID_ARG (counts, offsets, non-finite
+ * vertices, negative ids), OOM. Synchronises the stream.
+ */
+csl_status csl_contours_create(int32_t n_layers, int64_t n_loops, int64_t n_verts,
+                               const int64_t* layer_loop_off, const int64_t* loop_vert_off,
+                               const float* xy, const int32_t* edge_id, void* stream,
+                               csl_contours** out);
+
+/*
  * Zigzag infill of the contours (Sec. 6: the interior of each layer is filled
  * by a zigzag toolpath after its boundary contours). Scan lines
  * y_m = y0 + m spacing, m in [0, n_lines), the same in every layer (y_m is
@@ -486,6 +501,28 @@ csl_status csl_measure_fp32_peak(double* tflops, double* sm_clock_ghz, void* str
  */
 csl_status csl_simplify_contours(const csl_contours* in, int32_t nx, int32_t ny, double tol,
                                  void* stream, csl_contours** out);
+
+/*
+ * csl_smooth_contours -- topology-preserving smoothing of device contours, in
+ * place (the paper smooths its marching-squares boundaries without creating
+ * intersections, Sec. 4). Every vertex slides along its own grid edge of the
+ * padded nx x ny sample grid (pixel size `pixel`, first pixel centre at
+ * (x0 + pixel/2, y0 + pixel/2)): in each of `iterations` Jacobi steps its
+ * free coordinate a (x on a horizontal edge, y on a vertical one) becomes
+ * a + lambda (m - a), m the mean of that coordinate at its loop neighbours,
+ * in FP64, clamped to the edge's [margin, 1 - margin] part and rounded to
+ * float; the other coordinate, the edge ids and all offsets are unchanged;
+ * loops of fewer than 3 vertices stay as they are. Every segment stays
+ * inside its grid cell (or the 1 x 2 block of a vertex that simplification
+ * dropped), so no two segments can come to cross. c: device contours with
+ * edge ids of that grid. Errors: INVALID_ARG (host contours, no edge ids, an
+ * edge id outside the grid, nx/ny outside [1, 32000], pixel <= 0, lambda
+ * outside [0, 1], margin outside (0, 1/2], iterations outside [0, 10000]) with
+ * c unchanged; CAPACITY (more than 2^31 - 1 loops); OOM. Synchronises.
+ */
+csl_status csl_smooth_contours(csl_contours* c, double x0, double y0, double pixel, int32_t nx,
+                               int32_t ny, double lambda, double margin, int32_t iterations,
+                               void* stream);
 
 /* ---- ray casting of the implicit solid (a depth image, no mesh) --------- */
 

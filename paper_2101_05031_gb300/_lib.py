@@ -167,6 +167,10 @@ SIGNATURES = [
     ("csl_render_depth", c_i32, [c_vp, ctypes.POINTER(Camera), c_vp, c_vp]),
     ("csl_simplify_contours", c_i32, [ctypes.POINTER(Contours), c_i32, c_i32, c_f64, c_vp,
                                       ctypes.POINTER(ctypes.POINTER(Contours))]),
+    ("csl_smooth_contours", c_i32, [ctypes.POINTER(Contours), c_f64, c_f64, c_f64, c_i32, c_i32,
+                                    c_f64, c_f64, c_i32, c_vp]),
+    ("csl_contours_create", c_i32, [c_i32, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                    ctypes.POINTER(ctypes.POINTER(Contours))]),
     ("csl_support_optimize", c_i32, [c_vp, c_i64, c_vp, c_i64, c_vp, ctypes.POINTER(PoParams),
                                      c_vp, ctypes.POINTER(PoResult), c_vp]),
     ("csl_measure_fp32_peak", c_i32, [ctypes.POINTER(c_f64), ctypes.POINTER(c_f64), c_vp]),

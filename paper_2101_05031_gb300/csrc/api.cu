@@ -335,6 +335,53 @@ csl_status csl_contours_copy(const csl_contours* c, int64_t* layer_loop_off,
     });
 }
 
+csl_status csl_contours_create(int32_t n_layers, int64_t n_loops, int64_t n_verts,
+                               const int64_t* layer_loop_off, const int64_t* loop_vert_off,
+                               const float* xy, const int32_t* edge_id, void* stream,
+                               csl_contours** out) {
+    csl_contours* c = nullptr;
+    const csl_status st = guard([&] {
+        require(out != nullptr, "out is NULL");
+        *out = nullptr;
+        require(n_layers >= 0 && n_loops >= 0 && n_verts >= 0, "negative count");
+        require(n_loops <= 0x7fffffffLL && n_verts <= 0x7fffffffLL, "more than 2^31 - 1 items");
+        require(layer_loop_off != nullptr && loop_vert_off != nullptr, "offsets are NULL");
+        require(n_verts == 0 || xy != nullptr, "xy is NULL");
+        require(layer_loop_off[0] == 0 && layer_loop_off[n_layers] == n_loops,
+                "layer_loop_off must run from 0 to n_loops");
+        for (int32_t l = 0; l < n_layers; ++l)
+            require(layer_loop_off[l] <= layer_loop_off[l + 1], "layer_loop_off decreases");
+        require(loop_vert_off[0] == 0 && loop_vert_off[n_loops] == n_verts,
+                "loop_vert_off must run from 0 to n_verts");
+        for (int64_t L = 0; L < n_loops; ++L)
+            require(loop_vert_off[L] <= loop_vert_off[L + 1], "loop_vert_off decreases");
+        for (int64_t i = 0; i < 2 * n_verts; ++i) require(isfinite(xy[i]), "non-finite vertex");
+        if (edge_id)
+            for (int64_t i = 0; i < n_verts; ++i) require(edge_id[i] >= 0, "negative edge id");
+        cudaStream_t s = (cudaStream_t)stream;
+        c = new csl_contours();
+        c->n_layers = n_layers;
+        c->on_device = 1;
+        c->n_loops = n_loops;
+        c->n_verts = n_verts;
+        auto up = [&](void** dst, const void* src, size_t bytes) {
+            if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) {
+                cudaGetLastError();
+                fail(CSL_ERR_OOM, "device allocation of the contours failed");
+            }
+            if (bytes) CSL_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s));
+        };
+        up((void**)&c->layer_loop_off, layer_loop_off, (size_t)(n_layers + 1) * 8);
+        up((void**)&c->loop_vert_off, loop_vert_off, (size_t)(n_loops + 1) * 8);
+        up((void**)&c->xy, xy, (size_t)n_verts * 8);
+        if (edge_id) up((void**)&c->edge_id, edge_id, (size_t)n_verts * 4);
+        CSL_CUDA(cudaStreamSynchronize(s));
+        *out = c;
+    });
+    if (st != CSL_OK && c) csl_contours_free(c);
+    return st;
+}
+
 csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* stream,
                             csl_contours** out) {
     return guard([&] {

@@ -41,15 +41,22 @@ __global__ void k_sp_loop_layer(const int64_t* __restrict__ layer_off, int n_lay
     }
 }
 
+// An edge id outside the padded grid (contours of another grid) is skipped
+// and reported through *bad.
 __global__ void k_sp_mark(const int64_t* __restrict__ loop_off, const int32_t* __restrict__ eid,
                           const int32_t* __restrict__ loop_layer, int64_t n_loops, SpGrid g,
-                          uint32_t* __restrict__ bits) {
+                          uint32_t* __restrict__ bits, uint32_t* bad) {
+    const int64_t n_ids = 2 * (int64_t)g.W * g.H;
     for (int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; L < n_loops;
          L += (int64_t)gridDim.x * blockDim.x) {
         uint32_t* row = bits + (int64_t)loop_layer[L] * g.words;
         for (int64_t v = loop_off[L]; v < loop_off[L + 1]; ++v) {
-            const uint32_t e = (uint32_t)eid[v];
-            atomicOr(row + (e >> 5), 1u << (e & 31u));
+            const int64_t e = eid[v];
+            if (e < 0 || e >= n_ids) {
+                atomicOr(bad, 1u);
+                continue;
+            }
+            atomicOr(row + (e >> 5), 1u << (uint32_t)(e & 31));
         }
     }
 }
@@ -176,16 +183,18 @@ extern "C" csl_status csl_simplify_contours(const csl_contours* in, int32_t nx, 
         DevBuf d_bits((size_t)std::max<int64_t>((int64_t)n_layers * g.words, 1) * 4, s);
         DevBuf d_keep((size_t)std::max<int64_t>(n_verts, 1), s);
         DevBuf d_kept((size_t)std::max<int64_t>(n_loops, 1) * 4, s);
-        DevBuf d_tot(8, s);
+        DevBuf d_tot(8, s), d_bad(4, s);
         int64_t n_out = 0;
         if (n_loops > 0) {
+            CSL_CUDA(cudaMemsetAsync(d_bad.get(), 0, 4, s));
             CSL_CUDA(cudaMemsetAsync(d_bits.get(), 0, (size_t)n_layers * g.words * 4, s));
             k_sp_loop_layer<<<grid_for(n_loops, 256), 256, 0, s>>>(in->layer_loop_off, n_layers,
                                                                    n_loops, d_layer.as<int32_t>());
             CSL_LAUNCH_CHECK("simplify loop layers");
             k_sp_mark<<<grid_for(n_loops, 256), 256, 0, s>>>(in->loop_vert_off, in->edge_id,
                                                              d_layer.as<int32_t>(), n_loops, g,
-                                                             d_bits.as<uint32_t>());
+                                                             d_bits.as<uint32_t>(),
+                                                             d_bad.as<uint32_t>());
             CSL_LAUNCH_CHECK("simplify edge bitmap");
             k_sp_keep<<<grid_for(n_loops, 256), 256, 0, s>>>(
                 in->loop_vert_off, in->edge_id, in->xy, d_layer.as<int32_t>(), n_loops, g,
@@ -194,6 +203,9 @@ extern "C" csl_status csl_simplify_contours(const csl_contours* in, int32_t nx, 
             exclusive_scan_u32_to_i64(d_kept.as<uint32_t>(), c->loop_vert_off, n_loops,
                                       d_tot.as<int64_t>(), s);
             n_out = read_i64(d_tot.as<int64_t>(), s);
+            uint32_t bad = 0;
+            read_to_host(&bad, d_bad.get(), 4, s);
+            if (bad) fail(CSL_ERR_INVALID_ARG, "edge ids outside the nx x ny grid");
             CSL_CUDA(cudaMemcpyAsync(c->loop_vert_off + n_loops, d_tot.get(), 8,
                                      cudaMemcpyDeviceToDevice, s));
         } else {

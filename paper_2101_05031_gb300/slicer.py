@@ -103,6 +103,34 @@ class DeviceContours:
             lib.csl_hatches_free(h)
         return off, seg
 
+    @classmethod
+    def from_host(cls, layer_loop_off, loop_vert_off, xy, edge_id=None, stream=None):
+        """csl_contours_create: device contours from host arrays in the layout
+        of csl_contours (offsets int64, xy float32 [n, 2], edge ids int32)."""
+        lo = np.ascontiguousarray(layer_loop_off, dtype=np.int64)
+        vo = np.ascontiguousarray(loop_vert_off, dtype=np.int64)
+        xy = np.ascontiguousarray(xy, dtype=np.float32).reshape(-1, 2)
+        eid = None if edge_id is None else np.ascontiguousarray(edge_id, dtype=np.int32)
+        if lo.ndim != 1 or vo.ndim != 1 or lo.size < 1 or vo.size < 1:
+            raise ValueError("offsets must be 1-D with at least one entry")
+        if eid is not None and eid.shape != (xy.shape[0],):
+            raise ValueError("edge_id must have one entry per vertex")
+        out = ctypes.POINTER(_lib.Contours)()
+        _lib.check(_lib.load().csl_contours_create(
+            lo.size - 1, vo.size - 1, xy.shape[0], lo.ctypes.data_as(ctypes.c_void_p),
+            vo.ctypes.data_as(ctypes.c_void_p), xy.ctypes.data_as(ctypes.c_void_p),
+            eid.ctypes.data_as(ctypes.c_void_p) if eid is not None else None,
+            _stream_ptr(stream), ctypes.byref(out)))
+        return cls(out)
+
+    def smooth(self, x0, y0, pixel, nx, ny, lam=0.5, margin=0.05, iterations=4, stream=None):
+        """csl_smooth_contours, in place: every vertex slides along its own grid
+        edge toward its loop neighbours (needs edge ids). Returns self."""
+        _lib.check(_lib.load().csl_smooth_contours(self._ptr, float(x0), float(y0), float(pixel),
+                                                   int(nx), int(ny), float(lam), float(margin),
+                                                   int(iterations), _stream_ptr(stream)))
+        return self
+
     def simplify(self, nx, ny, tol, stream=None):
         """csl_simplify_contours: new DeviceContours with vertices dropped where
         that cannot create an intersection (needs edge ids; tol in mm)."""

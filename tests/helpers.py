@@ -95,3 +95,34 @@ def compare_layer_contours(gpu_loops, sig_ref, *, x0, y0, pixel, C):
     if excluded == 0:
         assert len(gpu_loops) == len(off) - 1, "GPU has extra loops"
     return matched, excluded
+
+
+def oracle_contour_set(cfg, layers):
+    """The oracle's marching-squares contours of the given layers of a
+    configuration (its field in FP64, vertices rounded to float32), in the
+    layout of csl_contours: (layer_loop_off, loop_vert_off, xy float32 [n, 2],
+    edge_id int32). Post-processing stages take these as their input, so no
+    oracle input comes from the GPU path."""
+    lo, vo, xys, eids = [0], [0], [], []
+    for k in layers:
+        sig = oracle.slice_sigma(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"],
+                                 C=cfg["C"], z0=cfg["z0"] + k * cfg["dz"], dz=cfg["dz"],
+                                 n_layers=1, x0=cfg["x0"], y0=cfg["y0"], nx=cfg["nx"],
+                                 ny=cfg["ny"], pixel=cfg["pixel"])[0]
+        off, eid, xy = oracle.marching_squares(sig, x0=cfg["x0"], y0=cfg["y0"],
+                                               pixel=cfg["pixel"], C=cfg["C"])
+        base = vo[-1]
+        vo.extend(int(base + o) for o in off[1:])
+        lo.append(lo[-1] + len(off) - 1)
+        xys.append(np.asarray(xy, dtype=np.float32).reshape(-1, 2))
+        eids.append(np.asarray(eid, dtype=np.int32))
+    return (np.array(lo, np.int64), np.array(vo, np.int64),
+            np.concatenate(xys) if xys else np.zeros((0, 2), np.float32),
+            np.concatenate(eids) if eids else np.zeros(0, np.int32))
+
+
+def layer_arrays(lo, vo, xy, eid, k):
+    """One layer's (loop_off from 0, edge ids, xy) out of a contour set."""
+    l0, l1 = int(lo[k]), int(lo[k + 1])
+    v0, v1 = int(vo[l0]), int(vo[l1])
+    return vo[l0:l1 + 1] - v0, eid[v0:v1], xy[v0:v1]

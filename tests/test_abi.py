@@ -147,6 +147,41 @@ def test_errors_cross_the_abi_as_codes():
     st = lib.csl_lattice_upload_streamed(nodes.ctypes.data_as(ctypes.c_void_p), 4, None, None, 0,
                                          None, -1, None, ctypes.byref(lat_out))
     assert st == 1 and b"batch_edges" in lib.csl_last_error()
+    # smoothing and contours from host arrays check their arguments first
+    st = lib.csl_smooth_contours(ctypes.byref(host), 0.0, 0.0, 0.1, 10, 10, 0.5, 0.05, 4, None)
+    assert st == 1 and b"edge ids" in lib.csl_last_error()
+    host.on_device = 0
+    st = lib.csl_smooth_contours(ctypes.byref(host), 0.0, 0.0, 0.1, 10, 10, 0.5, 0.05, 4, None)
+    assert st == 1 and b"device" in lib.csl_last_error()
+    host.on_device = 1
+    host.edge_id = 16   # never read: every call below fails its argument checks first
+    for args, word in (((0.1, 10, 10, 1.5, 0.05, 4), b"lambda"), ((0.1, 10, 10, 0.5, 0.0, 4), b"margin"),
+                       ((0.1, 10, 10, 0.5, 0.6, 4), b"margin"), ((0.0, 10, 10, 0.5, 0.05, 4), b"pixel"),
+                       ((0.1, 0, 10, 0.5, 0.05, 4), b"nx"), ((0.1, 10, 10, 0.5, 0.05, -1), b"iterations")):
+        st = lib.csl_smooth_contours(ctypes.byref(host), 0.0, 0.0, *args, None)
+        assert st == 1 and word in lib.csl_last_error(), word
+    lo = np.array([0, 1], np.int64)
+    xy = np.zeros((4, 2), np.float32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for vo, word in ((np.array([0, 5], np.int64), b"loop_vert_off"),
+                     (np.array([1, 4], np.int64), b"loop_vert_off")):
+        st = lib.csl_contours_create(1, 1, 4, p(lo), p(vo), p(xy), None, None, ctypes.byref(res_c))
+        assert st == 1 and word in lib.csl_last_error()
+    st = lib.csl_contours_create(1, 2, 4, p(lo), p(np.array([0, 3, 4], np.int64)), p(xy), None,
+                                 None, ctypes.byref(res_c))
+    assert st == 1 and b"layer_loop_off" in lib.csl_last_error()
+    st = lib.csl_contours_create(1, 2, 4, p(np.array([0, 2], np.int64)),
+                                 p(np.array([0, 5, 4], np.int64)), p(xy), None, None,
+                                 ctypes.byref(res_c))
+    assert st == 1 and b"decreases" in lib.csl_last_error()
+    bad_xy = xy.copy()
+    bad_xy[2, 1] = np.nan
+    st = lib.csl_contours_create(1, 1, 4, p(lo), p(np.array([0, 4], np.int64)), p(bad_xy), None,
+                                 None, ctypes.byref(res_c))
+    assert st == 1 and b"non-finite" in lib.csl_last_error()
+    st = lib.csl_contours_create(1, 1, 4, p(lo), p(np.array([0, 4], np.int64)), p(xy),
+                                 p(np.array([0, 2, -4, 6], np.int32)), None, ctypes.byref(res_c))
+    assert st == 1 and b"negative edge id" in lib.csl_last_error()
     # the wait test's poll count is checked before any device call
     assert lib.csl_debug_wait_timeout(0, None) == 1
     assert lib.csl_debug_wait_timeout(1 << 23, None) == 1

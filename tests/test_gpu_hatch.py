@@ -1,11 +1,13 @@
 """Zigzag infill on the GPU (csl_hatch_layers) against the reference hatcher
-applied to the same contours, and against the oracle's field."""
+applied to the same contours (the oracle's own, uploaded), and, on the GPU's
+slices, against the oracle's field."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
 from oracle import hatch
+from tests.helpers import oracle_contour_set
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -22,12 +24,15 @@ def _c1_contours(n_layers=50):
 
 
 def test_hatch_matches_reference_on_the_same_contours():
-    cfg, lat, dev = _c1_contours()
+    """The input is the oracle's own marching-squares contours of 50 layers
+    (float32), uploaded with csl_contours_create."""
+    import paper_2101_05031_gb300 as cs
+    cfg = synth.config(1)
+    lo, vo, xy, eid = oracle_contour_set(cfg, range(50))
+    dev = cs.DeviceContours.from_host(lo, vo, xy, eid)
     y0, sp, n_lines = cfg["y0"] + 0.025, 0.25, 80
     off, seg = dev.hatch(y0, sp, n_lines)
-    host = dev.to_host()
-    roff, rseg = hatch.hatch_contours(host.layer_loop_off, host.loop_vert_off, host.xy, y0, sp,
-                                      n_lines)
+    roff, rseg = hatch.hatch_contours(lo, vo, xy, y0, sp, n_lines)
     assert np.array_equal(off, roff)
     assert seg.shape == rseg.shape and len(seg) > 1000
     assert np.array_equal(seg[:, 2].astype(np.float64), rseg[:, 2])   # the same float32 lines
