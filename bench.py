@@ -342,7 +342,18 @@ def run_hatch(steps, warmup):
     out_simplify = {"ms_per_step": sms, "vertices_in": int(dev.n_verts),
                     "vertices_out": int(simp["n"]), "vertices_per_s": dev.n_verts / (sms / 1e3),
                     "tolerance_px": 0.25}
-    return {"simplify": out_simplify,
+    # smoothing of the same contours in place (4 Jacobi steps, lambda 1/2,
+    # margin 0.05 of an edge); the last use of them here
+    it = 4
+
+    def smooth_step():
+        dev.smooth(cfg["x0"], cfg["y0"], cfg["pixel"], cfg["nx"], cfg["ny"], lam=0.5,
+                   margin=0.05, iterations=it)
+
+    mms = _event_ms(smooth_step, steps, warmup, torch.cuda.current_stream())
+    out_smooth = {"ms_per_step": mms, "iterations": it, "vertices": int(dev.n_verts),
+                  "vertex_steps_per_s": dev.n_verts * it / (mms / 1e3)}
+    return {"simplify": out_simplify, "smooth": out_smooth,
             "workload": cfg["name"] + ", scan lines every 0.1 mm", "layers": cfg["n_layers"],
             "contour_vertices": int(dev.n_verts), "segments": out["segments"],
             "ms_per_step": ms, "segments_per_s": out["segments"] / (ms / 1e3),
