@@ -1,7 +1,6 @@
 """Vertex re-positioning on the GPU (csl_support_optimize) against the FP64
 oracle: the same moves round by round, the same positions, and the paper's
 metrics before and after."""
-import math
 
 import numpy as np
 import pytest
