@@ -44,3 +44,23 @@ def test_two_gloo_ranks():
     for _, t_max, rate in res.values():
         assert t_max == 200.0                       # the slowest rank
         assert rate == pytest.approx(8000 * 10 * 3 * 2 / 0.2)
+
+
+def test_reference_arm_under_two_ranks():
+    """bench.py --impl reference launched as two ranks (torch.distributed.run,
+    on CPU): rank 0 times the oracle and prints one JSON line; the other rank
+    exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--workload", "cubic-bcc-812", "--steps", "1", "--warmup", "1"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
