@@ -46,3 +46,27 @@ def test_isolated_strut_is_hit_on_its_cylinder():
     t = V.cast(nodes, edges, radius, np.array([0.0, 0.0, 25.0]), np.array([0.0, 0.0, -1.0]),
                R=R, step=0.01, lo=lo, hi=hi)
     assert 5.0 - R < t < 5.0
+
+
+def test_near_ray_filter_drops_no_contributor(monkeypatch):
+    """The filter keeps every strut that can reach the ray's line: 24 random
+    rays through the cubic+BCC lattice give the same depths as a brute-force
+    cast over all struts."""
+    import synth
+    cfg = synth.config(1)
+    nodes, edges, radius, R = cfg["nodes"], cfg["edges"], cfg["radius"], cfg["R"]
+    lo = np.asarray(nodes, np.float32).min(0).astype(np.float64) - R
+    hi = np.asarray(nodes, np.float32).max(0).astype(np.float64) + R
+    r = synth.rng(31)
+    rays = []
+    for _ in range(24):
+        o = r.uniform(lo - 5.0, hi + 5.0)
+        tgt = r.uniform(lo, hi)
+        d = (tgt - o) / np.linalg.norm(tgt - o)
+        rays.append((o, d))
+    kw = dict(R=R, C=1.0, step=0.05, refine=12, lo=lo, hi=hi)
+    filtered = [V.cast(nodes, edges, radius, o, d, **kw) for o, d in rays]
+    monkeypatch.setattr(V, "near_ray", lambda nodes_, edges_, o_, d_, R_: np.arange(len(edges_)))
+    brute = [V.cast(nodes, edges, radius, o, d, **kw) for o, d in rays]
+    assert filtered == brute
+    assert sum(not math.isinf(t) for t in brute) >= 8
