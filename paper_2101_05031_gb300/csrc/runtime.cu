@@ -68,7 +68,7 @@ int64_t device_bytes_peak_and_reset() {
 }
 
 // Keep freed workspace in the stream-ordered pool instead of returning it to
-// the driver at every synchronisation (per process, per device).
+// the CUDA driver at every synchronisation (per process, per device).
 static void keep_pool_memory() {
     static thread_local int done_for = -1;
     int dev = 0;
