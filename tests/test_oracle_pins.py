@@ -76,6 +76,39 @@ def test_segment_integral_matches_quadrature():
     assert hits > 200
 
 
+def test_three_point_gauss_legendre_is_exact_on_the_clipped_interval():
+    """The GPU evaluates Eq. 7 by 3-point Gauss-Legendre on the clipped
+    interval [tau1, tau2]: in the edge's frame the kernel is (w^2 - tau^2)^2 / R^4,
+    a polynomial of degree 4, which the rule integrates exactly. Written
+    here in FP64 from the rule's nodes (0, +-sqrt(3/5)) and weights (8/9,
+    5/9), it must equal the oracle's closed form to rounding. A dropped or
+    wrongly weighted node, or a midpoint/half-width mix-up, is off by far
+    more."""
+    g = math.sqrt(0.6)
+    hits = 0
+    for p, a, b, R in _random_cases(400, 7):
+        u = b - a
+        L = float(np.linalg.norm(u))
+        u = u / L
+        t0 = float(np.dot(p - a, u))
+        e = p - a - t0 * u
+        h2 = R * R - float(np.dot(e, e))
+        gl = 0.0
+        if h2 > 0.0:
+            w = math.sqrt(h2)
+            t1, t2 = max(-t0, -w), min(L - t0, w)
+            if t2 > t1:
+                m, h = 0.5 * (t1 + t2), 0.5 * (t2 - t1)
+                f = lambda tau: (h2 - tau * tau) ** 2 / R ** 4
+                gl = h * (5.0 / 9.0 * (f(m - g * h) + f(m + g * h)) + 8.0 / 9.0 * f(m))
+        ref = oracle.segment_integral(p, a, b, R)
+        # to rounding of integrals of order 1 (the closed form subtracts quintics,
+        # so near the support's edge it carries ~1e-15 absolute)
+        assert gl == pytest.approx(ref, rel=1e-11, abs=1e-14)
+        hits += ref > 0
+    assert hits > 200
+
+
 def test_segment_integral_clip_cases():
     R = 1.0
     a, b = np.array([0.0, 0, 0]), np.array([0.0, 0, 3.0])
