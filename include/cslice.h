@@ -187,7 +187,7 @@ typedef struct csl_contours {
  *         desc->mask_out, when set, the bit-packed inside mask
  *   out   receives the contours (library-owned; csl_contours_free); may be
  *         NULL with CSL_SLICE_NO_CONTOURS
- * Errors: INVALID_ARG for n_layers < 0, dz <= 0 (when n_layers > 1),
+ * Errors: INVALID_ARG for n_layers < 0, a non-finite dz, dz <= 0 (when n_layers > 1),
  * pixel <= 0, nx or ny outside [1, 32000], a non-finite origin, an
  * unsupported tile/slab/chunk value. CAPACITY when an internal count exceeds
  * 32-bit range per streamed chunk. Synchronises the stream.
@@ -410,19 +410,26 @@ void csl_batch_free(csl_batch* b);
  *   desc                         z0, dz, n_layers (<= 65535), x0, y0, nx, ny,
  *                                pixel are used; everything else is ignored
  *   sigma_out                    device float[n_layers][ny][nx] (caller-owned)
- * Its only scratch is a fixed static device array that every GPU which loads
- * this library keeps until the process exits: 256 bytes plus 32 bytes per
+ * Its only scratch is a fixed static device array: 256 bytes plus 32 bytes per
  * edge for at most CSL_STATIC_MAX_EDGES edges (8 MiB + 256 bytes); larger
- * inputs are rejected with CSL_ERR_CAPACITY. The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture. Every call reuses the array (its status word is
- * cleared, its records rewritten): calls whose GPU work overlaps, on other
- * streams or host threads, race on it and must be serialised by the caller.
+ * inputs are rejected with CSL_ERR_CAPACITY. The array is reserved when the
+ * library's module is loaded on a device, which with CUDA's lazy loading (the
+ * default) happens at the first call on that device, and it stays reserved
+ * until the process exits. That first call also looks up the array's device
+ * address (cudaGetSymbolAddress), and the module load may allocate and
+ * synchronise: callers with a fixed memory plan make the first call during
+ * set-up, and always before any stream capture. The address is cached per
+ * CUDA context, so a call after cudaDeviceReset looks it up again. Every call
+ * reuses the array (its status word is cleared, its records rewritten): calls
+ * whose GPU work overlaps, on other streams or host threads, race on it and
+ * must be serialised by the caller.
  * Edges are summed in edge order (not z order), so values agree with
  * csl_slice_layers within FP32 rounding, not bit for bit.
  * Errors: INVALID_ARG for the csl_lattice_upload and csl_slice_layers input
- * errors (bad index, non-finite value, radius <= 0 or >= R in PHYSICAL mode),
- * reported after the GPU work, in which case sigma_out is unspecified.
+ * errors (bad index, a non-finite node coordinate (of any node) or radius,
+ * radius <= 0 or >= R in PHYSICAL mode; a non-finite dz, even for one layer),
+ * the device-side ones reported after the GPU work, in which case sigma_out is
+ * unspecified.
  * Synchronises the stream.
  */
 #define CSL_STATIC_MAX_EDGES 262144

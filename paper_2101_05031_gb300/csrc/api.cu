@@ -105,7 +105,9 @@ void validate_desc(const csl_slice_desc* d) {
             "nx, ny must be in [1, 32000]");
     require_arg(isfinite(d->pixel) && d->pixel > 0, "pixel must be > 0");
     require_arg(isfinite(d->x0) && isfinite(d->y0) && isfinite(d->z0), "non-finite origin");
-    require_arg(d->n_layers <= 1 || (isfinite(d->dz) && d->dz > 0), "dz must be > 0");
+    // layer k lies at z0 + k dz, so a non-finite dz poisons even a single layer
+    require_arg(isfinite(d->dz), "dz must be finite");
+    require_arg(d->n_layers <= 1 || d->dz > 0, "dz must be > 0");
 }
 
 }  // namespace csl

@@ -7,6 +7,7 @@
 // array: the status word is cleared at the start of every call, the records
 // are rewritten by every call, and two calls whose GPU work overlaps (other
 // streams, other host threads) race on it.
+#include <cuda.h>   // driver API types only: cuCtxGetCurrent/cuCtxGetId are fetched at run time
 #include <math.h>
 
 #include <mutex>
@@ -22,18 +23,53 @@ static_assert(sizeof(csl_rec) == 32, "record layout");
 
 __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-// Device address of g_static_scratch on the current device. Host code cannot
-// use the symbol's name as a device address, so it is looked up once per
-// device (the first call on a device does it; make that call before any
-// stream capture).
+// Device address of g_static_scratch in the current context. Host code cannot
+// use the symbol's name as a device address, so it is looked up with
+// cudaGetSymbolAddress once per device, with that device current, and cached.
+// With lazy module loading (the CUDA default) that first look-up also loads
+// this file's module and so reserves the array; it may allocate and
+// synchronise, so make the first call during set-up, before any stream
+// capture. The cache is keyed on the context's unique id: after a
+// cudaDeviceReset the next call runs in a new primary context, finds a
+// different id and looks the address up again instead of using a stale one.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) fail(CSL_ERR_CUDA, "driver entry points for the context id");
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        fail(CSL_ERR_CUDA, "no current CUDA context");
+    return id;
+}
+
 void* scratch_address() {
     static std::mutex mu;
     static void* addr[64] = {};
+    static unsigned long long ctx_of[64] = {};
     int dev = 0;
     CSL_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) fail(CSL_ERR_NOT_READY, "device index out of range");
+    CSL_CUDA(cudaSetDevice(dev));   // makes the device's primary context current (no allocation)
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || ctx_of[dev] != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
@@ -42,6 +78,7 @@ void* scratch_address() {
                                    cudaGetErrorString(e));
         }
         addr[dev] = p;
+        ctx_of[dev] = ctx;
     }
     return addr[dev];
 }
@@ -52,6 +89,10 @@ __global__ void k_static_prep(const float* __restrict__ nodes, int64_t n_nodes,
                               const int32_t* __restrict__ edges, const float* __restrict__ radius,
                               int64_t n_edges, double R, double C, int mode,
                               csl_rec* __restrict__ rec, uint32_t* status) {
+    // every node coordinate, as csl_lattice_upload checks, also those no edge uses
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n_nodes;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(nodes[i])) atomicOr(status, ST_NONFINITE);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_edges;
          j += (int64_t)gridDim.x * blockDim.x) {
         csl_rec r = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -235,7 +276,8 @@ extern "C" csl_status csl_field_layers_static(const float* nodes_xyz, int64_t n_
                 "nx, ny must be in [1, 32000]");
         require(isfinite(d.pixel) && d.pixel > 0, "pixel must be > 0");
         require(isfinite(d.x0) && isfinite(d.y0) && isfinite(d.z0), "non-finite origin");
-        require(d.n_layers <= 1 || (isfinite(d.dz) && d.dz > 0), "dz must be > 0");
+        require(isfinite(d.dz), "dz must be finite");   // layer k lies at z0 + k dz
+        require(d.n_layers <= 1 || d.dz > 0, "dz must be > 0");
         require(d.n_layers == 0 || sigma_out != nullptr, "sigma_out is NULL");
         if (d.n_layers == 0) return CSL_OK;
         cudaStream_t s = (cudaStream_t)stream;
@@ -243,8 +285,8 @@ extern "C" csl_status csl_field_layers_static(const float* nodes_xyz, int64_t n_
         uint32_t* status = (uint32_t*)base;
         csl_rec* rec = (csl_rec*)(base + kHeaderBytes);
         CSL_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
-        if (n_edges > 0) {
-            k_static_prep<<<grid_for(n_edges, 256), 256, 0, s>>>(
+        if (n_edges > 0 || n_nodes > 0) {
+            k_static_prep<<<grid_for(n_edges > 3 * n_nodes ? n_edges : 3 * n_nodes, 256), 256, 0, s>>>(
                 nodes_xyz, n_nodes, edges_ij, radius, n_edges, R, C, mode, rec, status);
             CSL_LAUNCH_CHECK("static prep");
         }

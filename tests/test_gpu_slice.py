@@ -65,6 +65,16 @@ def c1():
     return cfg, lat
 
 
+def test_non_finite_dz_is_refused_for_one_layer(c1):
+    """Layer k lies at z0 + k dz, so even a single layer needs a finite dz."""
+    cfg, lat = c1
+    import paper_2101_05031_gb300 as cs
+    for dz in (float("inf"), float("nan")):
+        with pytest.raises(cs.CslError, match="INVALID_ARG"):
+            lat.slice(z0=1.0, dz=dz, n_layers=1, x0=0.0, y0=0.0, nx=16, ny=16, pixel=0.1,
+                      contours=False, sigma_out=torch.empty((1, 16, 16), device="cuda"))
+
+
 def test_c1_full_parity(c1):
     """Configuration 1 in full (812 struts, 200x200 px, 50 layers)."""
     cfg, lat = c1
