@@ -134,6 +134,22 @@ void csl_lattice_free(csl_lattice* lat);
                                             then run one after another on the caller's stream */
 #define CSL_SLICE_COUNT_PAIRS 16         /* count (pixel, layer, edge) pairs with a nonzero term */
 
+/* Field kernels (Eq. 6-7 on the pixel grid; the results agree within FP32
+ * rounding, and bit for bit at the same tile size):
+ *   CSL_FIELD_BLOCK      every warp owns an 8 x 4-pixel block of a 16 x 16 tile
+ *                        and sums, for each edge whose support can reach the
+ *                        block, the term of all 32 pixels (suits supports of
+ *                        many pixels);
+ *   CSL_FIELD_FOOTPRINT  one warp per layer walks each edge's footprint in the
+ *                        layer plane (the rows or columns of pixels within R of
+ *                        its line), 32 footprint pixels per step (suits
+ *                        supports of a few pixels).
+ * CSL_FIELD_AUTO takes the footprint kernel on 32-pixel tiles when R is below
+ * 10 pixels, else the block kernel. */
+#define CSL_FIELD_AUTO 0
+#define CSL_FIELD_BLOCK 1
+#define CSL_FIELD_FOOTPRINT 2
+
 typedef struct csl_slice_desc {
     double z0, dz;            /* layer k is the plane z = z0 + k dz                     */
     int32_t n_layers;         /* >= 0                                                   */
@@ -142,10 +158,13 @@ typedef struct csl_slice_desc {
     double x0, y0;            /* pixel (i, j) has its centre at (x0 + (i + 1/2) pixel,  */
     double pixel;             /*                                 y0 + (j + 1/2) pixel)  */
     float* sigma_out;         /* optional device float[n_layers][ny][nx]: Sigma per pixel */
-    int32_t tile;             /* pixels per tile side: 0 (auto) or 16                   */
+    int32_t tile;             /* pixels per tile side: 0 (auto), 16 or 32 (32: footprint
+                                 kernel only)                                            */
     int32_t slab;             /* layers per slab: 0 (auto), 1, 2, 4 or 8               */
     int32_t chunk_layers;     /* layers per streamed chunk: 0 (auto) or a multiple of slab */
-    int32_t reserved_;
+    int16_t field_kernel;     /* CSL_FIELD_AUTO (0), CSL_FIELD_BLOCK or CSL_FIELD_FOOTPRINT */
+    int16_t stage_records;    /* footprint kernel: records per staged copy, 0 (256) or a
+                                 multiple of 32 up to 1024                               */
     uint32_t* mask_out;       /* optional device uint32[n_layers][ny][ceil(nx/32)]: the binary
                                  image of each layer (Sec. 4, the DLP mask): bit i % 32 of word
                                  [k][j][i / 32] is set when pixel (i, j) of layer k is inside

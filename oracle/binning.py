@@ -2,7 +2,7 @@
 
 The paper's streaming slicer keeps, per plane, the edges whose swept sphere of
 radius R meets the plane (Eq. 8). The GPU build widens that set to a slab of
-layers and splits it over 16x16-pixel tiles; which edges land in which tile
+layers and splits it over square tiles of 16 or 32 pixels; which edges land in which tile
 is a rule of the build, not of the paper. This module re-implements that rule
 independently, in numpy float32 with the same operation order, so that the
 GPU lists can be compared bit for bit, and gives the FP64 set of edges that
@@ -17,7 +17,7 @@ from double to float) and an edge with exact endpoints (ax, ay, zlo) ->
   t0 = max(((zf - m) - zlo) / (zhi - zlo), 0), t1 = min(((zl + m) - zlo) / (zhi - zlo), 1);
   x(t) = ax + t (bx - ax), y(t) likewise;
   box = [min(x(t0), x(t1)) - m, max(...) + m] x [same for y];
-  tiles floor((box - float(x0)) * float(1 / (16 pixel))) clipped to the grid.
+  tiles floor((box - float(x0)) * float(1 / (T pixel))) clipped to the grid, T the tile side.
 The margin is float(R + 8e-6 S + 1e-6), S the largest magnitude among the
 node bounding box, the grid corners and the first and last layer planes (and
 at least 1).
@@ -41,18 +41,18 @@ def margin(nodes, R, *, x0, y0, nx, ny, pixel, z0, dz, n_layers):
 
 
 def bin_lists_fp32(nodes, edges, R, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny,
-                   pixel):
+                   pixel, tile=TILE):
     """Edge ids (ascending) per tile of the slab; returns (tile_off, ids)."""
     f32 = np.float32
     nodes = np.asarray(nodes, dtype=np.float32).reshape(-1, 3)
     edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
     m = margin(nodes, R, x0=x0, y0=y0, nx=nx, ny=ny, pixel=pixel, z0=z0, dz=dz,
                n_layers=first_layer + n_slab_layers)
-    ntx, nty = -(-nx // TILE), -(-ny // TILE)
+    ntx, nty = -(-nx // tile), -(-ny // tile)
     zf = f32(z0 + first_layer * dz)
     zl = f32(z0 + (first_layer + n_slab_layers - 1) * dz)
     fx0, fy0 = f32(x0), f32(y0)
-    inv_tile = f32(1.0 / (TILE * pixel))
+    inv_tile = f32(1.0 / (tile * pixel))
     a = nodes[edges[:, 0]]
     b = nodes[edges[:, 1]]
     swap = b[:, 2] < a[:, 2]

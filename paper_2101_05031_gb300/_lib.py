@@ -24,6 +24,7 @@ SLICE_NO_CONTOURS = 4
 SLICE_TIME_KERNELS = 8
 SLICE_COUNT_PAIRS = 16
 STATIC_MAX_EDGES = 262144
+FIELD_KERNELS = {"auto": 0, "block": 1, "footprint": 2}   # csl_slice_desc.field_kernel
 BATCH_MAX_CANDIDATES = 16
 
 
@@ -41,7 +42,8 @@ class SliceDesc(ctypes.Structure):
     _fields_ = [("z0", c_f64), ("dz", c_f64), ("n_layers", c_i32), ("nx", c_i32), ("ny", c_i32),
                 ("flags", c_i32), ("x0", c_f64), ("y0", c_f64), ("pixel", c_f64),
                 ("sigma_out", c_vp), ("tile", c_i32), ("slab", c_i32), ("chunk_layers", c_i32),
-                ("reserved_", c_i32), ("mask_out", c_vp)]
+                ("field_kernel", ctypes.c_int16), ("stage_records", ctypes.c_int16),
+                ("mask_out", c_vp)]
 
 
 class Contours(ctypes.Structure):

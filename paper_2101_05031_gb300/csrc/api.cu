@@ -27,14 +27,30 @@ void require_arg(bool ok, const char* msg) {
 
 // Resolves tile / slab / chunk sizes and the rounding margins of the binner.
 SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
-    require_arg(d.tile == 0 || d.tile == kTile, "tile must be 0 or 16");
+    require_arg(d.tile == 0 || d.tile == 16 || d.tile == 32, "tile must be 0, 16 or 32");
+    require_arg(d.field_kernel == CSL_FIELD_AUTO || d.field_kernel == CSL_FIELD_BLOCK ||
+                    d.field_kernel == CSL_FIELD_FOOTPRINT,
+                "field_kernel must be CSL_FIELD_AUTO, CSL_FIELD_BLOCK or CSL_FIELD_FOOTPRINT");
+    require_arg(d.stage_records == 0 ||
+                    (d.stage_records >= 32 && d.stage_records <= 1024 && d.stage_records % 32 == 0),
+                "stage_records must be 0 or a multiple of 32 up to 1024");
     SlicePlan p;
+    // the footprint kernel where the support is a few pixels across (its lanes
+    // follow the support), the block kernel where it covers whole blocks
+    int kernel = d.field_kernel;
+    if (kernel == CSL_FIELD_AUTO)
+        kernel = (d.tile != 16 && L->R < 10.0 * d.pixel) ? CSL_FIELD_FOOTPRINT : CSL_FIELD_BLOCK;
+    require_arg(kernel == CSL_FIELD_FOOTPRINT || d.tile != 32,
+                "32-pixel tiles need the footprint field kernel");
+    p.kernel = kernel == CSL_FIELD_FOOTPRINT ? kFieldFootprint : kFieldBlock;
+    p.T = d.tile ? d.tile : (p.kernel == kFieldFootprint ? 32 : 16);
+    p.K = d.stage_records ? d.stage_records : 256;
     int S = d.slab;
     if (S == 0) S = d.n_layers >= 8 ? 8 : (d.n_layers >= 4 ? 4 : (d.n_layers >= 2 ? 2 : 1));
     require_arg(S == 1 || S == 2 || S == 4 || S == 8, "slab must be 0, 1, 2, 4 or 8");
     p.S = S;
-    p.ntx = (int)ceil_div(d.nx, kTile);
-    p.nty = (int)ceil_div(d.ny, kTile);
+    p.ntx = (int)ceil_div(d.nx, p.T);
+    p.nty = (int)ceil_div(d.ny, p.T);
     const int64_t plane = (int64_t)d.nx * d.ny;
     int chunk = d.chunk_layers;
     if (chunk == 0) {
@@ -85,6 +101,9 @@ ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SliceP
     g.R = L->R;
     g.margin_xy = p.margin;
     g.margin_z = p.margin;
+    g.T = p.T;
+    g.kernel = p.kernel;
+    g.K = p.K;
     return g;
 }
 

@@ -136,7 +136,8 @@ void plan_jobs(csl_batch* b, int S) {
     for (auto& J : b->jobs) {
         csl_slice_desc d = J.d;
         d.slab = S;
-        d.tile = 0;
+        d.tile = 16;                         // the persistent field kernel's tiles
+        d.field_kernel = CSL_FIELD_BLOCK;
         d.chunk_layers = d.n_layers;
         const SlicePlan p = make_plan(J.L, d);
         require_arg(p.chunk >= d.n_layers,

@@ -206,7 +206,7 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     BinConst c;
     c.fx0 = (float)g.x0;
     c.fy0 = (float)g.y0;
-    c.inv_tile = (float)(1.0 / ((double)kTile * g.px));
+    c.inv_tile = (float)(1.0 / ((double)g.T * g.px));
     c.mxy = g.margin_xy;
     c.mz = g.margin_z;
     c.ntx = g.ntx;

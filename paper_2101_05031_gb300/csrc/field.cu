@@ -312,11 +312,12 @@ __global__ void k_item_keys(const FieldJob* __restrict__ jobs, const uint2* __re
 // Corner of each tile column / row and first plane of each slab, computed in
 // double (non-fused) and split into a (hi, lo) float pair.
 __global__ void k_origins(float2* __restrict__ org, int ntx, int nty, int n_slabs, double x0,
-                          double y0, double z0, double px, double dz, int first_layer, int S) {
+                          double y0, double z0, double px, double dz, int first_layer, int S,
+                          int T) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v;
-    if (i < ntx) v = __dadd_rn(x0, __dmul_rn((double)(i * kTile), px));
-    else if (i < ntx + nty) v = __dadd_rn(y0, __dmul_rn((double)((i - ntx) * kTile), px));
+    if (i < ntx) v = __dadd_rn(x0, __dmul_rn((double)(i * T), px));
+    else if (i < ntx + nty) v = __dadd_rn(y0, __dmul_rn((double)((i - ntx) * T), px));
     else if (i < ntx + nty + n_slabs)
         v = __dadd_rn(z0, __dmul_rn((double)(first_layer + (i - ntx - nty) * S), dz));
     else return;
@@ -370,7 +371,7 @@ FieldConst make_field_const(const ChunkGeom& g, float C, const float2* org) {
 
 void launch_origins(const ChunkGeom& g, float2* org, cudaStream_t s) {
     k_origins<<<(unsigned)ceil_div(g.ntx + g.nty + g.n_slabs, 128), 128, 0, s>>>(
-        org, g.ntx, g.nty, g.n_slabs, g.x0, g.y0, g.z0, g.px, g.dz, g.first_layer, g.S);
+        org, g.ntx, g.nty, g.n_slabs, g.x0, g.y0, g.z0, g.px, g.dz, g.first_layer, g.S, g.T);
     CSL_LAUNCH_CHECK("origins");
 }
 
@@ -381,6 +382,12 @@ void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins,
     // tile and slab origins in double, each split into a (hi, lo) float pair
     DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
     launch_origins(g, org_d.as<float2>(), s);
+    if (g.kernel == kFieldFootprint) {
+        field_chunk_fp(g, bins, C, org_d.as<float2>(), L->status.as<uint32_t>(), sigma, mask,
+                       count_pairs, s);
+        return;
+    }
+    if (g.T != kTile) fail(CSL_ERR_INVALID_ARG, "the block field kernel takes 16-pixel tiles");
     FieldConst c = make_field_const(g, C, org_d.as<float2>());
     c.err = L->status.as<uint32_t>();
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
@@ -416,6 +423,8 @@ void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb,
     for (int j = 0; j < n_jobs; ++j) {
         const ChunkGeom& g = jobs[j].g;
         if (g.S != S) fail(CSL_ERR_INVALID_ARG, "batch: one slab depth for every job");
+        if (g.T != kTile || g.kernel != kFieldBlock)
+            fail(CSL_ERR_INVALID_ARG, "batch: the persistent field kernel takes 16-pixel tiles");
         n_org += (size_t)g.ntx + g.nty + g.n_slabs;
         off[j + 1] = off[j] + (int64_t)g.n_slabs * g.ntx * g.nty;
     }

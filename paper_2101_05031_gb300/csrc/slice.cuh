@@ -7,8 +7,14 @@
 
 namespace csl {
 
-constexpr int kTile = 16;        // pixels per tile side
+constexpr int kTile = 16;        // pixels per tile side of the block field kernel
 constexpr int kFieldThreads = 256;
+
+// Field kernels: the pixel-block kernel (field.cu: warps own 8 x 4-pixel
+// blocks of a 16 x 16 tile, sums in registers) and the footprint kernel
+// (field_fp.cu: a warp per layer walks each edge's footprint, sums in shared
+// memory; tiles of 16 or 32 pixels).
+enum FieldKernel : int32_t { kFieldBlock = 1, kFieldFootprint = 2 };
 
 // Geometry of one streamed chunk of layers.
 struct ChunkGeom {
@@ -21,6 +27,10 @@ struct ChunkGeom {
     double R;
     float margin_xy;   // xy expansion of a clipped edge's box (R plus rounding slack)
     float margin_z;    // z expansion (R plus rounding slack)
+    // tile side in pixels, field kernel, records per staged copy (footprint kernel)
+    int32_t T = kTile;
+    int32_t kernel = kFieldBlock;
+    int32_t K = 256;
 };
 
 // Per-slab binning results (device).
@@ -64,6 +74,10 @@ inline int64_t mask_words_per_layer(int nx, int ny) {
 // terms that are nonzero, [1] += the number of terms evaluated.
 void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
                  float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s);
+// The footprint kernel's launch (field_fp.cu); org: the chunk's origin tables.
+void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const float2* org,
+                    uint32_t* err, float* sigma, uint32_t* mask, unsigned long long* count_pairs,
+                    cudaStream_t s);
 
 // Field of many chunks (the jobs of a batch, one chunk each) in one
 // persistent launch: CTAs take (job, slab, tile) items from a queue sorted
@@ -106,6 +120,7 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
 struct SlicePlan {
     int S, chunk, ntx, nty;
     float margin;
+    int T, kernel, K;
 };
 SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d);
 ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SlicePlan& p, int first,

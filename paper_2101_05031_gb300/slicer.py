@@ -244,24 +244,29 @@ class Lattice:
         _lib.check(_lib.load().csl_lattice_update(self._h, pn, pr, _stream_ptr(stream)))
 
     def _desc(self, z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab, chunk_layers,
-              mask_out=None):
+              mask_out=None, tile=0, field_kernel="auto", stage_records=0):
         d = _lib.SliceDesc()
         d.mask_out = ctypes.c_void_p(mask_out.data_ptr()) if mask_out is not None else None
         d.z0, d.dz, d.n_layers = float(z0), float(dz), int(n_layers)
         d.nx, d.ny, d.flags = int(nx), int(ny), int(flags)
         d.x0, d.y0, d.pixel = float(x0), float(y0), float(pixel)
         d.sigma_out = ctypes.c_void_p(sigma_out.data_ptr()) if sigma_out is not None else None
-        d.tile, d.slab, d.chunk_layers = 0, int(slab), int(chunk_layers)
+        d.tile, d.slab, d.chunk_layers = int(tile), int(slab), int(chunk_layers)
+        d.field_kernel = _lib.FIELD_KERNELS[field_kernel]
+        d.stage_records = int(stage_records)
         return d
 
     def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None, mask_out=None,
               contours=True, on_device=False, edge_ids=False, slab=0, chunk_layers=0,
-              time_kernels=False, count_pairs=False, stream=None):
+              time_kernels=False, count_pairs=False, stream=None, tile=0, field_kernel="auto",
+              stage_records=0):
         """csl_slice_layers. sigma_out: optional CUDA float32 tensor
         [n_layers, ny, nx] that receives Sigma; mask_out: optional CUDA int32
         tensor [n_layers, ny, ceil(nx / 32)] that receives the bit-packed inside
-        mask (bit i % 32 of word i / 32: pixel i inside). Returns a ContourSet (host),
-        a DeviceContours (on_device=True) or None (contours=False)."""
+        mask (bit i % 32 of word i / 32: pixel i inside). field_kernel: "auto",
+        "block" or "footprint"; tile: 0 (auto), 16 or 32; stage_records: records
+        per staged copy of the footprint kernel (0: 256). Returns a ContourSet
+        (host), a DeviceContours (on_device=True) or None (contours=False)."""
         if sigma_out is not None:
             if not (sigma_out.is_cuda and sigma_out.dtype == torch.float32
                     and sigma_out.is_contiguous()
@@ -286,7 +291,7 @@ class Lattice:
         if count_pairs:
             flags |= _lib.SLICE_COUNT_PAIRS
         d = self._desc(z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab,
-                       chunk_layers, mask_out)
+                       chunk_layers, mask_out, tile, field_kernel, stage_records)
         out = ctypes.POINTER(_lib.Contours)()
         _lib.check(_lib.load().csl_slice_layers(self._h, ctypes.byref(d), _stream_ptr(stream),
                                                 ctypes.byref(out)))
@@ -297,11 +302,12 @@ class Lattice:
         return _host_contours(out)
 
     def slab_bins(self, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny, pixel,
-                  stream=None):
-        """Binner output for one slab: (tile_off[n_tiles+1], edge ids sorted per tile)."""
+                  tile=16, stream=None):
+        """Binner output for one slab of tiles of `tile` pixels (16 or 32):
+        (tile_off[n_tiles+1], edge ids sorted per tile)."""
         d = self._desc(z0, dz, first_layer + n_slab_layers, x0, y0, nx, ny, pixel, 0, None,
-                       0, 0)
-        n_tiles = ((int(nx) + 15) // 16) * ((int(ny) + 15) // 16)
+                       0, 0, tile=tile, field_kernel="footprint" if tile == 32 else "auto")
+        n_tiles = ((int(nx) + tile - 1) // tile) * ((int(ny) + tile - 1) // tile)
         off = np.zeros(n_tiles + 1, np.int64)
         n = ctypes.c_int64()
         lib = _lib.load()

@@ -33,10 +33,12 @@ def _jobs(n_layers=12):
 
 
 def _per_job(lat, d, slab):
+    """Per-job slicing with the batch's field kernel (the block kernel on
+    16-pixel tiles), so that both sum the same terms in the same order."""
     sig = torch.empty((d["n_layers"], d["ny"], d["nx"]), dtype=torch.float32, device="cuda")
     cont = lat.slice(z0=d["z0"], dz=d["dz"], n_layers=d["n_layers"], x0=d["x0"], y0=d["y0"],
                      nx=d["nx"], ny=d["ny"], pixel=d["pixel"], sigma_out=sig, edge_ids=True,
-                     slab=slab)
+                     slab=slab, field_kernel="block", tile=16)
     torch.cuda.synchronize()
     return sig, cont
 

@@ -164,3 +164,107 @@ def test_cells_beyond_every_strut_support(c5):
     assert float(vf.abs().max()) <= 1e-30
     gr, gn = volume_fraction_backward(lat, cells, torch.ones((2, 3, 4), device="cuda"))
     assert int(torch.count_nonzero(gr)) == 0 and int(torch.count_nonzero(gn)) == 0
+
+
+# ---- iso-value C != 1 and RAW weights: T is absolute, dw/drho carries C ----
+
+@pytest.mark.parametrize("mode,C,T", [("physical", 1.7, 0.017), ("raw", 0.12, 0.0012)])
+def test_vf_parity_at_other_iso_values_and_raw_weights(mode, C, T):
+    """Forward and adjoint at C = 1.7 (T = 0.01 C as an absolute 0.017) and in
+    RAW mode (radius taken as the weight r_i of Eq. 6, C = 0.12): an error that
+    scales T by C, or drops C from dw/drho, fails here."""
+    import paper_2101_05031_gb300 as cs
+    from paper_2101_05031_gb300 import volume_fraction, volume_fraction_backward
+    cfg = synth.config(5, small=True)
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=C, mode=mode)
+    om = oracle.RAW if mode == "raw" else oracle.PHYSICAL
+    cells = _cells(cfg, T=T)
+    vf = volume_fraction(lat, cells).cpu().numpy().ravel()
+    ids = np.random.default_rng(5).choice(vf.size, 50, replace=False)
+    ref = oracle.volume_fraction(cfg["nodes"], cfg["edges"], cfg["radius"], cells, R=cfg["R"],
+                                 C=C, mode=om, ids=ids)
+    # T = 0.01 C in both cases, so the bound of VF_ATOL holds as it is
+    assert np.max(np.abs(vf[ids] - ref)) <= VF_ATOL
+    assert 0.02 < vf.max() <= 1.0
+    dims = cells["dims"]
+    n = dims[0] * dims[1] * dims[2]
+    r = np.random.default_rng(6)
+    sel = np.sort(r.choice(n, 40, replace=False))
+    g = np.zeros(n, np.float32)
+    g[sel] = r.normal(size=sel.size).astype(np.float32)
+    gr, gn = volume_fraction_backward(lat, cells, torch.from_numpy(g.reshape(dims[::-1])).cuda())
+    ref_r, ref_n = oracle.vf_backward(cfg["nodes"], cfg["edges"], cfg["radius"], cells,
+                                      g[sel].astype(np.float64), R=cfg["R"], C=C, mode=om,
+                                      ids=sel)
+    assert np.linalg.norm(ref_r) > 0
+    assert _rel(gr.cpu().numpy().astype(np.float64), ref_r) <= GRAD_RTOL
+    assert _rel(gn.cpu().numpy().astype(np.float64), ref_n) <= GRAD_RTOL
+
+
+# ---- the adjoint against finite differences of the GPU's own forward ----
+
+def _cell_block(cells, lo, hi, R):
+    """The cells whose samples can lie within R of the box [lo, hi]."""
+    o = np.asarray(cells["origin"], np.float64)
+    h = cells["h"]
+    dims = np.asarray(cells["dims"])
+    a = np.clip(np.floor((lo - R - o) / h).astype(int) - 1, 0, dims - 1)
+    b = np.clip(np.floor((hi + R - o) / h).astype(int) + 1, 0, dims - 1)
+    return a, b
+
+
+def test_adjoint_matches_finite_differences_of_the_gpu_forward():
+    """On the 1M-strut lattice (64^3 cells x 8^3 samples, T = 0.01): the
+    adjoint's d(sum g vf)/d(rho_j) against a Richardson-extrapolated central
+    difference (h = 1e-4 mm and h/2) of the GPU's own forward, on 1000 random
+    struts. Each difference runs the forward on the block of cells the strut
+    can reach (the others do not change).
+
+    The forward is FP32: a cell mean of 512 sigmoids carries a rounding error
+    of a few 1e-7, while a step of 1e-4 mm moves a cell's vf by about 1e-4, so
+    the difference quotient is good to a few 1e-3, not to the 1e-4 that the
+    adjoint reaches against the FP64 analytic gradient (test_vf_backward_parity
+    and the parity tests at other iso-values). The bounds here sit above that
+    noise floor (measured 4e-3 in the norm)."""
+    import paper_2101_05031_gb300 as cs
+    from paper_2101_05031_gb300 import volume_fraction, volume_fraction_backward
+    cfg = synth.config(5)
+    cells = cfg["cells"]
+    R = cfg["R"]
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=R)
+    dims = cells["dims"]
+    gen = np.random.default_rng(7)
+    g = gen.normal(size=(dims[2], dims[1], dims[0])).astype(np.float32)
+    gr, _ = volume_fraction_backward(lat, cells, torch.from_numpy(g).cuda())
+    gr = gr.cpu().numpy().astype(np.float64)
+    rad = torch.from_numpy(cfg["radius"].copy()).cuda()
+    nodes = cfg["nodes"].astype(np.float64)
+    ids = gen.choice(cfg["edges"].shape[0], 1000, replace=False)
+    h0 = 1e-4
+
+    def loss_block(j, d_rho, a, b):
+        r2 = rad.clone()
+        r2[j] += d_rho
+        lat.update(radius=r2)
+        blk = dict(cells, origin=tuple(np.asarray(cells["origin"]) + cells["h"] * a),
+                   dims=tuple(int(v) for v in (b - a + 1)))
+        v = volume_fraction(lat, blk).cpu().numpy().astype(np.float64)
+        gb = g[a[2]:b[2] + 1, a[1]:b[1] + 1, a[0]:b[0] + 1].astype(np.float64)
+        return float(np.sum(gb * v))
+
+    fd, ad = [], []
+    for j in ids:
+        e = cfg["edges"][j]
+        lo = np.minimum(nodes[e[0]], nodes[e[1]])
+        hi = np.maximum(nodes[e[0]], nodes[e[1]])
+        a, b = _cell_block(cells, lo, hi, R)
+        d1 = (loss_block(j, h0, a, b) - loss_block(j, -h0, a, b)) / (2 * h0)
+        d2 = (loss_block(j, h0 / 2, a, b) - loss_block(j, -h0 / 2, a, b)) / h0
+        fd.append((4 * d2 - d1) / 3)
+        ad.append(gr[j])
+    lat.update(radius=rad)
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.linalg.norm(ad) > 0
+    assert _rel(ad, fd) <= 1e-2, _rel(ad, fd)
+    big = np.abs(fd) > 1e-2 * np.abs(fd).max()
+    assert np.median(np.abs(ad - fd)[big] / np.abs(fd)[big]) <= 5e-3
