@@ -31,9 +31,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixel-evals/s and layers/s at 10M and 100M struts; backward/forward time ratio"
 F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the field kernel
-# FP32 instructions the field kernel executes per cycle as a fraction of the
-# FP32 peak (every evaluated lane), from an ncu capture of one launch
-NCU_FIELD_EXECUTED_FRAC = 8422.3 / (152 * 128 * 2)
+# Per field kernel, from an ncu capture of one launch on the 12.96M-strut
+# graded lattice (profiles/): the FP32 instructions it executes per cycle as a
+# fraction of the FP32 peak (every evaluated lane), and its DRAM bytes (read +
+# write) per pixel-layer (scaled by pixel-layers to a launch of the timed
+# workload). None where no capture of the current kernel exists.
+NCU_FIELD = {
+    "block": {"kernel": "k_field", "executed_frac": 8422.3 / (152 * 128 * 2),
+              "dram_bytes_per_pixel_layer": 1.2835e9 / (64 * 2000 * 2000),
+              "profile": "profiles/k_field_graded-10M.txt"},
+    "footprint": {"kernel": "k_field_fp", "executed_frac": None,
+                  "dram_bytes_per_pixel_layer": None,
+                  "profile": "profiles/k_field_fp_graded-10M.txt"},
+}
 HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
 # algorithmic bytes of the HBM-bound stages
 BIN_BYTES_PER_WINDOW_RECORD = 24   # xy box (16) + z range (8) of a record read per slab window
@@ -41,10 +51,6 @@ BIN_BYTES_PER_ENTRY = 8            # (key, record) of a bin entry written
 MS_BYTES_PER_PIXEL = 0.125         # inside-mask bit of a pixel read
 MS_BYTES_PER_CROSSING = 16         # two Sigma values read, the vertex (x, y) written
 MS_BYTES_PER_LOOP = 8              # the loop's vertex offset written
-# DRAM bytes (read + write) per pixel-layer of one field-kernel launch, from an
-# ncu capture of the current field kernel on the 12.96M-strut graded lattice
-# (1.28 GB for 64 layers of 2000 x 2000 pixels); scaled by pixel-layers.
-FIELD_DRAM_BYTES_PER_PIXEL_LAYER = 1.2835e9 / (64 * 2000 * 2000)
 N_SM = 152
 FP32_LANES = 128
 MAX_SM_MHZ = 2070.0
@@ -236,8 +242,9 @@ def radius_tuning(lat, cfg, iterations=20):
         loss = 0.5 * ((vf - target) ** 2).sum()
         loss.backward()
         with torch.no_grad():
-            if lr is None:   # a first step of at most 0.02 mm on any strut
-                lr = 0.02 / max(float(r.grad.abs().max()), 1e-12)
+            if lr is None:   # a first step of 0.01 mm at the 90th percentile of |grad|
+                g90 = float(torch.quantile(r.grad.abs()[::16].float(), 0.9))
+                lr = 0.01 / max(g90, 1e-12)
             r = (r - lr * r.grad).clamp(0.1, 0.9 * R)
         losses.append(loss.detach())
     e1.record(stream)
@@ -248,8 +255,9 @@ def radius_tuning(lat, cfg, iterations=20):
     return {"iterations": iterations, "ms_per_iteration": ms, "loss": curve,
             "loss_drop": curve[0] / max(curve[-1], 1e-30),
             "basis": "VolumeFraction.apply (lattice update + forward) and backward per "
-                     "iteration, CUDA events over all iterations; step 0.02 mm / max |grad| "
-                     "fixed at the first iteration"}
+                     "iteration, CUDA events over all iterations; step 0.01 mm / (90th "
+                     "percentile of |grad|) fixed at the first iteration, radii clamped to "
+                     "[0.1, 0.9 R]"}
 
 
 def run_vf(steps, warmup):
@@ -658,6 +666,11 @@ def main():
 
     for _ in range(args.warmup):
         step()
+    peak_main = cs.last_stats().device_bytes_peak
+    st0 = cs.last_stats()
+    plan = {"field_kernel": {1: "block", 2: "footprint"}.get(st0.field_kernel, "?"),
+            "tile": st0.tile, "slab": st0.slab, "stage_records": st0.stage_records,
+            "fused": bool(st0.fused)}
     # exact count of nonzero and of evaluated terms, once, outside the timed region
     pairs = evaluated = cand = 0
     if not args.no_count:
@@ -696,6 +709,7 @@ def main():
     clocks = clk.summary()
 
     # roofline of the field kernel: FP32 ALU
+    ncu = NCU_FIELD[plan["field_kernel"]]
     t_field = field_ms / max(field_launches, 1) / 1e3            # s per launch
     flops_per_launch = pairs * F_PAIR / max(field_launches, 1)
     achieved = flops_per_launch / t_field / 1e12 if t_field > 0 else 0.0
@@ -703,10 +717,11 @@ def main():
     px_layers_per_launch = cfg["nx"] * cfg["ny"] * cfg["n_layers"] / max(field_launches, 1)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": FIELD_DRAM_BYTES_PER_PIXEL_LAYER * px_layers_per_launch,
+            "traffic": (ncu["dram_bytes_per_pixel_layer"] * px_layers_per_launch
+                        if ncu["dram_bytes_per_pixel_layer"] else None),
             "traffic_basis": "ncu dram bytes of one field launch on the 12.96M-strut graded "
                              "lattice, scaled by pixel-layers per launch",
-            "kernel": "k_field", "flops_per_term": F_PAIR,
+            "kernel": ncu["kernel"], "flops_per_term": F_PAIR,
             "nonzero_terms_per_step": pairs, "evaluated_terms_per_step": evaluated,
             "candidate_entries_per_step": cand,
             "field_share_of_step": field_ms / staged_ms if staged_ms > 0 else None,
@@ -718,10 +733,10 @@ def main():
     # check of the derived peak: an FFMA microbenchmark of the library on this GPU
     ffma_tflops, _ = cs.measure_fp32_peak()
     roof["peak_check_ffma_microbenchmark_tflops"] = ffma_tflops
-    roof["executed_frac_ncu"] = NCU_FIELD_EXECUTED_FRAC
+    roof["executed_frac_ncu"] = ncu["executed_frac"]
     roof["executed_basis"] = ("ncu FFMA + FADD + FMUL thread instructions per cycle of one "
                               "field launch on the 12.96M-strut graded lattice, every evaluated "
-                              "lane included (profiles/k_field_graded-10M.txt)")
+                              f"lane included ({ncu['profile']})")
     # the HBM-bound stages, against the measured copy bandwidth: algorithmic
     # bytes (the minimum each stage must move) over its event-timed duration
     px_layers = cfg["nx"] * cfg["ny"] * cfg["n_layers"]
@@ -760,6 +775,25 @@ def main():
                                            "another; the timed steps overlap two chunks"},
             "setup_s": {"generate": t_gen, "upload_and_sort": t_up}}
 
+    line["slice_workspace_peak_bytes"] = int(peak_main)
+    line["plan"] = plan
+    if world == 1 and not args.no_extra and plan["field_kernel"] == "footprint":
+        # the same slice with the fused field and contour pass (no Sigma plane):
+        # time per step and workspace, beside the default (Sigma plane)
+        kw_u = dict(kw, fused=True)
+        lat.slice(**kw_u, on_device=True).free()
+        peak_u = cs.last_stats().device_bytes_peak
+        u_ms = _event_ms(lambda: lat.slice(**kw_u, on_device=True).free(), args.steps, 1,
+                         stream)
+        line["fused_vs_unfused"] = {
+            "fused_ms_per_step": u_ms, "unfused_ms_per_step": t_max / args.steps,
+            "fused_workspace_peak_bytes": int(peak_u),
+            "unfused_workspace_peak_bytes": int(peak_main),
+            "basis": "the same steps through csl_slice_layers with CSL_SLICE_FUSED (each "
+                     "tile's crossing vertices from shared memory, no Sigma plane) and without "
+                     "(the default: Sigma plane, marching squares reads it); contours kept on "
+                     "the device; workspace = largest device memory the call held at once"}
+
     if not args.no_e2e:
         # end to end through the public API: pinned host inputs, upload + prepare,
         # slice, contours copied back to host memory
@@ -768,9 +802,12 @@ def main():
         pr = torch.from_numpy(cfg["radius"]).pin_memory()
         h2d = pn.numel() * 4 + pe.numel() * 4 + pr.numel() * 4
 
+        e2e_peak = [0]
+
         def e2e_step():
             L2 = cs.Lattice(pn, pe, pr, R=cfg["R"], C=cfg["C"])
             cont = L2.slice(**kw)
+            e2e_peak[0] = cs.last_stats().device_bytes_peak
             nbytes = cont.layer_loop_off.nbytes + cont.loop_vert_off.nbytes + cont.xy.nbytes
             L2.close()
             del cont
@@ -794,7 +831,8 @@ def main():
         line["e2e"] = {"value": whole_job_rate(px_per_step, 1, world, e2e_ms),
                        "unit": "pixel-evals/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "ms_per_step": e2e_ms, "wall_ms_each_step": wall}
+                       "ms_per_step": e2e_ms, "wall_ms_each_step": wall,
+                       "slice_workspace_peak_bytes": int(e2e_peak[0])}
 
     if world == 1 and not args.no_extra:
         # self-support metrics (Eq. 11-14) of the same lattice, printing along z

@@ -133,6 +133,14 @@ void csl_lattice_free(csl_lattice* lat);
 #define CSL_SLICE_TIME_KERNELS 8         /* time each stage with CUDA events (csl_stats); the chunks
                                             then run one after another on the caller's stream */
 #define CSL_SLICE_COUNT_PAIRS 16         /* count (pixel, layer, edge) pairs with a nonzero term */
+#define CSL_SLICE_FUSED 32               /* footprint kernel with contours: the fused field and
+                                            contour pass. The field kernel evaluates each tile with
+                                            its next column and row and leaves the tile's crossing
+                                            vertices (from Sigma in shared memory) and saddle bits
+                                            instead of a Sigma plane: less device memory, the same
+                                            contours bit for bit; without it (the default) a Sigma
+                                            plane is written and marching squares reads it, which
+                                            is faster when the field kernel is issue-bound */
 
 /* Field kernels (Eq. 6-7 on the pixel grid; the results agree within FP32
  * rounding, and bit for bit at the same tile size):
@@ -473,6 +481,10 @@ typedef struct csl_stats {
     double output_ms;         /* ... of gathering the chunks into the result          */
     int64_t evaluated_terms;  /* terms the field kernel evaluated (CSL_SLICE_COUNT_PAIRS) */
     int64_t window_records;   /* records the binner examined (the slabs' z windows, summed) */
+    /* the plan the call resolved: field kernel (CSL_FIELD_BLOCK or CSL_FIELD_FOOTPRINT),
+       tile side, slab depth, records per staged copy, fused pass (0 or 1) */
+    int32_t field_kernel, tile, slab, stage_records;
+    int32_t fused, reserved_;
 } csl_stats;
 csl_status csl_last_stats(csl_stats* out);
 

@@ -17,7 +17,9 @@ from double to float) and an edge with exact endpoints (ax, ay, zlo) ->
   t0 = max(((zf - m) - zlo) / (zhi - zlo), 0), t1 = min(((zl + m) - zlo) / (zhi - zlo), 1);
   x(t) = ax + t (bx - ax), y(t) likewise;
   box = [min(x(t0), x(t1)) - m, max(...) + m] x [same for y];
-  tiles floor((box - float(x0)) * float(1 / (T pixel))) clipped to the grid, T the tile side.
+  tiles floor((box - float(x0)) * float(1 / (T pixel))) clipped to the grid, T the tile side;
+  with a one-pixel halo (tiles that also evaluate their next column and row), the
+  box's low corner is first lowered by float(pixel).
 The margin is float(R + 8e-6 S + 1e-6), S the largest magnitude among the
 node bounding box, the grid corners and the first and last layer planes (and
 at least 1).
@@ -41,7 +43,7 @@ def margin(nodes, R, *, x0, y0, nx, ny, pixel, z0, dz, n_layers):
 
 
 def bin_lists_fp32(nodes, edges, R, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny,
-                   pixel, tile=TILE):
+                   pixel, tile=TILE, halo=False):
     """Edge ids (ascending) per tile of the slab; returns (tile_off, ids)."""
     f32 = np.float32
     nodes = np.asarray(nodes, dtype=np.float32).reshape(-1, 3)
@@ -75,6 +77,9 @@ def bin_lists_fp32(nodes, edges, R, *, z0, dz, first_layer, n_slab_layers, x0, y
     ya, yb = lo[:, 1] + t0 * ey, lo[:, 1] + t1 * ey
     xmin, xmax = np.minimum(xa, xb) - m, np.maximum(xa, xb) + m
     ymin, ymax = np.minimum(ya, yb) - m, np.maximum(ya, yb) + m
+    if halo:
+        xmin = xmin - f32(pixel)
+        ymin = ymin - f32(pixel)
     gx0 = np.floor((xmin - fx0) * inv_tile)
     gx1 = np.floor((xmax - fx0) * inv_tile)
     gy0 = np.floor((ymin - fy0) * inv_tile)

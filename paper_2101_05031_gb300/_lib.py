@@ -23,6 +23,7 @@ SLICE_EDGE_IDS = 2
 SLICE_NO_CONTOURS = 4
 SLICE_TIME_KERNELS = 8
 SLICE_COUNT_PAIRS = 16
+SLICE_FUSED = 32
 STATIC_MAX_EDGES = 262144
 FIELD_KERNELS = {"auto": 0, "block": 1, "footprint": 2}   # csl_slice_desc.field_kernel
 BATCH_MAX_CANDIDATES = 16
@@ -62,7 +63,9 @@ class Stats(ctypes.Structure):
                 ("chunks", c_i64), ("device_bytes_peak", c_i64), ("kernel_launches", c_i64),
                 ("field_launches", c_i64), ("field_ms", c_f64), ("contributing_pairs", c_i64),
                 ("bin_ms", c_f64), ("contour_ms", c_f64), ("output_ms", c_f64),
-                ("evaluated_terms", c_i64), ("window_records", c_i64)]
+                ("evaluated_terms", c_i64), ("window_records", c_i64),
+                ("field_kernel", c_i32), ("tile", c_i32), ("slab", c_i32),
+                ("stage_records", c_i32), ("fused", c_i32), ("reserved_", c_i32)]
 
 
 class Voxels(ctypes.Structure):

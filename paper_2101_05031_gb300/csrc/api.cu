@@ -82,6 +82,11 @@ SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d) {
     return p;
 }
 
+bool wants_fused(const csl_slice_desc& d, const SlicePlan& p) {
+    return p.kernel == kFieldFootprint && !(d.flags & CSL_SLICE_NO_CONTOURS) &&
+           (d.flags & CSL_SLICE_FUSED);
+}
+
 ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SlicePlan& p, int first,
                      int n) {
     ChunkGeom g;
@@ -104,6 +109,7 @@ ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SliceP
     g.T = p.T;
     g.kernel = p.kernel;
     g.K = p.K;
+    g.fused = p.fused;
     return g;
 }
 
@@ -416,9 +422,15 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         const bool want_eid = (d.flags & CSL_SLICE_EDGE_IDS) != 0;
         cudaStream_t s = (cudaStream_t)stream;
         SlicePlan p = make_plan(L, d);
+        p.fused = wants_fused(d, p);
         device_bytes_peak_and_reset();
         launches_and_reset();
         csl_stats st = {};
+        st.field_kernel = p.kernel == kFieldFootprint ? CSL_FIELD_FOOTPRINT : CSL_FIELD_BLOCK;
+        st.tile = p.T;
+        st.slab = p.S;
+        st.stage_records = p.K;
+        st.fused = p.fused ? 1 : 0;
         const bool time_kernels = (d.flags & CSL_SLICE_TIME_KERNELS) != 0;
         const bool count_pairs = (d.flags & CSL_SLICE_COUNT_PAIRS) != 0;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -477,15 +489,29 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             streams[1] = side.s2;
         }
         DevBuf sigma_ws[2], mask_ws[2];
+        FusedVerts fv_ws[2];
         const int chunk_alloc = std::min(p.chunk, std::max(d.n_layers, 1));
         const int64_t mask_layer = mask_words_per_layer(d.nx, d.ny);
+        const int64_t n_tiles = (int64_t)p.ntx * p.nty;
         for (int b = 0; b < n_par; ++b) {
             // without contours nothing reads the Sigma plane: the field kernel
-            // then writes only the mask (the binary image) unless sigma_out is set
-            if (!d.sigma_out && want_contours && d.n_layers > 0)
+            // then writes only the mask (the binary image) unless sigma_out is
+            // set; the fused pass leaves vertex lists instead of a plane
+            if (!d.sigma_out && want_contours && !p.fused && d.n_layers > 0)
                 sigma_ws[b].alloc((size_t)chunk_alloc * plane * 4, streams[b]);
             if ((want_contours || d.mask_out) && d.n_layers > 0)
                 mask_ws[b].alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
+            if (p.fused && d.n_layers > 0) {
+                FusedVerts& f = fv_ws[b];
+                f.tbase.alloc((size_t)chunk_alloc * n_tiles * 4, streams[b]);
+                f.roff.alloc((size_t)chunk_alloc * n_tiles * (p.T + 1) * 2, streams[b]);
+                f.saddle.alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
+                f.counter.alloc(8, streams[b]);
+                // first guess: a crossing per 4 pixel-layers (grown on overflow)
+                f.cap = std::max<int64_t>((int64_t)1 << 20, (int64_t)chunk_alloc * plane / 4);
+                f.cap = std::min<int64_t>(f.cap, 0xffffffffLL);
+                f.verts.alloc((size_t)f.cap * 8, streams[b]);
+            }
         }
 
         std::vector<ChunkContours> dev_chunks;
@@ -522,11 +548,11 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         auto contour_stage = [&](int k, const ChunkGeom& g) {
             cudaStream_t ks = streams[k % n_par];
             const float* sigma = d.sigma_out ? d.sigma_out + (int64_t)g.first_layer * plane
-                                             : sigma_ws[k % n_par].as<float>();
+                                             : sigma_ws[k % n_par].as<float>();   // null: fused
             ChunkContours cc;
             timed(st.contour_ms, [&] {
                 contours_chunk(g, L->C, sigma, mask_ws[k % n_par].as<uint32_t>(), want_eid, cc,
-                               ks);
+                               ks, nullptr, p.fused ? &fv_ws[k % n_par] : nullptr);
             });
             st.crossings += cc.n_verts;
             st.loops += cc.n_loops;
@@ -628,12 +654,37 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 st.window_records += bins.n_cand;
                 uint32_t* mask = (want_contours || d.mask_out) ? mask_ws[k % n_par].as<uint32_t>()
                                                                : nullptr;
-                if (mask)
-                    CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, ks));
-                timed(st.field_ms, [&] {
-                    field_chunk(LB, g, bins, (float)L->C, sigma, mask,
-                                count_pairs ? pair_count.as<unsigned long long>() : nullptr, ks);
-                });
+                FusedVerts* fv = p.fused ? &fv_ws[k % n_par] : nullptr;
+                auto run_field = [&] {
+                    if (mask) CSL_CUDA(cudaMemsetAsync(mask, 0, (size_t)n * mask_layer * 4, ks));
+                    if (fv) {
+                        CSL_CUDA(cudaMemsetAsync(fv->saddle.get(), 0, (size_t)n * mask_layer * 4, ks));
+                        CSL_CUDA(cudaMemsetAsync(fv->counter.get(), 0, 8, ks));
+                    }
+                    timed(st.field_ms, [&] {
+                        field_chunk(LB, g, bins, (float)L->C, sigma, mask,
+                                    count_pairs ? pair_count.as<unsigned long long>() : nullptr, ks,
+                                    fv);
+                    });
+                };
+                run_field();
+                if (fv) {
+                    // the vertex lists' capacity was a guess: on overflow, grow it
+                    // to what the chunk needs and run the field again
+                    uint32_t cnt[2];
+                    read_to_host(cnt, fv->counter.get(), 8, ks);
+                    if (cnt[1]) {
+                        if (count_pairs) fail(CSL_ERR_CAPACITY, "fused vertex lists overflowed "
+                                                                "while counting pairs");
+                        fv->cap = std::min<int64_t>((int64_t)cnt[0] + cnt[0] / 4 + (1 << 20),
+                                                    0xffffffffLL);
+                        fv->verts.release();
+                        fv->verts.alloc((size_t)fv->cap * 8, ks);
+                        run_field();
+                        read_to_host(cnt, fv->counter.get(), 8, ks);
+                        if (cnt[1]) fail(CSL_ERR_CAPACITY, "fused vertex lists overflowed twice");
+                    }
+                }
                 ++st.field_launches;
                 if (d.mask_out) {
                     const int64_t wpr = ceil_div(d.nx, 32);
@@ -793,6 +844,7 @@ csl_status csl_debug_slab_bins(csl_lattice* L, const csl_slice_desc* desc, int32
         csl_slice_desc d = *desc;
         if (d.n_layers < first_layer + n_slab_layers) d.n_layers = first_layer + n_slab_layers;
         SlicePlan p = make_plan(L, d);
+        p.fused = wants_fused(d, p);   // the bins of the pass csl_slice_layers would run
         ChunkGeom g = chunk_geom(L, d, p, first_layer, n_slab_layers);
         g.S = n_slab_layers;
         g.n_slabs = 1;

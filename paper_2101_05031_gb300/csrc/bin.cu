@@ -15,9 +15,13 @@
 //       t0 = max(((zf - mz) - zlo) / (zhi - zlo), 0), t1 = min(((zl + mz) - zlo) / (zhi - zlo), 1)
 //   x(t) = ax + t (bx - ax), y(t) likewise;
 //   box = [min(x(t0), x(t1)) - mxy, max(...) + mxy] x [same in y];
-//   tile range = floor((box - origin) * inv_tile), clipped to the grid.
+//   tile range = floor((box - origin) * inv_tile), clipped to the grid; with a
+//   one-pixel halo (the fused field and contour pass, which also evaluates each
+//   tile's next column and row) the low corner is floor(((min - mxy) - px -
+//   origin) * inv_tile).
 // mz and mxy are R plus a slack for FP32 rounding, so every pixel centre of
-// the tile within distance R of the edge at some layer of the slab is inside.
+// the tile (and of its halo) within distance R of the edge at some layer of
+// the slab is inside.
 #include <math.h>
 
 #include "slice.cuh"
@@ -27,6 +31,7 @@ namespace {
 
 struct BinConst {
     float fx0, fy0, inv_tile, mxy, mz;
+    float halo;   // 0, or the pixel size: the low corner also reaches the tile below
     int32_t ntx, nty, n_tiles;
 };
 
@@ -52,6 +57,10 @@ __device__ __forceinline__ bool bin_rect(const float4 e, float zlo, float zhi, f
     float ya = __fadd_rn(e.y, __fmul_rn(t0, ey)), yb = __fadd_rn(e.y, __fmul_rn(t1, ey));
     float xmin = __fsub_rn(fminf(xa, xb), c.mxy), xmax = __fadd_rn(fmaxf(xa, xb), c.mxy);
     float ymin = __fsub_rn(fminf(ya, yb), c.mxy), ymax = __fadd_rn(fmaxf(ya, yb), c.mxy);
+    if (c.halo > 0.0f) {
+        xmin = __fsub_rn(xmin, c.halo);
+        ymin = __fsub_rn(ymin, c.halo);
+    }
     float fx0 = floorf(__fmul_rn(__fsub_rn(xmin, c.fx0), c.inv_tile));
     float fx1 = floorf(__fmul_rn(__fsub_rn(xmax, c.fx0), c.inv_tile));
     float fy0 = floorf(__fmul_rn(__fsub_rn(ymin, c.fy0), c.inv_tile));
@@ -209,6 +218,7 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     c.inv_tile = (float)(1.0 / ((double)g.T * g.px));
     c.mxy = g.margin_xy;
     c.mz = g.margin_z;
+    c.halo = g.fused ? (float)g.px : 0.0f;
     c.ntx = g.ntx;
     c.nty = g.nty;
     c.n_tiles = n_tiles;

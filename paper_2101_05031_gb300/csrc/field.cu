@@ -378,15 +378,17 @@ void launch_origins(const ChunkGeom& g, float2* org, cudaStream_t s) {
 }  // namespace
 
 void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
-                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s) {
+                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s,
+                 FusedVerts* fv) {
     // tile and slab origins in double, each split into a (hi, lo) float pair
     DevBuf org_d(((size_t)g.ntx + g.nty + g.n_slabs) * sizeof(float2), s);
     launch_origins(g, org_d.as<float2>(), s);
     if (g.kernel == kFieldFootprint) {
         field_chunk_fp(g, bins, C, org_d.as<float2>(), L->status.as<uint32_t>(), sigma, mask,
-                       count_pairs, s);
+                       count_pairs, s, fv);
         return;
     }
+    if (g.fused || fv) fail(CSL_ERR_INVALID_ARG, "the fused pass needs the footprint kernel");
     if (g.T != kTile) fail(CSL_ERR_INVALID_ARG, "the block field kernel takes 16-pixel tiles");
     FieldConst c = make_field_const(g, C, org_d.as<float2>());
     c.err = L->status.as<uint32_t>();

@@ -35,6 +35,8 @@
 // the block kernel loses nothing and keeps its sums in registers.
 #include <math.h>
 
+#include <algorithm>
+
 #include "field_tile.cuh"
 #include "slice.cuh"
 
@@ -42,7 +44,7 @@ namespace csl {
 namespace {
 
 struct FpConst {
-    int32_t nx, ny, ntx, n_tiles;
+    int32_t nx, ny, ntx, nty, n_tiles;
     int32_t n_layers;    // layers in this chunk
     int32_t K;           // records staged per bulk copy
     float R2, inv_R4, fpx, inv_px, fdz, cull;
@@ -53,6 +55,14 @@ struct FpConst {
     int32_t mwr;         // mask words per row
     int64_t mask_wpl;    // mask words per layer
     uint32_t* err;       // device status word: ST_TIMEOUT when a wait gave up
+    // fused pass (FusedVerts): tables, vertices, saddle bits, allocation counter
+    uint32_t* tbase;
+    uint16_t* roff;
+    float2* verts;
+    uint32_t* saddle;
+    uint32_t* counter;
+    uint32_t cap;
+    float fx0, fy0;      // grid origin as the contour stage takes it (float)
 };
 
 // One (record, layer) footprint, 16 bytes: the span of row (or column) u
@@ -67,7 +77,7 @@ struct __align__(16) Foot {
 
 // Footprint of record (A, B) in layer plane zl of a T x T tile; false when
 // the edge's support misses the tile in that plane.
-template <int T>
+template <int T, int EXT>
 __device__ __forceinline__ bool make_foot(const float4 A, const float4 B, float zl, int rec,
                                           const FpConst& c, Foot& f) {
     const float ax = A.x, ay = A.y, az = A.z, ux = A.w, uy = B.x, uz = B.y, len = B.z;
@@ -95,10 +105,11 @@ __device__ __forceinline__ bool make_foot(const float4 A, const float4 B, float 
     const float fx1 = fmaf(fmaxf(xa, xb) + c.cull, c.inv_px, -0.5f);
     const float fy0 = fmaf(fminf(ya, yb) - c.cull, c.inv_px, -0.5f);
     const float fy1 = fmaf(fmaxf(ya, yb) + c.cull, c.inv_px, -0.5f);
+    // tile-local pixels 0 .. EXT (EXT = T - 1, or T with the fused pass's halo)
     const int i0 = max(0, (int)ceilf(fmaxf(fx0, -1.0f)));
-    const int i1 = min(T - 1, (int)floorf(fminf(fx1, (float)T)));
+    const int i1 = min(EXT, (int)floorf(fminf(fx1, (float)(EXT + 1))));
     const int j0 = max(0, (int)ceilf(fmaxf(fy0, -1.0f)));
-    const int j1 = min(T - 1, (int)floorf(fminf(fy1, (float)T)));
+    const int j1 = min(EXT, (int)floorf(fminf(fy1, (float)(EXT + 1))));
     if (i0 > i1 || j0 > j1) return false;
     const bool rows = fabsf(uy) >= fabsf(ux);
     const float au = rows ? ay : ax, av = rows ? ax : ay;
@@ -142,10 +153,11 @@ constexpr int plane_pitch() {   // row pitch of a Sigma plane in shared memory (
 // are affine in the pixel indices: dx = i px + (px / 2 - a_x). INTERIOR: every
 // pixel within R has its whole chord [t0 - w, t0 + w] on the edge, where the
 // quartic's integral is (16/15) w^5 (the 3-point rule's value at m = 0, h = w).
-template <int T, bool ROWS, bool INTERIOR, bool COUNT>
+template <int T, bool ROWS, bool INTERIOR, bool COUNT, bool FUSED>
 __device__ __forceinline__ void walk_foot(const Foot& fq, const float4 A, const float4 B,
-                                          float zl, float* __restrict__ sig_l, const FpConst& c,
-                                          int lane, uint32_t& n_nonzero, uint32_t& n_eval) {
+                                          const float2 An, float zl, float* __restrict__ sig_l,
+                                          const FpConst& c, int lane, uint32_t& n_nonzero,
+                                          uint32_t& n_eval) {
     constexpr float P = (float)plane_pitch<T>();
     const float Wf = (float)((fq.w1 >> 16) & 0xffu);
     const int passes = (int)(fq.w1 >> 24);
@@ -157,6 +169,11 @@ __device__ __forceinline__ void walk_foot(const Foot& fq, const float4 A, const 
     const float inv_w = __fdividef(1.0f, weff);   // floor((k + 1/2) / weff) is exact with it
     const float half_w = 0.5f * inv_w;
     const float ox = fmaf(0.5f, c.fpx, -A.x), oy = fmaf(0.5f, c.fpx, -A.y);
+    // the fused pass's halo (column T, row T) in the next tiles' frames (An: v_s
+    // relative to their corners), so that its values are the ones those tiles
+    // compute for their first column and row, bit for bit
+    const float oxn = FUSED ? fmaf(0.5f, c.fpx, -An.x) : 0.0f;
+    const float oyn = FUSED ? fmaf(0.5f, c.fpx, -An.y) : 0.0f;
     const float dz = zl - A.z;
     const float dzuz = dz * B.y;
     const float wI = INTERIOR ? B.w * (16.0f / 15.0f) : B.w;
@@ -169,7 +186,11 @@ __device__ __forceinline__ void walk_foot(const Foot& fq, const float4 A, const 
         const float v = fmaxf(s, v0) + kk;
         const bool valid = rr < n_rows && v <= v1 && v < s + Wf;
         const float xi = ROWS ? v : u, yj = ROWS ? u : v;
-        const float dx = fmaf(xi, c.fpx, ox), dy = fmaf(yj, c.fpx, oy);
+        float dx = fmaf(xi, c.fpx, ox), dy = fmaf(yj, c.fpx, oy);
+        if (FUSED) {
+            if (xi == (float)T) dx = fmaf(0.0f, c.fpx, oxn);
+            if (yj == (float)T) dy = fmaf(0.0f, c.fpx, oyn);
+        }
         const float t0 = fmaf(dx, A.w, fmaf(dy, B.x, dzuz));
         const float ex = fmaf(-t0, A.w, dx);
         const float ey = fmaf(-t0, B.x, dy);
@@ -188,9 +209,129 @@ __device__ __forceinline__ void walk_foot(const Foot& fq, const float4 A, const 
     }
 }
 
+// The fused pass's contour inputs of one layer (warp): the tile's crossing
+// vertices in edge-id order, their row offsets and list base, and the
+// saddle-join bits (FusedVerts). sig_l holds Sigma of the tile's pixels and of
+// its next column and row (those computed in the next tiles' frames, so equal
+// to what they compute); pixels outside the grid count as 0 (outside), like
+// the padding ring. Each row's inside samples are one 64-bit word, bit a + 1
+// for tile-local column a in [-1, T] (column -1: the padding sample before the
+// first tile column, always outside); the crossing bits of a row are then
+// in ^ (in >> 1) (x edges) and in ^ (the row above) (y edges), as the contour
+// stage derives them from the mask. Vertex and saddle expressions are the
+// contour stage's.
+template <int T>
+__device__ __forceinline__ void fused_epilogue(const float* __restrict__ sig_l, const FpConst& c,
+                                               int tx, int ty, int tile, int64_t lg, int lane,
+                                               unsigned char* scratch) {
+    constexpr int P = plane_pitch<T>();
+    uint64_t* s_in = reinterpret_cast<uint64_t*>(scratch);           // rows -1 .. T
+    uint16_t* s_roff = reinterpret_cast<uint16_t*>(scratch + (T + 2) * 8);
+    const int gx = tx * T, gy = ty * T;
+    auto val = [&](int a, int b) -> float {
+        return (a >= 0 && b >= 0 && a <= T && b <= T && gx + a < c.nx && gy + b < c.ny)
+                   ? sig_l[b * P + a]
+                   : 0.0f;
+    };
+    // inside words of rows -1 .. T
+    for (int b = -1; b <= T; ++b) {
+        const bool in_l = lane <= T && val(lane, b) >= c.C;          // columns 0 .. 31 (T = 16: .. 16)
+        const uint32_t bl = __ballot_sync(0xffffffffu, in_l);
+        const bool in_t = T == 32 && val(T, b) >= c.C;                // column 32 (T = 32 only)
+        if (lane == 0) s_in[b + 1] = ((uint64_t)bl << 1) | ((uint64_t)in_t << (T + 1));
+    }
+    __syncwarp();
+    const int a_hi = min(T - 1, c.nx - 1 - gx), b_hi = min(T - 1, c.ny - 1 - gy);
+    const int a_lo = tx == 0 ? -1 : 0, b_lo = ty == 0 ? -1 : 0;
+    // owned samples: bits a_lo + 1 .. a_hi + 1
+    const uint64_t own = ((2ull << (a_hi + 1)) - 1ull) & ~((1ull << (a_lo + 1)) - 1ull);
+    uint32_t total = 0;
+    for (int b = -1; b < T; ++b) {
+        uint32_t cnt = 0;
+        if (b >= b_lo && b <= b_hi) {
+            const uint64_t in = s_in[b + 1], up = s_in[b + 2];
+            cnt = __popcll((in ^ (in >> 1)) & own) + __popcll((in ^ up) & own);
+        }
+        if (lane == 0) s_roff[b + 1] = (uint16_t)total;
+        total += cnt;
+    }
+    __syncwarp();
+    const int64_t tl = lg * c.n_tiles + tile;
+    for (int k = lane; k <= T; k += 32) c.roff[tl * (T + 1) + k] = s_roff[k];
+    uint32_t base = 0;
+    if (lane == 0) {
+        base = atomicAdd(c.counter, total);
+        if ((uint64_t)base + total > c.cap) atomicOr(c.counter + 1, 1u);
+        c.tbase[tl] = base;
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((uint64_t)base + total > c.cap) return;   // reported: the chunk runs again
+    for (int b = b_lo; b <= b_hi; ++b) {
+        const uint64_t in = s_in[b + 1], up = s_in[b + 2];
+        const uint64_t hx = (in ^ (in >> 1)) & own, vy = (in ^ up) & own;
+        const int J = gy + b + 1;
+        const uint32_t row0 = base + s_roff[b + 1];
+        // column -1 (first tile column): its x edge from the padding sample to pixel 0
+        if ((hx & 1ull) && lane == 0) {
+            const float sa = val(0, b);
+            const float t = __fdividef(sa - c.C, sa - 0.0f);
+            const float xp = 0.0f + 0.5f - t;
+            c.verts[row0] = make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
+        }
+        // columns 0 .. T - 1: lane a, bit a + 1
+        const int a = lane;
+        const int q = a + 1;
+        const bool hb = q <= T && ((hx >> q) & 1ull);
+        const bool vb = q <= T && ((vy >> q) & 1ull);
+        if (hb || vb) {
+            const uint64_t below = (1ull << q) - 1ull;
+            const uint32_t pos = row0 + __popcll(hx & below) + __popcll(vy & below);
+            const int I = gx + a + 1;
+            const float v0 = val(a, b);
+            const bool in0 = v0 >= c.C;
+            if (hb) {   // x edge (I, J) -> (I + 1, J)
+                const float v1 = val(a + 1, b);
+                const float sa = in0 ? v0 : v1, sbv = in0 ? v1 : v0;
+                const float t = __fdividef(sa - c.C, sa - sbv);
+                const float xp = in0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
+                c.verts[pos] = make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
+            }
+            if (vb) {   // y edge (I, J) -> (I, J + 1)
+                const float v3 = val(a, b + 1);
+                const float sa = in0 ? v0 : v3, sbv = in0 ? v3 : v0;
+                const float t = __fdividef(sa - c.C, sa - sbv);
+                const float yp = in0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
+                c.verts[pos + (hb ? 1u : 0u)] =
+                    make_float2(c.fx0 + ((float)I - 0.5f) * c.fpx, c.fy0 + yp * c.fpx);
+            }
+        }
+        // saddle cells (a, b), a, b >= 0: inside corners on one diagonal only
+        if (b >= 0) {
+            const uint64_t c0 = in, c1 = in >> 1, c3 = up, c2 = up >> 1;
+            const uint64_t sad = ((c0 & c2 & ~c1 & ~c3) | (c1 & c3 & ~c0 & ~c2)) & own & ~1ull;
+            if (sad) {
+                bool joined = false;
+                if (q <= T && ((sad >> q) & 1ull)) {
+                    const float w0 = val(a, b), w1 = val(a + 1, b), w2 = val(a + 1, b + 1),
+                                w3 = val(a, b + 1);
+                    joined = 0.25f * (w0 + w1 + w2 + w3) >= c.C;
+                }
+                const uint32_t sb = __ballot_sync(0xffffffffu, joined);
+                if (lane == 0 && sb) {
+                    uint32_t* row = c.saddle + lg * c.mask_wpl + (int64_t)J * c.mwr;
+                    const int sh = (gx + 1) & 31;
+                    atomicOr(row + ((gx + 1) >> 5), sb << sh);
+                    const uint32_t hi = sh ? sb >> (32 - sh) : 0u;
+                    if (hi) atomicOr(row + ((gx + 1) >> 5) + 1, hi);
+                }
+            }
+        }
+    }
+}
+
 // One (tile, slab) of the field. Shared memory: S Sigma planes of T rows,
 // then K staged records, then 32 footprints per warp.
-template <int T, int S, bool COUNT>
+template <int T, int S, bool COUNT, bool FUSED>
 __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                                               const uint32_t* __restrict__ tstart,
                                               const uint32_t* __restrict__ tend,
@@ -200,10 +341,14 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                                               int slab, unsigned char* smem, uint64_t* bar,
                                               uint32_t& phase) {
     constexpr int P = plane_pitch<T>();
+    constexpr int ROWS = FUSED ? T + 1 : T;   // the fused pass also evaluates the next row
     float* s_sig = reinterpret_cast<float*>(smem);
-    float4* s_rec = reinterpret_cast<float4*>(smem + (size_t)S * T * P * sizeof(float));
-    Foot* s_foot = reinterpret_cast<Foot*>(reinterpret_cast<unsigned char*>(s_rec) +
-                                           (size_t)c.K * sizeof(csl_rec));
+    float4* s_rec = reinterpret_cast<float4*>(smem + (size_t)S * ROWS * P * sizeof(float));
+    // the fused pass keeps each record's v_s.xy also relative to the next tiles' corners
+    float2* s_recn = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(s_rec) +
+                                               (size_t)c.K * sizeof(csl_rec));
+    Foot* s_foot = reinterpret_cast<Foot*>(reinterpret_cast<unsigned char*>(s_recn) +
+                                           (FUSED ? (size_t)c.K * sizeof(float2) : 0));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = tile % c.ntx, ty = tile / c.ntx;
     const uint32_t key = (uint32_t)slab * (uint32_t)c.n_tiles + (uint32_t)tile;
@@ -211,8 +356,8 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
     const int l0 = slab * S;
     const int nl = min(S, c.n_layers - l0);
     const int l = warp;   // this warp's layer in the slab
-    float* sig_l = s_sig + l * T * P;
-    for (int q = lane; q < T * P / 4; q += 32)
+    float* sig_l = s_sig + l * ROWS * P;
+    for (int q = lane; q < ROWS * P / 4; q += 32)
         reinterpret_cast<float4*>(sig_l)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     Foot* my_foot = s_foot + warp * 32;
     uint32_t n_nonzero = 0, n_eval = 0;
@@ -221,6 +366,11 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
     if (end > beg) {
         const float2 ox = c.org_x[tx], oy = c.org_y[ty], oz = c.org_z[slab];
         const float oxh = ox.x, oxl = ox.y, oyh = oy.x, oyl = oy.y, ozh = oz.x, ozl = oz.y;
+        // the next tile column's and row's corners (the fused pass's halo); past
+        // the grid's last tile the halo lies outside and its values are not used
+        const float2 oxn = FUSED ? c.org_x[min(tx + 1, c.ntx - 1)] : ox;
+        const float2 oyn = FUSED ? c.org_y[min(ty + 1, c.nty - 1)] : oy;
+        const float oxnh = oxn.x, oxnl = oxn.y, oynh = oyn.x, oynl = oyn.y;
         for (uint32_t c0 = beg; c0 < end; c0 += (uint32_t)c.K) {
             const int cnt = (int)min((uint32_t)c.K, end - c0);
             if (threadIdx.x == 0) {
@@ -235,6 +385,8 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
             phase ^= 1u;
             for (int r = threadIdx.x; r < cnt; r += 32 * S) {
                 const float4 r0 = s_rec[2 * r], r1 = s_rec[2 * r + 1];
+                if (FUSED)
+                    s_recn[r] = make_float2((r0.x - oxnh) - oxnl, (r0.y - oynh) - oynl);
                 s_rec[2 * r] =
                     make_float4((r0.x - oxh) - oxl, (r0.y - oyh) - oyl, (r0.z - ozh) - ozl, r0.w);
                 s_rec[2 * r + 1] = make_float4(r1.x, r1.y, r1.z, r1.w * c.inv_R4);
@@ -244,8 +396,8 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                 for (int r0 = 0; r0 < cnt; r0 += 32) {
                     const int r = r0 + lane;
                     Foot f;
-                    const bool ok = r < cnt && make_foot<T>(s_rec[2 * r], s_rec[2 * r + 1], zl, r,
-                                                            c, f);
+                    const bool ok = r < cnt && make_foot<T, FUSED ? T : T - 1>(
+                                                   s_rec[2 * r], s_rec[2 * r + 1], zl, r, c, f);
                     const uint32_t ball = __ballot_sync(0xffffffffu, ok);
                     if (ok) my_foot[__popc(ball & ((1u << lane) - 1u))] = f;
                     __syncwarp();
@@ -254,11 +406,12 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                         const Foot fq = my_foot[q];
                         const int rec = (int)(fq.w1 & 0x3fffu);
                         const float4 A = s_rec[2 * rec], B = s_rec[2 * rec + 1];
+                        const float2 An = FUSED ? s_recn[rec] : make_float2(0.0f, 0.0f);
                         switch ((fq.w1 >> 14) & 3u) {   // interior | rows << 1, warp-uniform
-                            case 0: walk_foot<T, false, false, COUNT>(fq, A, B, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            case 1: walk_foot<T, false, true, COUNT>(fq, A, B, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            case 2: walk_foot<T, true, false, COUNT>(fq, A, B, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            default: walk_foot<T, true, true, COUNT>(fq, A, B, zl, sig_l, c, lane, n_nonzero, n_eval); break;
+                            case 0: walk_foot<T, false, false, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
+                            case 1: walk_foot<T, false, true, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
+                            case 2: walk_foot<T, true, false, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
+                            default: walk_foot<T, true, true, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
                         }
                     }
                     __syncwarp();   // the next group overwrites the footprints
@@ -310,10 +463,13 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
             if (hi) atomicOr(row + (I0 >> 5) + 1, hi);
         }
     }
+    if (FUSED)
+        fused_epilogue<T>(sig_l, c, tx, ty, tile, (int64_t)(l0 + l), lane,
+                          reinterpret_cast<unsigned char*>(my_foot));
     return true;
 }
 
-template <int T, int S, bool COUNT>
+template <int T, int S, bool COUNT, bool FUSED>
 __global__ void __launch_bounds__(32 * S)
 k_field_fp(const csl_rec* __restrict__ recs, const uint32_t* __restrict__ tstart,
            const uint32_t* __restrict__ tend, FpConst c, float* __restrict__ sigma,
@@ -326,22 +482,23 @@ k_field_fp(const csl_rec* __restrict__ recs, const uint32_t* __restrict__ tstart
     }
     __syncthreads();
     uint32_t phase = 0;
-    field_tile_fp<T, S, COUNT>(recs, tstart, tend, c, sigma, mask, n_pairs, blockIdx.x,
-                               blockIdx.y, smem, &bar, phase);
+    field_tile_fp<T, S, COUNT, FUSED>(recs, tstart, tend, c, sigma, mask, n_pairs, blockIdx.x,
+                                      blockIdx.y, smem, &bar, phase);
 }
 
-template <int T, int S>
+template <int T, int S, bool FUSED>
 size_t fp_smem_bytes(int K) {
-    return (size_t)S * T * plane_pitch<T>() * sizeof(float) + (size_t)K * sizeof(csl_rec) +
+    return (size_t)S * (FUSED ? T + 1 : T) * plane_pitch<T>() * sizeof(float) +
+           (size_t)K * sizeof(csl_rec) + (FUSED ? (size_t)K * sizeof(float2) : 0) +
            (size_t)S * 32 * sizeof(Foot);
 }
 
-template <int T, int S, bool COUNT>
+template <int T, int S, bool COUNT, bool FUSED>
 void launch_fp(const FpConst& c, dim3 grid, const csl_rec* recs, const uint32_t* ts,
                const uint32_t* te, float* sigma, uint32_t* mask, unsigned long long* count,
                cudaStream_t s) {
-    const size_t smem = fp_smem_bytes<T, S>(c.K);
-    auto kern = k_field_fp<T, S, COUNT>;
+    const size_t smem = fp_smem_bytes<T, S, FUSED>(c.K);
+    auto kern = k_field_fp<T, S, COUNT, FUSED>;
     CSL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, 32 * S, smem, s>>>(recs, ts, te, c, sigma, mask, count);
 }
@@ -349,20 +506,26 @@ void launch_fp(const FpConst& c, dim3 grid, const csl_rec* recs, const uint32_t*
 template <int T, int S>
 void launch_fp_count(const FpConst& c, dim3 grid, const csl_rec* recs, const uint32_t* ts,
                      const uint32_t* te, float* sigma, uint32_t* mask, unsigned long long* count,
-                     cudaStream_t s) {
-    if (count) launch_fp<T, S, true>(c, grid, recs, ts, te, sigma, mask, count, s);
-    else launch_fp<T, S, false>(c, grid, recs, ts, te, sigma, mask, nullptr, s);
+                     cudaStream_t s, bool fused) {
+    if (fused) {
+        if (count) launch_fp<T, S, true, true>(c, grid, recs, ts, te, sigma, mask, count, s);
+        else launch_fp<T, S, false, true>(c, grid, recs, ts, te, sigma, mask, nullptr, s);
+    } else {
+        if (count) launch_fp<T, S, true, false>(c, grid, recs, ts, te, sigma, mask, count, s);
+        else launch_fp<T, S, false, false>(c, grid, recs, ts, te, sigma, mask, nullptr, s);
+    }
 }
 
 }  // namespace
 
 void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const float2* org,
                     uint32_t* err, float* sigma, uint32_t* mask, unsigned long long* count_pairs,
-                    cudaStream_t s) {
+                    cudaStream_t s, FusedVerts* fv) {
     FpConst c;
     c.nx = g.nx;
     c.ny = g.ny;
     c.ntx = g.ntx;
+    c.nty = g.nty;
     c.n_tiles = g.ntx * g.nty;
     c.n_layers = g.n_layers;
     c.K = g.K;
@@ -379,6 +542,17 @@ void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const flo
     c.mwr = (int32_t)mask_words_per_row(g.nx);
     c.mask_wpl = mask_words_per_layer(g.nx, g.ny);
     c.err = err;
+    c.fx0 = (float)g.x0;
+    c.fy0 = (float)g.y0;
+    const bool fused = g.fused;
+    if (fused != (fv != nullptr) || (fused && !mask))
+        fail(CSL_ERR_INVALID_ARG, "fused pass: vertex lists and mask are required");
+    c.tbase = fused ? fv->tbase.as<uint32_t>() : nullptr;
+    c.roff = fused ? fv->roff.as<uint16_t>() : nullptr;
+    c.verts = fused ? fv->verts.as<float2>() : nullptr;
+    c.saddle = fused ? fv->saddle.as<uint32_t>() : nullptr;
+    c.counter = fused ? fv->counter.as<uint32_t>() : nullptr;
+    c.cap = fused ? (uint32_t)std::min<int64_t>(fv->cap, 0xffffffffLL) : 0u;
     if (c.K < 32 || c.K > 1024 || c.K % 32) fail(CSL_ERR_INVALID_ARG, "staging chunk K");
     dim3 grid((unsigned)c.n_tiles, (unsigned)g.n_slabs);
     const csl_rec* recs = bins.recs.as<csl_rec>();
@@ -386,7 +560,7 @@ void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const flo
     const uint32_t* te = bins.tile_end.as<uint32_t>();
 #define CSL_FP_CASE(TV, SV)                                                                \
     if (g.T == TV && g.S == SV) {                                                          \
-        launch_fp_count<TV, SV>(c, grid, recs, ts, te, sigma, mask, count_pairs, s);       \
+        launch_fp_count<TV, SV>(c, grid, recs, ts, te, sigma, mask, count_pairs, s, fused); \
         CSL_LAUNCH_CHECK("footprint field");                                               \
         return;                                                                            \
     }

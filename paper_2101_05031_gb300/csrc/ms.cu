@@ -100,22 +100,56 @@ struct Dense {
     int32_t ewr;
 };
 
+// The fused pass's vertex lists (FusedVerts, as the field kernel leaves them).
+struct FusedIn {
+    const uint32_t* tbase;
+    const uint16_t* roff;
+    const float2* verts;
+    const uint32_t* saddle;
+    int32_t T, ntx, n_tiles;
+};
+
+// Vertex of the crossing on the edge from padded sample (I, J) in direction
+// dir (0: x, 1: y): the tile owning the sample lists its crossings in edge-id
+// order, so its place is the tile's base + the row's offset + the number of
+// crossing edges of row J from the row's first owned sample up to this edge
+// (the interleaved edge words hold exactly those bits).
+__device__ __forceinline__ float2 fused_vertex(const FusedIn& F, const Dense& D, int layer, int I,
+                                               int J, int dir) {
+    const int tx = I == 0 ? 0 : (I - 1) / F.T, ty = J == 0 ? 0 : (J - 1) / F.T;
+    const int b = J - 1 - ty * F.T;                 // tile-local row, -1 .. T - 1
+    const int Ia = tx == 0 ? 0 : tx * F.T + 1;      // first sample of the row the tile owns
+    const uint32_t* row = D.ew + (int64_t)layer * D.edge_wpl + (int64_t)J * D.ewr;
+    const int lo = 2 * Ia, hi = 2 * I + dir;
+    uint32_t rank = 0;
+    for (int w = lo >> 5; w <= ((hi - 1) >> 5) && hi > lo; ++w) {
+        uint32_t m = row[w];
+        if (w == (lo >> 5)) m &= 0xffffffffu << (lo & 31);
+        if (w == (hi >> 5)) m &= (1u << (hi & 31)) - 1u;
+        rank += __popc(m);
+    }
+    const int64_t tl = (int64_t)layer * F.n_tiles + (int64_t)ty * F.ntx + tx;
+    return F.verts[(int64_t)F.tbase[tl] + F.roff[tl * (F.T + 1) + b + 1] + rank];
+}
+
 __device__ __forceinline__ float value_at(const float* __restrict__ sg, const MsConst& c, int I,
                                           int J) {
     if (I < 1 || J < 1 || I > c.nx || J > c.ny) return 0.0f;
     return sg[(int64_t)(J - 1) * c.nx + (I - 1)];
 }
 
-// grid: x over (row J <= ny, mask word k), y = layer
+// grid: x over (row J <= ny, mask word k), y = layer. FUSED: vertices and
+// saddle decisions from the fused pass (F) instead of Sigma.
+template <bool FUSED>
 __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
-                       MsConst c, Dense D, Xing* __restrict__ rec, uint32_t n_cap,
-                       uint32_t* flag) {
+                       MsConst c, Dense D, FusedIn F, Xing* __restrict__ rec,
+                       uint32_t* __restrict__ pred, uint32_t n_cap, uint32_t* flag) {
     const int layer = blockIdx.y;
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (uint32_t)(c.ny + 1) * (uint32_t)c.mwr) return;
     const int J = (int)(idx / (uint32_t)c.mwr), k = (int)(idx - (uint32_t)J * c.mwr);
     const uint32_t* m = mask + (int64_t)layer * c.mask_wpl;
-    const float* sg = sigma + (int64_t)layer * c.nx * c.ny;
+    const float* sg = FUSED ? nullptr : sigma + (int64_t)layer * c.nx * c.ny;
     const bool last = k + 1 >= c.mwr;
     const uint32_t in0 = m[(int64_t)J * c.mwr + k];
     const uint32_t in1 = last ? 0u : m[(int64_t)J * c.mwr + k + 1];
@@ -160,28 +194,38 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
         };
         const bool h_own = (hb >> b) & 1u, v_own = (vb >> b) & 1u;
         // Sigma only where a vertex is placed (or a saddle is decided)
-        const float v0 = (h_own || v_own) ? value_at(sg, c, I, J) : 0.0f;
+        const float v0 = (!FUSED && (h_own || v_own)) ? value_at(sg, c, I, J) : 0.0f;
         const int64_t eb = 2 * ((int64_t)J * c.W + I);
         if (h_own) {   // vertex on the bottom edge (I, J) -> (I+1, J)
             const uint32_t id = id_bottom;
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
-            const float v1 = value_at(sg, c, I + 1, J);
-            const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
-            const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
-            const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
-            *reinterpret_cast<float2*>(&rec[id].x) =
-                make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
+            float2 xy;
+            if (FUSED) {
+                xy = fused_vertex(F, D, layer, I, J, 0);
+            } else {
+                const float v1 = value_at(sg, c, I + 1, J);
+                const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
+                const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
+                const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
+                xy = make_float2(c.fx0 + xp * c.fpx, c.fy0 + ((float)J - 0.5f) * c.fpx);
+            }
+            *reinterpret_cast<float2*>(&rec[id].x) = xy;
             rec[id].eid = (int32_t)eb;
         }
         if (v_own) {   // vertex on the left edge (I, J) -> (I, J+1)
             const uint32_t id = id_left;
             if (id >= n_cap) { atomicOr(flag, 1u); continue; }
-            const float v3 = value_at(sg, c, I, J + 1);
-            const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
-            const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
-            const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
-            *reinterpret_cast<float2*>(&rec[id].x) =
-                make_float2(c.fx0 + ((float)I - 0.5f) * c.fpx, c.fy0 + yp * c.fpx);
+            float2 xy;
+            if (FUSED) {
+                xy = fused_vertex(F, D, layer, I, J, 1);
+            } else {
+                const float v3 = value_at(sg, c, I, J + 1);
+                const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
+                const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
+                const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
+                xy = make_float2(c.fx0 + ((float)I - 0.5f) * c.fpx, c.fy0 + yp * c.fpx);
+            }
+            *reinterpret_cast<float2*>(&rec[id].x) = xy;
             rec[id].eid = (int32_t)(eb + 1);
         }
         // successors. Side k runs from corner k to corner k+1; bit k of nxt is corner k+1.
@@ -190,35 +234,37 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
         const uint32_t enter = cs & ~nxt & 0xfu;   // inside -> outside
         const uint32_t leave = ~cs & nxt & 0xfu;   // outside -> inside
         if (__popc(enter) == 1) {
-            const uint32_t a = side(__ffs(enter) - 1);
-            if (a < n_cap) rec[a].succ = side(__ffs(leave) - 1);
-            else atomicOr(flag, 1u);
+            const uint32_t a = side(__ffs(enter) - 1), b = side(__ffs(leave) - 1);
+            if (a < n_cap && b < n_cap) {
+                rec[a].succ = b;
+                pred[b] = a;
+            } else {
+                atomicOr(flag, 1u);
+            }
         } else if (enter) {
-            const float w0 = value_at(sg, c, I, J), w1 = value_at(sg, c, I + 1, J);
-            const float w2 = value_at(sg, c, I + 1, J + 1), w3 = value_at(sg, c, I, J + 1);
-            const bool joined = 0.25f * (w0 + w1 + w2 + w3) >= c.C;
+            bool joined;
+            if (FUSED) {
+                const uint32_t sw = F.saddle[(int64_t)layer * c.mask_wpl + (int64_t)J * c.mwr +
+                                             (I >> 5)];
+                joined = (sw >> (I & 31)) & 1u;
+            } else {
+                const float w0 = value_at(sg, c, I, J), w1 = value_at(sg, c, I + 1, J);
+                const float w2 = value_at(sg, c, I + 1, J + 1), w3 = value_at(sg, c, I, J + 1);
+                joined = 0.25f * (w0 + w1 + w2 + w3) >= c.C;
+            }
             const int k0 = __ffs(enter) - 1, k1 = 31 - __clz(enter);
             const uint32_t a0 = side(k0), a1 = side(k1);
-            if (a0 < n_cap && a1 < n_cap) {
-                rec[a0].succ = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
-                rec[a1].succ = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
+            const uint32_t b0 = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
+            const uint32_t b1 = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
+            if (a0 < n_cap && a1 < n_cap && b0 < n_cap && b1 < n_cap) {
+                rec[a0].succ = b0;
+                rec[a1].succ = b1;
+                pred[b0] = a0;
+                pred[b1] = a1;
             } else {
                 atomicOr(flag, 1u);
             }
         }
-    }
-}
-
-// pred[succ[i]] = i (thread i writes next to its neighbours' targets: the
-// successors of consecutive crossings are close). A successor out of range is
-// reported through *status and nothing is written.
-__global__ void k_pred(const Xing* __restrict__ rec, int64_t n, uint32_t* __restrict__ pred,
-                       uint32_t* status) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s = rec[i].succ;
-        if ((int64_t)s < n) pred[s] = (uint32_t)i;
-        else atomicOr(status, ST_CAPACITY);
     }
 }
 
@@ -257,43 +303,78 @@ __global__ void k_split_list(const uint32_t* __restrict__ flag, const uint32_t* 
 }
 
 // Each splitter walks its segment up to the next splitter (nxt: successor |
-// splitter bit, one 4-byte load per step).
+// splitter bit, one 4-byte load per step). A walk is a chain of dependent
+// loads, so every thread advances kWalks walks of different segments in
+// lockstep: their loads are independent and in flight together.
+constexpr int kWalks = 1;
+
 __global__ void k_segments(const uint32_t* __restrict__ nxt,
                            const uint32_t* __restrict__ spos, const uint32_t* __restrict__ split_id,
                            int64_t ns, int64_t n, uint32_t* __restrict__ seg_next,
                            uint32_t* __restrict__ seg_len, uint32_t* status) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s0 = split_id[t];
-        if ((int64_t)s0 >= n) {   // a replay whose sizes changed (flagged): no walk
-            atomicOr(status, ST_CAPACITY);
-            seg_next[t] = (uint32_t)t;
-            seg_len[t] = 1;
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < ns;
+         t0 += stride * kWalks) {
+        uint32_t j[kWalks];
+        int64_t len[kWalks];
+        bool live[kWalks], bad[kWalks];
+#pragma unroll
+        for (int g = 0; g < kWalks; ++g) {
+            const int64_t t = t0 + g * stride;
+            live[g] = bad[g] = false;
+            len[g] = 1;
+            j[g] = 0;
+            if (t >= ns) continue;
+            const uint32_t s0 = split_id[t];
+            if ((int64_t)s0 >= n) {   // a replay whose sizes changed (flagged): no walk
+                bad[g] = true;
+                continue;
+            }
+            j[g] = nxt[s0] & 0x7fffffffu;
+            live[g] = true;
         }
-        uint32_t j = nxt[s0] & 0x7fffffffu;
-        int64_t len = 1;
-        while ((int64_t)j < n && len <= n) {
-            const uint32_t v = nxt[j];
-            if (v >> 31) break;   // the next splitter
-            j = v & 0x7fffffffu;
-            ++len;
+        for (;;) {
+            bool any = false;
+            uint32_t v[kWalks];
+#pragma unroll
+            for (int g = 0; g < kWalks; ++g) {
+                if (live[g] && ((int64_t)j[g] >= n || len[g] > n)) {   // corrupt links
+                    live[g] = false;
+                    bad[g] = true;
+                }
+                v[g] = live[g] ? nxt[j[g]] : 0u;
+            }
+#pragma unroll
+            for (int g = 0; g < kWalks; ++g) {
+                if (!live[g]) continue;
+                if (v[g] >> 31) {   // the next splitter
+                    live[g] = false;
+                } else {
+                    j[g] = v[g] & 0x7fffffffu;
+                    ++len[g];
+                    any = true;
+                }
+            }
+            if (!any) break;
         }
-        if ((int64_t)j >= n || len > n) {   // corrupt links: report, never loop forever
-            atomicOr(status, ST_CAPACITY);
-            seg_next[t] = (uint32_t)t;
-            seg_len[t] = 1;
-            continue;
+#pragma unroll
+        for (int g = 0; g < kWalks; ++g) {
+            const int64_t t = t0 + g * stride;
+            if (t >= ns) continue;
+            uint32_t sn = 0;
+            if (!bad[g]) {
+                sn = spos[j[g]];
+                if ((int64_t)sn >= ns) bad[g] = true;   // more splitters than planned (flagged)
+            }
+            if (bad[g]) {   // report, never loop forever
+                atomicOr(status, ST_CAPACITY);
+                seg_next[t] = (uint32_t)t;
+                seg_len[t] = 1;
+            } else {
+                seg_next[t] = sn;
+                seg_len[t] = (uint32_t)len[g];
+            }
         }
-        const uint32_t sn = spos[j];
-        if ((int64_t)sn >= ns) {   // more splitters than planned (flagged)
-            atomicOr(status, ST_CAPACITY);
-            seg_next[t] = (uint32_t)t;
-            seg_len[t] = 1;
-            continue;
-        }
-        seg_next[t] = sn;
-        seg_len[t] = (uint32_t)len;
     }
 }
 
@@ -484,7 +565,8 @@ __global__ void k_check_packed(const int64_t* __restrict__ total, int64_t n_loop
     if (*status) atomicOr(flag, 2u);
 }
 
-// Each splitter writes its segment at its loop's offset + rank_start.
+// Each splitter writes its segment at its loop's offset + rank_start; as in
+// k_segments, every thread walks kWalks segments in lockstep.
 __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* __restrict__ cm,
                                  const uint32_t* __restrict__ spos,
                                  const uint32_t* __restrict__ split_id,
@@ -493,23 +575,46 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
                                  const int64_t* __restrict__ scan, int64_t ns, int64_t n,
                                  int64_t n_loops, int64_t* __restrict__ loop_off,
                                  float2* __restrict__ oxy, int32_t* __restrict__ oeid) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t ht = cm[t];
-        if ((int64_t)ht >= n) continue;              // only if the links were inconsistent
-        const uint32_t h = spos[ht];                 // the head splitter of this loop
-        if ((int64_t)h >= ns) continue;
-        const int64_t voff = scan[h] & 0xffffffffLL;
-        if (h == (uint32_t)t && (scan[h] >> 32) < n_loops) loop_off[scan[h] >> 32] = voff;
-        const int64_t base = voff + (int64_t)rank_start[t];
-        uint32_t j = split_id[t];
-        const int64_t len = seg_len[t];
-        if (base < 0 || base + len > n) continue;   // only if the links were inconsistent
-        for (int64_t r = 0; r < len && (int64_t)j < n; ++r) {
-            const Xing x = rec[j];
-            oxy[base + r] = make_float2(x.x, x.y);
-            if (oeid) oeid[base + r] = x.eid;
-            j = x.succ;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < ns;
+         t0 += stride * kWalks) {
+        uint32_t j[kWalks];
+        int64_t base[kWalks], len[kWalks];
+        int64_t max_len = 0;
+#pragma unroll
+        for (int g = 0; g < kWalks; ++g) {
+            const int64_t t = t0 + g * stride;
+            len[g] = 0;
+            base[g] = 0;
+            j[g] = 0;
+            if (t >= ns) continue;
+            const uint32_t ht = cm[t];
+            if ((int64_t)ht >= n) continue;              // only if the links were inconsistent
+            const uint32_t h = spos[ht];                 // the head splitter of this loop
+            if ((int64_t)h >= ns) continue;
+            const int64_t voff = scan[h] & 0xffffffffLL;
+            if (h == (uint32_t)t && (scan[h] >> 32) < n_loops) loop_off[scan[h] >> 32] = voff;
+            const int64_t b = voff + (int64_t)rank_start[t];
+            const int64_t l = seg_len[t];
+            if (b < 0 || b + l > n) continue;           // only if the links were inconsistent
+            base[g] = b;
+            len[g] = l;
+            j[g] = split_id[t];
+            max_len = max(max_len, l);
+        }
+        for (int64_t r = 0; r < max_len; ++r) {
+            Xing x[kWalks];
+#pragma unroll
+            for (int g = 0; g < kWalks; ++g)
+                if (r < len[g] && (int64_t)j[g] < n) x[g] = rec[j[g]];
+#pragma unroll
+            for (int g = 0; g < kWalks; ++g) {
+                if (r < len[g] && (int64_t)j[g] < n) {
+                    oxy[base[g] + r] = make_float2(x[g].x, x[g].y);
+                    if (oeid) oeid[base[g] + r] = x[g].eid;
+                    j[g] = x[g].succ;
+                }
+            }
         }
     }
 }
@@ -530,7 +635,8 @@ __global__ void k_layer_loops(const uint32_t* __restrict__ prefix, int64_t edge_
 }  // namespace
 
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
-                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp) {
+                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp,
+                    const FusedVerts* fv) {
     const bool replay = rp && rp->replay;
     MsConst c;
     c.nx = g.nx;
@@ -593,20 +699,34 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     if (n_cross >= ((int64_t)1 << 31)) fail(CSL_ERR_CAPACITY, "marching squares: too many crossings");
     DevBuf rec((size_t)n_cross * sizeof(Xing), s);
     CSL_CUDA(cudaMemsetAsync(rec.get(), 0xff, (size_t)n_cross * sizeof(Xing), s));
+    // pred[succ[i]] = i, written by the emit kernel beside each successor link
+    DevBuf pred((size_t)n_cross * 4, s);
+    CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     Dense D{ew.as<uint32_t>(), prefix.as<uint32_t>(), c.edge_wpl, c.ewr};
     {
         const int64_t n_thr = (int64_t)(c.ny + 1) * c.mwr;
         dim3 grid((unsigned)ceil_div(n_thr, 256), (unsigned)g.n_layers);
-        k_emit<<<grid, 256, 0, s>>>(sigma, mask, c, D, rec.as<Xing>(), (uint32_t)n_cross, flag);
+        FusedIn F{};
+        if (fv) {
+            F.tbase = fv->tbase.as<uint32_t>();
+            F.roff = fv->roff.as<uint16_t>();
+            F.verts = fv->verts.as<float2>();
+            F.saddle = fv->saddle.as<uint32_t>();
+            F.T = g.T;
+            F.ntx = g.ntx;
+            F.n_tiles = g.ntx * g.nty;
+            k_emit<true><<<grid, 256, 0, s>>>(sigma, mask, c, D, F, rec.as<Xing>(),
+                                              pred.as<uint32_t>(), (uint32_t)n_cross, flag);
+        } else {
+            k_emit<false><<<grid, 256, 0, s>>>(sigma, mask, c, D, F, rec.as<Xing>(),
+                                               pred.as<uint32_t>(), (uint32_t)n_cross, flag);
+        }
         CSL_LAUNCH_CHECK("ms emit");
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
-    DevBuf pred((size_t)n_cross * 4, s), sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
+    DevBuf sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
     DevBuf nxt((size_t)n_cross * 4, s);
-    CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
-    k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
-    CSL_LAUNCH_CHECK("ms pred");
     k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
                                      sflag.as<uint32_t>(), nxt.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms splitter flags");

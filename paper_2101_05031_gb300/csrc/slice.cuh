@@ -31,6 +31,9 @@ struct ChunkGeom {
     int32_t T = kTile;
     int32_t kernel = kFieldBlock;
     int32_t K = 256;
+    // fused field and contour pass: tiles also take their next column and row
+    // (binner halo), and the field kernel leaves vertex lists instead of Sigma
+    bool fused = false;
 };
 
 // Per-slab binning results (device).
@@ -68,16 +71,38 @@ inline int64_t mask_words_per_layer(int nx, int ny) {
     return mask_words_per_row(nx) * ((int64_t)ny + 2);
 }
 
+// Output of the fused field and contour pass (field_fp.cu) in place of a Sigma
+// plane. A tile owns the padded samples of its pixels (and, in the first tile
+// column / row, the padding column / row before them) and the grid edges from
+// them to the next sample in x and in y. For every (layer, tile) its crossing
+// vertices are listed in edge-id order (rows, then samples, the x edge before
+// the y edge) at verts[tbase[layer][tile] + roff[layer][tile][row + 1] + rank
+// in the row], row in [-1, T - 1] tile-local; `saddle` has the mask's layout,
+// bit (I, J) set when cell (I, J) is a saddle whose inside corners join (mean
+// of the four corners >= C). Vertices are the same float expressions as the
+// unfused contour stage evaluates from Sigma, so both give identical contours.
+struct FusedVerts {
+    DevBuf tbase;     // uint32 [n_layers][n_tiles]
+    DevBuf roff;      // uint16 [n_layers][n_tiles][T + 1]
+    DevBuf verts;     // float2 [cap]
+    DevBuf saddle;    // uint32 [n_layers][mask words per layer]
+    DevBuf counter;   // uint32 [2]: vertices allocated (even past cap), overflow flag
+    int64_t cap = 0;
+};
+
 // Sigma for every pixel of the chunk's layers: sigma[layer][ny][nx], and the
 // inside mask (OR-ed into `mask`, which must be zero on entry; may be null).
 // count_pairs (device, may be null): [0] += the number of (pixel, layer, edge)
 // terms that are nonzero, [1] += the number of terms evaluated.
+// With g.fused, fv (allocated for the chunk, saddle and counter zero) receives
+// the vertex lists and sigma may be null.
 void field_chunk(const csl_lattice* L, const ChunkGeom& g, const SlabBins& bins, float C,
-                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s);
+                 float* sigma, uint32_t* mask, unsigned long long* count_pairs, cudaStream_t s,
+                 FusedVerts* fv = nullptr);
 // The footprint kernel's launch (field_fp.cu); org: the chunk's origin tables.
 void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const float2* org,
                     uint32_t* err, float* sigma, uint32_t* mask, unsigned long long* count_pairs,
-                    cudaStream_t s);
+                    cudaStream_t s, FusedVerts* fv);
 
 // Field of many chunks (the jobs of a batch, one chunk each) in one
 // persistent launch: CTAs take (job, slab, tile) items from a queue sorted
@@ -111,8 +136,10 @@ struct ChunkContours {
 };
 // Contours of a chunk. In a replay (rp->replay), out's arrays must already
 // hold rp->plan's sizes; they are filled in place.
+// With fv (the fused pass's vertex lists) sigma is not read and may be null.
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
-                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp = nullptr);
+                    bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp = nullptr,
+                    const FusedVerts* fv = nullptr);
 
 // Slicing request resolution (api.cu): tile / slab / chunk sizes and the
 // binner's rounding margin; the geometry of one chunk; argument checks that
@@ -121,7 +148,11 @@ struct SlicePlan {
     int S, chunk, ntx, nty;
     float margin;
     int T, kernel, K;
+    bool fused = false;   // the fused field and contour pass (set by the slicing call)
 };
+// Whether a slicing request runs the fused pass: the footprint kernel, contours
+// wanted, and CSL_SLICE_FUSED.
+bool wants_fused(const csl_slice_desc& d, const SlicePlan& p);
 SlicePlan make_plan(const csl_lattice* L, const csl_slice_desc& d);
 ChunkGeom chunk_geom(const csl_lattice* L, const csl_slice_desc& d, const SlicePlan& p, int first,
                      int n);

@@ -259,13 +259,16 @@ class Lattice:
     def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None, mask_out=None,
               contours=True, on_device=False, edge_ids=False, slab=0, chunk_layers=0,
               time_kernels=False, count_pairs=False, stream=None, tile=0, field_kernel="auto",
-              stage_records=0):
+              stage_records=0, fused=False):
         """csl_slice_layers. sigma_out: optional CUDA float32 tensor
         [n_layers, ny, nx] that receives Sigma; mask_out: optional CUDA int32
         tensor [n_layers, ny, ceil(nx / 32)] that receives the bit-packed inside
         mask (bit i % 32 of word i / 32: pixel i inside). field_kernel: "auto",
         "block" or "footprint"; tile: 0 (auto), 16 or 32; stage_records: records
-        per staged copy of the footprint kernel (0: 256). Returns a ContourSet
+        per staged copy of the footprint kernel (0: 256); fused: with the
+        footprint kernel, the fused field and contour pass (no Sigma plane; the
+        same contours as the default, which writes a Sigma plane and runs
+        marching squares on it). Returns a ContourSet
         (host), a DeviceContours (on_device=True) or None (contours=False)."""
         if sigma_out is not None:
             if not (sigma_out.is_cuda and sigma_out.dtype == torch.float32
@@ -290,6 +293,8 @@ class Lattice:
             flags |= _lib.SLICE_TIME_KERNELS
         if count_pairs:
             flags |= _lib.SLICE_COUNT_PAIRS
+        if fused:
+            flags |= _lib.SLICE_FUSED
         d = self._desc(z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab,
                        chunk_layers, mask_out, tile, field_kernel, stage_records)
         out = ctypes.POINTER(_lib.Contours)()
@@ -302,11 +307,14 @@ class Lattice:
         return _host_contours(out)
 
     def slab_bins(self, *, z0, dz, first_layer, n_slab_layers, x0, y0, nx, ny, pixel,
-                  tile=16, stream=None):
-        """Binner output for one slab of tiles of `tile` pixels (16 or 32):
-        (tile_off[n_tiles+1], edge ids sorted per tile)."""
-        d = self._desc(z0, dz, first_layer + n_slab_layers, x0, y0, nx, ny, pixel, 0, None,
-                       0, 0, tile=tile, field_kernel="footprint" if tile == 32 else "auto")
+                  tile=16, halo=False, stream=None):
+        """Binner output for one slab of tiles of `tile` pixels (16 or 32), with
+        the fused pass's one-pixel halo or without: (tile_off[n_tiles+1], edge
+        ids sorted per tile)."""
+        kern = "footprint" if (tile == 32 or halo) else "auto"
+        d = self._desc(z0, dz, first_layer + n_slab_layers, x0, y0, nx, ny, pixel,
+                       _lib.SLICE_FUSED if halo else 0, None, 0, 0, tile=tile,
+                       field_kernel=kern)
         n_tiles = ((int(nx) + tile - 1) // tile) * ((int(ny) + tile - 1) // tile)
         off = np.zeros(n_tiles + 1, np.int64)
         n = ctypes.c_int64()

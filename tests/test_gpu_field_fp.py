@@ -205,3 +205,77 @@ def test_bad_kernel_options_are_refused(c1):
                 dict(field_kernel="footprint", stage_records=2048)):
         with pytest.raises(cs.CslError, match="INVALID_ARG"):
             lat.slice(**base, **bad)
+
+
+# ---- the fused field and contour pass: no Sigma plane, the same contours ----
+
+def _same_contours(a, b):
+    assert np.array_equal(a.layer_loop_off, b.layer_loop_off)
+    assert np.array_equal(a.loop_vert_off, b.loop_vert_off)
+    assert np.array_equal(a.edge_id, b.edge_id)
+    assert np.array_equal(a.xy.view(np.uint32), b.xy.view(np.uint32))
+
+
+@pytest.mark.parametrize("tile,slab", [(32, 8), (32, 2), (16, 4), (16, 1)])
+def test_fused_pass_gives_the_unfused_contours(c1, c3s, tile, slab):
+    """The fused pass's vertices are the same float expressions of the same
+    Sigma values, read in shared memory instead of a plane: identical contours,
+    ragged grids and odd origins included."""
+    for cfg, lat, kw in ((c1[0], c1[1], {}), (c3s[0], c3s[1], {}),
+                         (c1[0], c1[1], dict(nx=157, ny=93, x0=1.234, y0=-0.77, n_layers=7))):
+        _, a, _ = _slice(lat, cfg, field_kernel="footprint", tile=tile, slab=slab, fused=True,
+                         **kw)
+        _, b, _ = _slice(lat, cfg, field_kernel="footprint", tile=tile, slab=slab, **kw)
+        assert a.xy.shape[0] > 0
+        _same_contours(a, b)
+
+
+def test_fused_pass_against_the_oracle(c3s):
+    cfg, lat = c3s
+    g = dict(z0=cfg["z0"], dz=cfg["dz"], n_layers=cfg["n_layers"], x0=cfg["x0"], y0=cfg["y0"],
+             nx=cfg["nx"], ny=cfg["ny"], pixel=cfg["pixel"])
+    cont = lat.slice(**g, edge_ids=True, field_kernel="footprint", fused=True)   # no Sigma plane
+    assert _contours_vs_oracle(cont, _oracle(cfg, g), cfg, g) > 0
+
+
+def test_fused_bins_bit_exact_with_the_halo():
+    """The fused pass bins each tile with its next column and row: the binner
+    against its FP32 restatement with the one-pixel halo (on the jittered
+    Freudenthal block; the graded lattice's dyadic node grid happens to put no
+    box start within a pixel above a tile boundary)."""
+    cfg = synth.config(2, small=True)
+    lat = _cs().Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"])
+    for tile in (16, 32):
+        off, ids = lat.slab_bins(z0=cfg["z0"], dz=cfg["dz"], first_layer=0, n_slab_layers=4,
+                                 x0=cfg["x0"], y0=cfg["y0"], nx=cfg["nx"], ny=cfg["ny"],
+                                 pixel=cfg["pixel"], tile=tile, halo=True)
+        roff, rids = binning.bin_lists_fp32(cfg["nodes"], cfg["edges"], lat.R, z0=cfg["z0"],
+                                            dz=cfg["dz"], first_layer=0, n_slab_layers=4,
+                                            x0=cfg["x0"], y0=cfg["y0"], nx=cfg["nx"],
+                                            ny=cfg["ny"], pixel=cfg["pixel"], tile=tile,
+                                            halo=True)
+        assert np.array_equal(off, roff) and np.array_equal(ids, rids)
+        plain = lat.slab_bins(z0=cfg["z0"], dz=cfg["dz"], first_layer=0, n_slab_layers=4,
+                              x0=cfg["x0"], y0=cfg["y0"], nx=cfg["nx"], ny=cfg["ny"],
+                              pixel=cfg["pixel"], tile=tile)[1]
+        assert ids.size > plain.size   # the halo adds entries
+
+
+def test_fused_vertex_lists_grow_when_the_first_guess_is_short():
+    """A field of thin vertical struts every 3 pixels has about one crossing
+    per pixel, four times the first guess of the vertex lists' size: the chunk
+    is run again with room for them, and the contours equal the unfused ones."""
+    n, sp, px = 400, 0.15, 0.05
+    xs = (np.arange(n) + 0.5) * sp
+    X, Y = np.meshgrid(xs, xs)
+    top = np.stack([X.ravel(), Y.ravel(), np.full(n * n, 1.0)], 1)
+    bot = np.stack([X.ravel(), Y.ravel(), np.zeros(n * n)], 1)
+    nodes = np.concatenate([bot, top]).astype(np.float32)
+    edges = np.stack([np.arange(n * n), np.arange(n * n) + n * n], 1).astype(np.int32)
+    radius = np.full(n * n, 0.035, np.float32)
+    lat = _cs().Lattice(nodes, edges, radius, R=0.05)
+    g = dict(z0=0.5, dz=0.1, n_layers=2, x0=0.0, y0=0.0, nx=1200, ny=1200, pixel=px)
+    a = lat.slice(**g, edge_ids=True, field_kernel="footprint", fused=True)
+    b = lat.slice(**g, edge_ids=True, field_kernel="footprint")
+    assert a.xy.shape[0] > 2 * 1200 * 1200 // 4   # more than the first guess
+    _same_contours(a, b)

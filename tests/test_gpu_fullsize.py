@@ -36,7 +36,8 @@ def _edges_near(cfg, x0, y0, w, z_lo, z_hi):
     return nodes[used], remap[edges[sel]].astype(np.int32), cfg["radius"][sel], sel
 
 
-def _check_windows(cfg, lat, first, n, n_windows, seed, win=WIN):
+def _check_windows(cfg, lat, first, n, n_windows, seed, win=WIN, at=()):
+    """n_windows random windows, plus one at each (layer, i0, j0) of `at`."""
     nx, ny, px = cfg["nx"], cfg["ny"], cfg["pixel"]
     sig = torch.empty((n, ny, nx), dtype=torch.float32, device="cuda")
     z0 = cfg["z0"] + first * cfg["dz"]
@@ -46,10 +47,9 @@ def _check_windows(cfg, lat, first, n, n_windows, seed, win=WIN):
     r = np.random.default_rng(seed)
     W = nx + 2
     matched = 0
-    for _ in range(n_windows):
-        k = int(r.integers(0, n))
-        i0 = int(r.integers(0, nx - win))
-        j0 = int(r.integers(0, ny - win))
+    places = [(int(r.integers(0, n)), int(r.integers(0, nx - win)), int(r.integers(0, ny - win)))
+              for _ in range(n_windows)] + list(at)
+    for k, i0, j0 in places:
         wx0, wy0 = cfg["x0"] + i0 * px, cfg["y0"] + j0 * px
         z = z0 + k * cfg["dz"]
         sn, se, sr, _ = _edges_near(cfg, wx0, wy0, win * px, z, z)
@@ -80,12 +80,54 @@ def _check_windows(cfg, lat, first, n, n_windows, seed, win=WIN):
     return matched
 
 
-def test_graded_100M_windows():
+@pytest.fixture(scope="module")
+def graded_100m():
     import paper_2101_05031_gb300 as cs
     cfg = synth.config(3)
     lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], C=cfg["C"])
+    yield cfg, lat
+    lat.close()
+
+
+def _dense_band_window(cfg, win=WIN):
+    """(i0, j0) of a window centred where the graded density rho(x) = 0.1 +
+    0.3 (0.5 + 0.5 sin(2 pi x / 50) cos(2 pi y / 50)) peaks (x = 62.5, y = 100 mm)."""
+    px = cfg["pixel"]
+    return int((62.5 - cfg["x0"]) / px) - win // 2, int((100.0 - cfg["y0"]) / px) - win // 2
+
+
+def test_graded_100M_windows(graded_100m):
+    cfg, lat = graded_100m
     matched = _check_windows(cfg, lat, first=496, n=16, n_windows=6, seed=31)
     assert matched > 20
+
+
+def test_graded_100M_lowest_and_highest_layers_and_the_dense_band(graded_100m):
+    """The first and last 16 of the 1000 layers (where the lattice starts and
+    ends), with random windows and one in the densest band of rho(x)."""
+    cfg, lat = graded_100m
+    i0, j0 = _dense_band_window(cfg)
+    m = 0
+    for first, seed in ((0, 35), (cfg["n_layers"] - 16, 36)):
+        m += _check_windows(cfg, lat, first=first, n=16, n_windows=3, seed=seed,
+                            at=[(3, i0, j0), (12, i0, j0)])
+    assert m > 10
+
+
+def test_graded_100M_fused_pass_equals_the_default(graded_100m):
+    """The fused field and contour pass on 16 full layers of the 100M-strut
+    workload: the same contours, bit for bit, as the default path."""
+    cfg, lat = graded_100m
+    kw = dict(z0=cfg["z0"] + 496 * cfg["dz"], dz=cfg["dz"], n_layers=16, x0=cfg["x0"],
+              y0=cfg["y0"], nx=cfg["nx"], ny=cfg["ny"], pixel=cfg["pixel"], edge_ids=True,
+              on_device=True)
+    a = lat.slice(**kw, fused=True).to_host()
+    b = lat.slice(**kw).to_host()
+    assert a.xy.shape[0] > 1_000_000
+    for x, y in ((a.layer_loop_off, b.layer_loop_off), (a.loop_vert_off, b.loop_vert_off),
+                 (a.edge_id, b.edge_id)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.xy.view(np.uint32), b.xy.view(np.uint32))
 
 
 def test_freudenthal_430k_windows():
