@@ -40,8 +40,9 @@ NCU_FIELD = {
     "block": {"kernel": "k_field", "executed_frac": 8422.3 / (152 * 128 * 2),
               "dram_bytes_per_pixel_layer": 1.2835e9 / (64 * 2000 * 2000),
               "profile": "profiles/k_field_graded-10M.txt"},
-    "footprint": {"kernel": "k_field_fp", "executed_frac": None,
-                  "dram_bytes_per_pixel_layer": None,
+    "footprint": {"kernel": "k_field_fp",
+                  "executed_frac": (2 * 2876.6 + 1136.9 + 1613.3) / (152 * 128 * 2),
+                  "dram_bytes_per_pixel_layer": (0.717973e9 + 4.252283e9) / (264 * 2000 * 2000),
                   "profile": "profiles/k_field_fp_graded-10M.txt"},
 }
 HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
@@ -229,9 +230,18 @@ def radius_tuning(lat, cfg, iterations=20):
     target = torch.tensor(np.broadcast_to(target, (d[2], d[1], d[0])).copy(),
                           dtype=torch.float32, device="cuda")
     nodes = torch.tensor(cfg["nodes"], device="cuda")
-    r = torch.tensor(cfg["radius"], device="cuda")
+    r0 = torch.tensor(cfg["radius"], device="cuda")
     R = cfg["R"]
-    losses, lr = [], None
+    # one untimed iteration: the step size (0.01 mm at the 90th percentile of
+    # |grad|), and the first use of the autograd path and of torch's kernels
+    # (lazily loaded modules, seconds on first use)
+    rw = r0.clone().requires_grad_(True)
+    loss = 0.5 * ((VolumeFraction.apply(rw, nodes, lat, cells) - target) ** 2).sum()
+    loss.backward()
+    g90 = float(torch.quantile(rw.grad.detach().abs()[::16].float(), 0.9))
+    lr = 0.01 / max(g90, 1e-12)
+    r = r0.clone()
+    losses = []
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -242,9 +252,6 @@ def radius_tuning(lat, cfg, iterations=20):
         loss = 0.5 * ((vf - target) ** 2).sum()
         loss.backward()
         with torch.no_grad():
-            if lr is None:   # a first step of 0.01 mm at the 90th percentile of |grad|
-                g90 = float(torch.quantile(r.grad.abs()[::16].float(), 0.9))
-                lr = 0.01 / max(g90, 1e-12)
             r = (r - lr * r.grad).clamp(0.1, 0.9 * R)
         losses.append(loss.detach())
     e1.record(stream)
@@ -255,9 +262,9 @@ def radius_tuning(lat, cfg, iterations=20):
     return {"iterations": iterations, "ms_per_iteration": ms, "loss": curve,
             "loss_drop": curve[0] / max(curve[-1], 1e-30),
             "basis": "VolumeFraction.apply (lattice update + forward) and backward per "
-                     "iteration, CUDA events over all iterations; step 0.01 mm / (90th "
-                     "percentile of |grad|) fixed at the first iteration, radii clamped to "
-                     "[0.1, 0.9 R]"}
+                     "iteration, CUDA events over all iterations after one untimed iteration "
+                     "that fixes the step (0.01 mm / 90th percentile of |grad|); radii "
+                     "clamped to [0.1, 0.9 R]"}
 
 
 def run_vf(steps, warmup):
@@ -347,13 +354,19 @@ def run_batch(steps, warmup):
 
     plain_ms = _event_ms(plain, steps, warmup, stream)
     px = int(info.pixel_evals)
-    cands = [{"slab": int(info.cand_slab[i]), "ctas_per_sm": int(info.cand_ctas[i]),
+    kname = {1: "block", 2: "footprint"}
+    cands = [{"field_kernel": kname.get(int(info.cand_kernel[i]), "?"),
+              "tile": int(info.cand_tile[i]), "slab": int(info.cand_slab[i]),
+              "ctas_per_sm": int(info.cand_ctas[i]), "stage_records": int(info.cand_stage[i]),
               "ms": float(info.cand_ms[i])} for i in range(info.n_candidates)]
     out = {"workload": cfg["name"], "jobs": len(jobs),
            "struts": int(sum(jb["edges"].shape[0] for jb in cfg["jobs"])),
            "pixel_evals_per_step": px,
            "batched": {"ms_per_step": batch_ms, "pixel_evals_per_s": px / (batch_ms / 1e3),
-                       "slab": int(info.slab), "ctas_per_sm": int(info.ctas_per_sm),
+                       "field_kernel": kname.get(int(info.field_kernel), "?"),
+                       "tile": int(info.tile), "slab": int(info.slab),
+                       "ctas_per_sm": int(info.ctas_per_sm),
+                       "stage_records": int(info.stage_records),
                        "graph_nodes": int(info.graph_nodes), "queue_items": int(info.n_items),
                        "create_s": create_s, "plan_ms": info.plan_ms, "tune_ms": info.tune_ms,
                        "candidates": cands},
@@ -666,11 +679,7 @@ def main():
 
     for _ in range(args.warmup):
         step()
-    peak_main = cs.last_stats().device_bytes_peak
-    st0 = cs.last_stats()
-    plan = {"field_kernel": {1: "block", 2: "footprint"}.get(st0.field_kernel, "?"),
-            "tile": st0.tile, "slab": st0.slab, "stage_records": st0.stage_records,
-            "fused": bool(st0.fused)}
+
     # exact count of nonzero and of evaluated terms, once, outside the timed region
     pairs = evaluated = cand = 0
     if not args.no_count:
@@ -698,6 +707,10 @@ def main():
     # one more step, untimed, with every stage timed by events: the chunks then
     # run one after another (no two-chunk overlap), so each kernel runs alone
     st, _ = step(flags_time=True)
+    plan = {"field_kernel": {1: "block", 2: "footprint"}.get(st.field_kernel, "?"),
+            "tile": st.tile, "slab": st.slab, "stage_records": st.stage_records,
+            "fused": bool(st.fused)}
+    peak_main = st.device_bytes_peak
     field_ms, bin_ms, contour_ms, output_ms = st.field_ms, st.bin_ms, st.contour_ms, st.output_ms
     field_launches = st.field_launches
     staged_ms = field_ms + bin_ms + contour_ms + output_ms

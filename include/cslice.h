@@ -349,11 +349,16 @@ csl_status csl_volume_fraction_backward(csl_lattice* lat, const csl_cells* cells
  * of all jobs that reads nothing back into a CUDA graph: the binner and the
  * contour stages of the jobs run on parallel branches, and the field of all
  * jobs is one persistent kernel whose CTAs take (job, slab, tile) items from
- * a queue sorted longest tile list first. With autotune set, it times the
- * graph for every slab depth S in {2, 4, 8} and 2, 4 or 6 resident CTAs per
- * SM and keeps the fastest; the choice is cached per process for the same
- * job sizes. The tile is fixed at 16 x 16 pixels and the staging chunk at 256
- * records (one per thread of the 8-warp CTA).
+ * a queue sorted longest tile list first (the block or the footprint kernel,
+ * one for all jobs). With autotune set, it times the graph over a staged
+ * search and keeps the fastest: first the field kernel and tile T (block on
+ * 16-pixel tiles, footprint on 16- and 32-pixel tiles) at the default slab
+ * depth; then, for the best of those, slab depth S in {2, 4, 8} x resident
+ * CTAs per SM (2, 4, 6 for the block kernel; 2, 4 for the footprint kernel,
+ * whose shared-memory planes bound residency); then, for the footprint
+ * kernel, the records per staged copy K in {128, 256, 512}. The choice is
+ * cached per process for the same job sizes; csl_batch_info lists every
+ * timed candidate.
  *
  * csl_batch_run launches the graph on `stream` and waits for it. The jobs'
  * lattices are read at run time, so radii and node positions may change
@@ -371,10 +376,17 @@ csl_status csl_volume_fraction_backward(csl_lattice* lat, const csl_cells* cells
 typedef struct csl_batch csl_batch;   /* opaque */
 
 typedef struct csl_batch_opts {
-    int32_t autotune;         /* nonzero: time the (slab, CTAs per SM) candidates        */
+    int32_t autotune;         /* nonzero: time the candidates (field kernel and tile, slab,
+                                 CTAs per SM, staging chunk) and keep the fastest          */
     int32_t slab;             /* without autotune: 0 (8, or less for short jobs) or 2, 4, 8 */
     int32_t ctas_per_sm;      /* without autotune: 0 (4) or 1 .. 6                     */
     int32_t branches;         /* parallel graph branches for binner and contours: 0 (8) or 1 .. 32 */
+    int32_t field_kernel;     /* without autotune: CSL_FIELD_AUTO (the block kernel),
+                                 CSL_FIELD_BLOCK or CSL_FIELD_FOOTPRINT                 */
+    int32_t tile;             /* without autotune: 0 (16; 32 with the footprint kernel), 16, 32 */
+    int32_t stage_records;    /* without autotune: 0 (256) or a multiple of 32 up to 1024
+                                 (footprint kernel)                                      */
+    int32_t reserved_;
 } csl_batch_opts;
 
 #define CSL_BATCH_MAX_CANDIDATES 16
@@ -395,6 +407,13 @@ typedef struct csl_batch_info {
     int32_t cand_slab[CSL_BATCH_MAX_CANDIDATES];
     int32_t cand_ctas[CSL_BATCH_MAX_CANDIDATES];
     float cand_ms[CSL_BATCH_MAX_CANDIDATES];
+    int32_t cand_kernel[CSL_BATCH_MAX_CANDIDATES];   /* CSL_FIELD_BLOCK / _FOOTPRINT */
+    int32_t cand_tile[CSL_BATCH_MAX_CANDIDATES];
+    int32_t cand_stage[CSL_BATCH_MAX_CANDIDATES];
+    int32_t field_kernel;     /* chosen field kernel, tile and staging chunk              */
+    int32_t tile;
+    int32_t stage_records;
+    int32_t reserved_;
 } csl_batch_info;
 
 /*

@@ -110,7 +110,9 @@ class CellsDesc(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("autotune", c_i32), ("slab", c_i32), ("ctas_per_sm", c_i32), ("branches", c_i32)]
+    _fields_ = [("autotune", c_i32), ("slab", c_i32), ("ctas_per_sm", c_i32), ("branches", c_i32),
+                ("field_kernel", c_i32), ("tile", c_i32), ("stage_records", c_i32),
+                ("reserved_", c_i32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -120,7 +122,12 @@ class BatchInfo(ctypes.Structure):
                 ("tune_ms", c_f64), ("n_candidates", c_i32),
                 ("cand_slab", c_i32 * BATCH_MAX_CANDIDATES),
                 ("cand_ctas", c_i32 * BATCH_MAX_CANDIDATES),
-                ("cand_ms", c_f32 * BATCH_MAX_CANDIDATES)]
+                ("cand_ms", c_f32 * BATCH_MAX_CANDIDATES),
+                ("cand_kernel", c_i32 * BATCH_MAX_CANDIDATES),
+                ("cand_tile", c_i32 * BATCH_MAX_CANDIDATES),
+                ("cand_stage", c_i32 * BATCH_MAX_CANDIDATES),
+                ("field_kernel", c_i32), ("tile", c_i32), ("stage_records", c_i32),
+                ("reserved_", c_i32)]
 
 
 class CslError(RuntimeError):

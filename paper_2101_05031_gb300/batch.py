@@ -25,11 +25,13 @@ class _DeviceArray:
 
 class Batch:
     """jobs: list of (Lattice, dict(z0, dz, n_layers, x0, y0, nx, ny, pixel
-    [, edge_ids])). autotune: time slab depth x CTAs per SM and keep the best
-    (cached per process for the same job sizes)."""
+    [, edge_ids])). autotune: time the field kernel and tile, slab depth x CTAs
+    per SM and the staging chunk, and keep the best (cached per process for
+    the same job sizes); otherwise field_kernel ("auto" = "block", or
+    "footprint"), tile (0, 16, 32) and stage_records (0 = 256) as given."""
 
     def __init__(self, jobs, *, autotune=False, slab=0, ctas_per_sm=0, branches=0,
-                 stream=None):
+                 field_kernel="auto", tile=0, stage_records=0, stream=None):
         n = len(jobs)
         self._lats = [lat for lat, _ in jobs]   # the lattices must outlive the batch
         self._shapes = []
@@ -45,7 +47,8 @@ class Batch:
             x.x0, x.y0, x.pixel = float(d["x0"]), float(d["y0"]), float(d["pixel"])
             x.flags = _lib.SLICE_EDGE_IDS if d.get("edge_ids") else 0
             self._shapes.append((x.n_layers, x.ny, x.nx))
-        opts = _lib.BatchOpts(1 if autotune else 0, int(slab), int(ctas_per_sm), int(branches))
+        opts = _lib.BatchOpts(1 if autotune else 0, int(slab), int(ctas_per_sm), int(branches),
+                              _lib.FIELD_KERNELS[field_kernel], int(tile), int(stage_records), 0)
         h = ctypes.c_void_p()
         _lib.check(_lib.load().csl_batch_create(handles, descs, n, ctypes.byref(opts),
                                                 _stream_ptr(stream), ctypes.byref(h)))

@@ -40,6 +40,7 @@ struct csl_batch {
     };
     std::vector<Job> jobs;
     int S = 8, ctas = 4, n_sm = 0, branches = 8;
+    int kernel = CSL_FIELD_BLOCK, T = 16, K = 256;   // field kernel, tile, staging chunk
     cudaStream_t st = nullptr;           // planning, capture and copies
     std::vector<cudaStream_t> side;      // capture branches
     std::vector<cudaEvent_t> ev;         // fork / join events of the capture
@@ -101,8 +102,15 @@ double now_ms() {
 }
 
 // ---- per-process autotuning cache ----
-std::mutex g_tune_mu;
-std::map<uint64_t, std::pair<int, int>> g_tune_cache;   // key -> (slab, CTAs per SM)
+std::mutex& g_tune_cache_mu() {
+    static std::mutex mu;
+    return mu;
+}
+// key -> (slab, CTAs per SM, field kernel, tile, staging chunk)
+struct TuneChoice {
+    int S, ctas, kernel, T, K;
+};
+std::map<uint64_t, TuneChoice> g_tune_cache;
 
 uint64_t fnv(uint64_t h, const void* p, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(p);
@@ -128,7 +136,7 @@ uint64_t workload_key(const csl_batch* b) {
 }
 
 // ---- planning: every job once through the ordinary (reading) pipeline ----
-void plan_jobs(csl_batch* b, int S) {
+void plan_jobs(csl_batch* b, int S, int kernel, int T, int K) {
     b->drop_graph();
     b->fb = FieldBatch();
     uint32_t* flag = b->flag_d.as<uint32_t>();
@@ -136,8 +144,10 @@ void plan_jobs(csl_batch* b, int S) {
     for (auto& J : b->jobs) {
         csl_slice_desc d = J.d;
         d.slab = S;
-        d.tile = 16;                         // the persistent field kernel's tiles
-        d.field_kernel = CSL_FIELD_BLOCK;
+        d.tile = T;
+        d.field_kernel = (int16_t)kernel;
+        d.stage_records = (int16_t)K;
+        d.flags &= ~CSL_SLICE_FUSED;
         d.chunk_layers = d.n_layers;
         const SlicePlan p = make_plan(J.L, d);
         require_arg(p.chunk >= d.n_layers,
@@ -163,6 +173,9 @@ void plan_jobs(csl_batch* b, int S) {
     read_to_host(&f, flag, 4, b->st);
     if (f) fail(CSL_ERR_CUDA, "batch planning: a stage reported inconsistent sizes");
     b->S = S;
+    b->kernel = kernel;
+    b->T = T;
+    b->K = K;
     int64_t pairs = 0, cross = 0, loops = 0;
     for (auto& J : b->jobs) {
         pairs += J.plan.n_pairs;
@@ -279,8 +292,17 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
         *out = nullptr;
         require_arg(n_jobs >= 1, "n_jobs must be >= 1");
         require_arg(lats != nullptr && descs != nullptr, "lats or descs is NULL");
-        csl_batch_opts o = {0, 0, 0, 0};
+        csl_batch_opts o = {0, 0, 0, 0, 0, 0, 0, 0};
         if (opts) o = *opts;
+        require_arg(o.field_kernel == CSL_FIELD_AUTO || o.field_kernel == CSL_FIELD_BLOCK ||
+                        o.field_kernel == CSL_FIELD_FOOTPRINT,
+                    "field_kernel must be CSL_FIELD_AUTO, CSL_FIELD_BLOCK or CSL_FIELD_FOOTPRINT");
+        require_arg(o.tile == 0 || o.tile == 16 || o.tile == 32, "tile must be 0, 16 or 32");
+        require_arg(o.tile != 32 || o.field_kernel == CSL_FIELD_FOOTPRINT,
+                    "32-pixel tiles need the footprint field kernel");
+        require_arg(o.stage_records == 0 || (o.stage_records >= 32 && o.stage_records <= 1024 &&
+                                             o.stage_records % 32 == 0),
+                    "stage_records must be 0 or a multiple of 32 up to 1024");
         require_arg(o.slab == 0 || o.slab == 2 || o.slab == 4 || o.slab == 8,
                     "slab must be 0, 2, 4 or 8");
         require_arg(o.ctas_per_sm >= 0 && o.ctas_per_sm <= 6, "ctas_per_sm must be in [0, 6]");
@@ -336,17 +358,24 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
                 mo += J.mask_words;
             }
 
-            int S = o.slab;
-            if (S == 0) S = min_layers >= 8 ? 8 : (min_layers >= 4 ? 4 : 2);
+            const int S0 = min_layers >= 8 ? 8 : (min_layers >= 4 ? 4 : 2);
+            int S = o.slab ? o.slab : S0;
             int ctas = o.ctas_per_sm ? o.ctas_per_sm : 4;
+            int kernel = o.field_kernel == CSL_FIELD_FOOTPRINT ? CSL_FIELD_FOOTPRINT
+                                                               : CSL_FIELD_BLOCK;
+            int T = o.tile ? o.tile : (kernel == CSL_FIELD_FOOTPRINT ? 32 : 16);
+            int K = o.stage_records ? o.stage_records : 256;
             const uint64_t key = workload_key(b);
             bool tune = o.autotune != 0;
             if (tune) {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
+                std::lock_guard<std::mutex> lk(g_tune_cache_mu());
                 auto it = g_tune_cache.find(key);
                 if (it != g_tune_cache.end()) {
-                    S = it->second.first;
-                    ctas = it->second.second;
+                    S = it->second.S;
+                    ctas = it->second.ctas;
+                    kernel = it->second.kernel;
+                    T = it->second.T;
+                    K = it->second.K;
                     tune = false;
                     b->info.from_cache = 1;
                 }
@@ -355,50 +384,78 @@ csl_status csl_batch_create(csl_lattice* const* lats, const csl_slice_desc* desc
                 const double t0 = now_ms();
                 double plan_ms = 0.0;
                 float best = 1e30f;
-                int bS = 8, bC = 4, nc = 0;
-                const int slabs[3] = {2, 4, 8}, ctas_c[3] = {2, 4, 6};
-                for (int si = 0; si < 3; ++si) {
+                TuneChoice bc{S0, 4, CSL_FIELD_BLOCK, 16, 256};
+                int nc = 0;
+                auto plan = [&](int s_, int k_, int t_, int K_) {
+                    if (b->S == s_ && b->kernel == k_ && b->T == t_ && b->K == K_ && b->fb.n_items)
+                        return;
                     const double tp = now_ms();
-                    plan_jobs(b, slabs[si]);
+                    plan_jobs(b, s_, k_, t_, K_);
                     plan_ms += now_ms() - tp;
+                };
+                auto try_one = [&](int s_, int c_, int k_, int t_, int K_) {
+                    plan(s_, k_, t_, K_);
+                    capture(b, c_);
+                    const float ms = time_graph(b);
+                    if (nc < CSL_BATCH_MAX_CANDIDATES) {
+                        b->info.cand_slab[nc] = s_;
+                        b->info.cand_ctas[nc] = c_;
+                        b->info.cand_kernel[nc] = k_;
+                        b->info.cand_tile[nc] = t_;
+                        b->info.cand_stage[nc] = K_;
+                        b->info.cand_ms[nc] = ms;
+                        ++nc;
+                    }
+                    if (ms < best) {
+                        best = ms;
+                        bc = TuneChoice{s_, c_, k_, t_, K_};
+                    }
+                };
+                // 1. field kernel and tile, at the default slab depth
+                try_one(S0, 4, CSL_FIELD_BLOCK, 16, 256);
+                try_one(S0, 4, CSL_FIELD_FOOTPRINT, 32, 256);
+                try_one(S0, 4, CSL_FIELD_FOOTPRINT, 16, 256);
+                // 2. slab depth x CTAs per SM for the best of them
+                const TuneChoice k1 = bc;
+                const int slabs[3] = {2, 4, 8};
+                for (int si = 0; si < 3; ++si) {
+                    if (slabs[si] > min_layers && slabs[si] != 2) continue;
+                    const int cand_c[3] = {2, 4, 6};
                     for (int ci = 0; ci < 3; ++ci) {
-                        capture(b, ctas_c[ci]);
-                        const float ms = time_graph(b);
-                        if (nc < CSL_BATCH_MAX_CANDIDATES) {
-                            b->info.cand_slab[nc] = slabs[si];
-                            b->info.cand_ctas[nc] = ctas_c[ci];
-                            b->info.cand_ms[nc] = ms;
-                            ++nc;
-                        }
-                        if (ms < best) {
-                            best = ms;
-                            bS = slabs[si];
-                            bC = ctas_c[ci];
-                        }
+                        if (k1.kernel == CSL_FIELD_FOOTPRINT && cand_c[ci] > 4) continue;
+                        if (slabs[si] == S0 && cand_c[ci] == 4) continue;   // timed in step 1
+                        try_one(slabs[si], cand_c[ci], k1.kernel, k1.T, 256);
                     }
                 }
-                b->info.n_candidates = nc;
-                S = bS;
-                ctas = bC;
-                if (b->S != S) {
-                    const double tp = now_ms();
-                    plan_jobs(b, S);
-                    plan_ms += now_ms() - tp;
+                // 3. the footprint kernel's staging chunk
+                if (bc.kernel == CSL_FIELD_FOOTPRINT) {
+                    const TuneChoice k2 = bc;
+                    for (int kk : {128, 512}) try_one(k2.S, k2.ctas, k2.kernel, k2.T, kk);
                 }
+                b->info.n_candidates = nc;
+                S = bc.S;
+                ctas = bc.ctas;
+                kernel = bc.kernel;
+                T = bc.T;
+                K = bc.K;
+                plan(S, kernel, T, K);
                 capture(b, ctas);
                 b->info.plan_ms = plan_ms;
                 b->info.tune_ms = now_ms() - t0 - plan_ms;
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune_cache[key] = {S, ctas};
+                std::lock_guard<std::mutex> lk(g_tune_cache_mu());
+                g_tune_cache[key] = TuneChoice{S, ctas, kernel, T, K};
             } else {
                 const double tp = now_ms();
                 b->ctas = ctas;
-                plan_jobs(b, S);
+                plan_jobs(b, S, kernel, T, K);
                 b->info.plan_ms = now_ms() - tp;
                 capture(b, ctas);
             }
             b->info.slab = b->S;
             b->info.ctas_per_sm = b->ctas;
+            b->info.field_kernel = b->kernel;
+            b->info.tile = b->T;
+            b->info.stage_records = b->K;
             CSL_CUDA(cudaStreamSynchronize(b->st));
         } catch (...) {
             delete b;

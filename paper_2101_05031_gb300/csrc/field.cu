@@ -420,25 +420,33 @@ void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb,
     const int n_jobs = (int)jobs.size();
     if (n_jobs == 0) fail(CSL_ERR_INVALID_ARG, "empty batch");
     const int S = jobs[0].g.S;
+    const int kern = jobs[0].g.kernel, T = jobs[0].g.T, K = jobs[0].g.K;
     size_t n_org = 0;
     std::vector<int64_t> off(n_jobs + 1, 0);
     for (int j = 0; j < n_jobs; ++j) {
         const ChunkGeom& g = jobs[j].g;
         if (g.S != S) fail(CSL_ERR_INVALID_ARG, "batch: one slab depth for every job");
-        if (g.T != kTile || g.kernel != kFieldBlock)
-            fail(CSL_ERR_INVALID_ARG, "batch: the persistent field kernel takes 16-pixel tiles");
+        if (g.kernel != kern || g.T != T || g.K != K || g.fused)
+            fail(CSL_ERR_INVALID_ARG, "batch: one field kernel, tile and staging chunk");
+        if (kern == kFieldBlock && T != kTile)
+            fail(CSL_ERR_INVALID_ARG, "batch: the block field kernel takes 16-pixel tiles");
         n_org += (size_t)g.ntx + g.nty + g.n_slabs;
         off[j + 1] = off[j] + (int64_t)g.n_slabs * g.ntx * g.nty;
     }
     if (off[n_jobs] >= 0xffffffffLL) fail(CSL_ERR_CAPACITY, "batch: more than 2^32 - 1 tiles");
     fb.S = S;
+    fb.kernel = kern;
+    fb.T = T;
+    fb.K = K;
     fb.n_items = off[n_jobs];
     fb.origins.alloc_persistent(n_org * sizeof(float2));
     std::vector<FieldJob> hj(n_jobs);
+    std::vector<const float2*> orgs(n_jobs);
     size_t o = 0;
     for (int j = 0; j < n_jobs; ++j) {
         const FieldBatchJob& J = jobs[j];
         float2* org = fb.origins.as<float2>() + o;
+        orgs[j] = org;
         launch_origins(J.g, org, s);
         o += (size_t)J.g.ntx + J.g.nty + J.g.n_slabs;
         hj[j].c = make_field_const(J.g, (float)J.L->C, org);
@@ -453,6 +461,13 @@ void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb,
     DevBuf off_d((size_t)(n_jobs + 1) * 8, s);
     CSL_CUDA(cudaMemcpyAsync(fb.jobs.get(), hj.data(), sizeof(FieldJob) * n_jobs,
                              cudaMemcpyHostToDevice, s));
+    std::vector<unsigned char> hfp;
+    if (kern == kFieldFootprint) {
+        fp_batch_jobs(jobs, orgs.data(), hfp);
+        fb.fp_jobs.alloc_persistent(hfp.size());
+        CSL_CUDA(cudaMemcpyAsync(fb.fp_jobs.get(), hfp.data(), hfp.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
     CSL_CUDA(cudaMemcpyAsync(off_d.get(), off.data(), (size_t)(n_jobs + 1) * 8,
                              cudaMemcpyHostToDevice, s));
     const size_t n = (size_t)fb.n_items;
@@ -482,6 +497,10 @@ void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s) {
     const uint2* items = fb.items.as<uint2>();
     const uint32_t* order = fb.vals.as<uint32_t>();
     uint32_t* counter = fb.counter.as<uint32_t>();
+    if (fb.kernel == kFieldFootprint) {
+        fp_batch_launch(fb.fp_jobs.get(), items, order, n, counter, fb.T, fb.S, fb.K, n_ctas, s);
+        return;
+    }
     switch (fb.S) {
         case 1: k_field_batch<1><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;
         case 2: k_field_batch<2><<<n_ctas, kFieldThreads, 0, s>>>(jobs, items, order, n, counter); break;

@@ -35,7 +35,10 @@
 // the block kernel loses nothing and keeps its sums in registers.
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <vector>
 
 #include "field_tile.cuh"
 #include "slice.cuh"
@@ -486,6 +489,59 @@ k_field_fp(const csl_rec* __restrict__ recs, const uint32_t* __restrict__ tstart
                                       blockIdx.y, smem, &bar, phase);
 }
 
+// One job of a batch for the persistent footprint kernel.
+struct FpJob {
+    FpConst c;
+    const csl_rec* recs;   // the binned records, in list order
+    const uint32_t* tstart;
+    const uint32_t* tend;
+    float* sigma;
+    uint32_t* mask;
+};
+static_assert(sizeof(FpJob) % 4 == 0, "FpJob is copied as 32-bit words");
+
+// Persistent footprint field kernel over the (job, slab, tile) items of a
+// batch, in the order `order` gives (longest tile lists first): each CTA takes
+// the next item from a shared counter. Every job has the same tile side, slab
+// depth and staging chunk.
+template <int T, int S>
+__global__ void __launch_bounds__(32 * S)
+k_field_fp_batch(const FpJob* __restrict__ jobs, const uint2* __restrict__ items,
+                 const uint32_t* __restrict__ order, uint32_t n_items, uint32_t* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_item;
+    __shared__ FpJob s_job;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    uint32_t cur_job = 0xffffffffu;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= n_items) break;
+        const uint2 item = items[order[it]];
+        if (item.x != cur_job) {   // consecutive items often belong to the same job
+            cur_job = item.x;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs + item.x);
+            for (int i = threadIdx.x; i < (int)(sizeof(FpJob) / 4); i += 32 * S)
+                reinterpret_cast<uint32_t*>(&s_job)[i] = src[i];
+            __syncthreads();
+        }
+        const uint32_t n_tiles = (uint32_t)s_job.c.n_tiles;
+        if (!field_tile_fp<T, S, false, false>(s_job.recs, s_job.tstart, s_job.tend, s_job.c,
+                                               s_job.sigma, s_job.mask, nullptr,
+                                               (int)(item.y % n_tiles), (int)(item.y / n_tiles),
+                                               smem, &bar, phase))
+            break;   // a bulk copy gave up (reported): this CTA takes no more items
+        __syncthreads();   // shared memory is reused by the next item
+    }
+}
+
 template <int T, int S, bool FUSED>
 size_t fp_smem_bytes(int K) {
     return (size_t)S * (FUSED ? T + 1 : T) * plane_pitch<T>() * sizeof(float) +
@@ -516,12 +572,9 @@ void launch_fp_count(const FpConst& c, dim3 grid, const csl_rec* recs, const uin
     }
 }
 
-}  // namespace
 
-void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const float2* org,
-                    uint32_t* err, float* sigma, uint32_t* mask, unsigned long long* count_pairs,
-                    cudaStream_t s, FusedVerts* fv) {
-    FpConst c;
+FpConst make_fp_const(const ChunkGeom& g, float C, const float2* org, uint32_t* err) {
+    FpConst c{};
     c.nx = g.nx;
     c.ny = g.ny;
     c.ntx = g.ntx;
@@ -544,6 +597,15 @@ void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const flo
     c.err = err;
     c.fx0 = (float)g.x0;
     c.fy0 = (float)g.y0;
+    return c;
+}
+
+}  // namespace
+
+void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const float2* org,
+                    uint32_t* err, float* sigma, uint32_t* mask, unsigned long long* count_pairs,
+                    cudaStream_t s, FusedVerts* fv) {
+    FpConst c = make_fp_const(g, C, org, err);
     const bool fused = g.fused;
     if (fused != (fv != nullptr) || (fused && !mask))
         fail(CSL_ERR_INVALID_ARG, "fused pass: vertex lists and mask are required");
@@ -574,6 +636,45 @@ void field_chunk_fp(const ChunkGeom& g, const SlabBins& bins, float C, const flo
     CSL_FP_CASE(32, 8)
 #undef CSL_FP_CASE
     fail(CSL_ERR_INVALID_ARG, "footprint field: tile 16 or 32, slab 1, 2, 4 or 8");
+}
+
+// Batch jobs for the persistent footprint kernel (device array of FpJob).
+void fp_batch_jobs(const std::vector<FieldBatchJob>& jobs, const float2* const* orgs,
+                   std::vector<unsigned char>& host) {
+    host.assign(jobs.size() * sizeof(FpJob), 0);
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const FieldBatchJob& J = jobs[j];
+        FpJob f;
+        f.c = make_fp_const(J.g, (float)J.L->C, orgs[j], J.err);
+        f.recs = J.bins->recs.as<csl_rec>();
+        f.tstart = J.bins->tile_start.as<uint32_t>();
+        f.tend = J.bins->tile_end.as<uint32_t>();
+        f.sigma = J.sigma;
+        f.mask = J.mask;
+        memcpy(host.data() + j * sizeof(FpJob), &f, sizeof(FpJob));
+    }
+}
+
+void fp_batch_launch(const void* jobs, const uint2* items, const uint32_t* order, uint32_t n,
+                     uint32_t* counter, int T, int S, int K, int n_ctas, cudaStream_t s) {
+    const FpJob* J = static_cast<const FpJob*>(jobs);
+#define CSL_FPB_CASE(TV, SV)                                                                 \
+    if (T == TV && S == SV) {                                                                \
+        const size_t smem = fp_smem_bytes<TV, SV, false>(K);                                 \
+        CSL_CUDA(cudaFuncSetAttribute(k_field_fp_batch<TV, SV>,                              \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_field_fp_batch<TV, SV><<<n_ctas, 32 * SV, smem, s>>>(J, items, order, n, counter);  \
+        CSL_LAUNCH_CHECK("batch footprint field");                                           \
+        return;                                                                              \
+    }
+    CSL_FPB_CASE(16, 2)
+    CSL_FPB_CASE(16, 4)
+    CSL_FPB_CASE(16, 8)
+    CSL_FPB_CASE(32, 2)
+    CSL_FPB_CASE(32, 4)
+    CSL_FPB_CASE(32, 8)
+#undef CSL_FPB_CASE
+    fail(CSL_ERR_INVALID_ARG, "batch footprint field: tile 16 or 32, slab 2, 4 or 8");
 }
 
 }  // namespace csl

@@ -132,24 +132,46 @@ __device__ __forceinline__ float2 fused_vertex(const FusedIn& F, const Dense& D,
     return F.verts[(int64_t)F.tbase[tl] + F.roff[tl * (F.T + 1) + b + 1] + rank];
 }
 
-__device__ __forceinline__ float value_at(const float* __restrict__ sg, const MsConst& c, int I,
-                                          int J) {
-    if (I < 1 || J < 1 || I > c.nx || J > c.ny) return 0.0f;
-    return sg[(int64_t)(J - 1) * c.nx + (I - 1)];
-}
 
-// grid: x over (row J <= ny, mask word k), y = layer. FUSED: vertices and
-// saddle decisions from the fused pass (F) instead of Sigma.
+// A block of k_emit covers a band of kEmitRows cell rows and kEmitWords mask
+// words (32 cells each) of one layer: one thread per (row, word). The Sigma
+// values its vertices and saddles need (pixel rows J0 - 1 .. J0 + kEmitRows - 1,
+// columns 32 k0 - 1 .. 32 (k0 + kEmitWords) - 1) are staged into shared memory
+// first with coalesced loads, so that every Sigma row is read from DRAM about
+// once instead of as scattered words at each crossing.
+constexpr int kEmitRows = 8, kEmitWords = 32;
+constexpr int kEmitCols = 32 * kEmitWords + 1;
+
+// grid: x over (band of kEmitRows rows J <= ny, segment of kEmitWords mask
+// words), y = layer. FUSED: vertices and saddle decisions from the fused pass
+// (F) instead of Sigma.
 template <bool FUSED>
 __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
-                       MsConst c, Dense D, FusedIn F, Xing* __restrict__ rec,
-                       uint32_t* __restrict__ pred, uint32_t n_cap, uint32_t* flag) {
+                       MsConst c, Dense D, FusedIn F, Xing* __restrict__ rec, uint32_t n_cap,
+                       uint32_t* flag) {
+    __shared__ float s_sig[FUSED ? 1 : (kEmitRows + 1) * kEmitCols];
     const int layer = blockIdx.y;
-    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (uint32_t)(c.ny + 1) * (uint32_t)c.mwr) return;
-    const int J = (int)(idx / (uint32_t)c.mwr), k = (int)(idx - (uint32_t)J * c.mwr);
+    const int n_segs = (c.mwr + kEmitWords - 1) / kEmitWords;
+    const int band = blockIdx.x / n_segs, seg = blockIdx.x - band * n_segs;
+    const int J0 = band * kEmitRows, k0 = seg * kEmitWords;
+    const int J = J0 + (int)(threadIdx.x / kEmitWords), k = k0 + (int)(threadIdx.x % kEmitWords);
     const uint32_t* m = mask + (int64_t)layer * c.mask_wpl;
     const float* sg = FUSED ? nullptr : sigma + (int64_t)layer * c.nx * c.ny;
+    if (!FUSED) {   // pixel (i, j) -> s_sig[(j - (J0 - 1)) * kEmitCols + i - (32 k0 - 1)]
+        const int i0 = 32 * k0 - 1, j0 = J0 - 1;
+        for (int q = threadIdx.x; q < (kEmitRows + 1) * kEmitCols; q += blockDim.x) {
+            const int r = q / kEmitCols, col = q - r * kEmitCols;
+            const int i = i0 + col, j = j0 + r;
+            s_sig[q] = (i >= 0 && j >= 0 && i < c.nx && j < c.ny) ? sg[(int64_t)j * c.nx + i]
+                                                                   : 0.0f;
+        }
+        __syncthreads();
+    }
+    // Sigma at padded sample (I, J) of this block (0 outside the grid, like the ring)
+    auto value_s = [&](int I, int J2) -> float {
+        return s_sig[(J2 - J0) * kEmitCols + (I - 32 * k0)];
+    };
+    if (J > c.ny || k >= c.mwr) return;
     const bool last = k + 1 >= c.mwr;
     const uint32_t in0 = m[(int64_t)J * c.mwr + k];
     const uint32_t in1 = last ? 0u : m[(int64_t)J * c.mwr + k + 1];
@@ -194,7 +216,7 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
         };
         const bool h_own = (hb >> b) & 1u, v_own = (vb >> b) & 1u;
         // Sigma only where a vertex is placed (or a saddle is decided)
-        const float v0 = (!FUSED && (h_own || v_own)) ? value_at(sg, c, I, J) : 0.0f;
+        const float v0 = (!FUSED && (h_own || v_own)) ? value_s(I, J) : 0.0f;
         const int64_t eb = 2 * ((int64_t)J * c.W + I);
         if (h_own) {   // vertex on the bottom edge (I, J) -> (I+1, J)
             const uint32_t id = id_bottom;
@@ -203,7 +225,7 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
             if (FUSED) {
                 xy = fused_vertex(F, D, layer, I, J, 0);
             } else {
-                const float v1 = value_at(sg, c, I + 1, J);
+                const float v1 = value_s(I + 1, J);
                 const float sa = in_c0 ? v0 : v1, sbv = in_c0 ? v1 : v0;
                 const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
                 const float xp = in_c0 ? ((float)I - 0.5f + t) : ((float)I + 0.5f - t);
@@ -219,7 +241,7 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
             if (FUSED) {
                 xy = fused_vertex(F, D, layer, I, J, 1);
             } else {
-                const float v3 = value_at(sg, c, I, J + 1);
+                const float v3 = value_s(I, J + 1);
                 const float sa = in_c0 ? v0 : v3, sbv = in_c0 ? v3 : v0;
                 const float t = __fdividef(sa - c.C, sa - sbv);   // in [0, 1]; sa > C > sbv
                 const float yp = in_c0 ? ((float)J - 0.5f + t) : ((float)J + 0.5f - t);
@@ -234,13 +256,9 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
         const uint32_t enter = cs & ~nxt & 0xfu;   // inside -> outside
         const uint32_t leave = ~cs & nxt & 0xfu;   // outside -> inside
         if (__popc(enter) == 1) {
-            const uint32_t a = side(__ffs(enter) - 1), b = side(__ffs(leave) - 1);
-            if (a < n_cap && b < n_cap) {
-                rec[a].succ = b;
-                pred[b] = a;
-            } else {
-                atomicOr(flag, 1u);
-            }
+            const uint32_t a = side(__ffs(enter) - 1);
+            if (a < n_cap) rec[a].succ = side(__ffs(leave) - 1);
+            else atomicOr(flag, 1u);
         } else if (enter) {
             bool joined;
             if (FUSED) {
@@ -248,23 +266,35 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
                                              (I >> 5)];
                 joined = (sw >> (I & 31)) & 1u;
             } else {
-                const float w0 = value_at(sg, c, I, J), w1 = value_at(sg, c, I + 1, J);
-                const float w2 = value_at(sg, c, I + 1, J + 1), w3 = value_at(sg, c, I, J + 1);
+                const float w0 = value_s(I, J), w1 = value_s(I + 1, J);
+                const float w2 = value_s(I + 1, J + 1), w3 = value_s(I, J + 1);
                 joined = 0.25f * (w0 + w1 + w2 + w3) >= c.C;
             }
             const int k0 = __ffs(enter) - 1, k1 = 31 - __clz(enter);
             const uint32_t a0 = side(k0), a1 = side(k1);
-            const uint32_t b0 = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
-            const uint32_t b1 = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
-            if (a0 < n_cap && a1 < n_cap && b0 < n_cap && b1 < n_cap) {
-                rec[a0].succ = b0;
-                rec[a1].succ = b1;
-                pred[b0] = a0;
-                pred[b1] = a1;
+            if (a0 < n_cap && a1 < n_cap) {
+                rec[a0].succ = side(joined ? ((k0 + 1) & 3) : ((k0 + 3) & 3));
+                rec[a1].succ = side(joined ? ((k1 + 1) & 3) : ((k1 + 3) & 3));
             } else {
                 atomicOr(flag, 1u);
             }
         }
+    }
+}
+
+// pred[succ[i]] = i (thread i writes next to its neighbours' targets: the
+// successors of consecutive crossings are close). A successor out of range is
+// reported through *status and nothing is written. (Writing these links in
+// the emit kernel beside the successors made the contour stage slower: the
+// emit kernel is bound by its dependent loads, and the scattered stores
+// lengthened it more than this streaming pass costs.)
+__global__ void k_pred(const Xing* __restrict__ rec, int64_t n, uint32_t* __restrict__ pred,
+                       uint32_t* status) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = rec[i].succ;
+        if ((int64_t)s < n) pred[s] = (uint32_t)i;
+        else atomicOr(status, ST_CAPACITY);
     }
 }
 
@@ -699,13 +729,12 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     if (n_cross >= ((int64_t)1 << 31)) fail(CSL_ERR_CAPACITY, "marching squares: too many crossings");
     DevBuf rec((size_t)n_cross * sizeof(Xing), s);
     CSL_CUDA(cudaMemsetAsync(rec.get(), 0xff, (size_t)n_cross * sizeof(Xing), s));
-    // pred[succ[i]] = i, written by the emit kernel beside each successor link
-    DevBuf pred((size_t)n_cross * 4, s);
-    CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
+
     Dense D{ew.as<uint32_t>(), prefix.as<uint32_t>(), c.edge_wpl, c.ewr};
     {
-        const int64_t n_thr = (int64_t)(c.ny + 1) * c.mwr;
-        dim3 grid((unsigned)ceil_div(n_thr, 256), (unsigned)g.n_layers);
+        const int64_t n_bands = ceil_div((int64_t)c.ny + 1, kEmitRows);
+        const int64_t n_segs = ceil_div((int64_t)c.mwr, kEmitWords);
+        dim3 grid((unsigned)(n_bands * n_segs), (unsigned)g.n_layers);
         FusedIn F{};
         if (fv) {
             F.tbase = fv->tbase.as<uint32_t>();
@@ -716,17 +745,20 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
             F.ntx = g.ntx;
             F.n_tiles = g.ntx * g.nty;
             k_emit<true><<<grid, 256, 0, s>>>(sigma, mask, c, D, F, rec.as<Xing>(),
-                                              pred.as<uint32_t>(), (uint32_t)n_cross, flag);
+                                              (uint32_t)n_cross, flag);
         } else {
             k_emit<false><<<grid, 256, 0, s>>>(sigma, mask, c, D, F, rec.as<Xing>(),
-                                               pred.as<uint32_t>(), (uint32_t)n_cross, flag);
+                                               (uint32_t)n_cross, flag);
         }
         CSL_LAUNCH_CHECK("ms emit");
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
-    DevBuf sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
+    DevBuf pred((size_t)n_cross * 4, s), sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
     DevBuf nxt((size_t)n_cross * 4, s);
+    CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
+    k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
+    CSL_LAUNCH_CHECK("ms pred");
     k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
                                      sflag.as<uint32_t>(), nxt.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms splitter flags");

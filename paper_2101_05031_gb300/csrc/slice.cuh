@@ -116,12 +116,19 @@ struct FieldBatchJob {
     uint32_t* err;          // device word OR-ed with ST_TIMEOUT when a wait gives up
 };
 struct FieldBatch {
-    DevBuf jobs, origins, items, keys, vals, tmp_keys, tmp_vals, counter;
+    DevBuf jobs, fp_jobs, origins, items, keys, vals, tmp_keys, tmp_vals, counter;
     int64_t n_items = 0;
     int S = 0;
+    int kernel = kFieldBlock, T = kTile, K = 256;   // the jobs' field kernel, tile, staging chunk
 };
 // One-time tables (synchronises s).
 void field_batch_prepare(const std::vector<FieldBatchJob>& jobs, FieldBatch& fb, cudaStream_t s);
+// The footprint kernel's part of them (field_fp.cu): the jobs as the persistent
+// footprint kernel reads them (host bytes, one record per job), and its launch.
+void fp_batch_jobs(const std::vector<FieldBatchJob>& jobs, const float2* const* orgs,
+                   std::vector<unsigned char>& host);
+void fp_batch_launch(const void* jobs, const uint2* items, const uint32_t* order, uint32_t n,
+                     uint32_t* counter, int T, int S, int K, int n_ctas, cudaStream_t s);
 // The run itself: queue order, counter reset, persistent launch of n_ctas
 // CTAs; reads nothing back (capturable in a CUDA graph).
 void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s);

@@ -32,13 +32,14 @@ def _jobs(n_layers=12):
     return jobs, specs
 
 
-def _per_job(lat, d, slab):
-    """Per-job slicing with the batch's field kernel (the block kernel on
-    16-pixel tiles), so that both sum the same terms in the same order."""
+def _per_job(lat, d, slab, kernel="block", tile=16, stage=0):
+    """Per-job slicing with the batch's field kernel and tile (default: the
+    block kernel on 16-pixel tiles), so that both sum the same terms in the
+    same order."""
     sig = torch.empty((d["n_layers"], d["ny"], d["nx"]), dtype=torch.float32, device="cuda")
     cont = lat.slice(z0=d["z0"], dz=d["dz"], n_layers=d["n_layers"], x0=d["x0"], y0=d["y0"],
                      nx=d["nx"], ny=d["ny"], pixel=d["pixel"], sigma_out=sig, edge_ids=True,
-                     slab=slab, field_kernel="block", tile=16)
+                     slab=slab, field_kernel=kernel, tile=tile, stage_records=stage)
     torch.cuda.synchronize()
     return sig, cont
 
@@ -73,6 +74,25 @@ def test_batch_equals_per_job_slicing(job_set):
             assert torch.equal(b.sigma(j), ref[j][0]), j
             _same_contours(b.contours(j), ref[j][1])
         b.close()
+
+
+@pytest.mark.parametrize("tile,slab,stage", [(32, 8, 0), (16, 4, 128), (32, 2, 512)])
+def test_footprint_batch_equals_per_job_slicing(job_set, tile, slab, stage):
+    """The persistent footprint kernel over the batch's queue: the same sums
+    as per-job slicing with the footprint kernel on the same tiles."""
+    import paper_2101_05031_gb300 as cs
+    jobs, _ = job_set
+    ref = [_per_job(lat, d, slab, "footprint", tile, stage) for lat, d in jobs]
+    b = cs.Batch(jobs, slab=slab, ctas_per_sm=2, branches=3, field_kernel="footprint",
+                 tile=tile, stage_records=stage)
+    b.run()
+    info = b.info()
+    assert (info.field_kernel, info.tile, info.slab) == (2, tile, slab)
+    assert info.stage_records == (stage or 256)
+    for j in range(len(jobs)):
+        assert torch.equal(b.sigma(j), ref[j][0]), j
+        _same_contours(b.contours(j), ref[j][1])
+    b.close()
 
 
 def test_batch_against_oracle(job_set):
@@ -112,24 +132,39 @@ def test_replay_is_stable(job_set):
 
 
 def test_autotune_and_cache(job_set):
+    """The staged search times the block kernel on 16-pixel tiles and the
+    footprint kernel on 16- and 32-pixel tiles, then slab depth x CTAs per SM
+    for the best, then (footprint) the staging chunk; the choice is the
+    fastest candidate, is cached, and gives per-job slicing's results."""
     import paper_2101_05031_gb300 as cs
     jobs, _ = job_set
     b = cs.Batch(jobs[:3], autotune=True)
     info = b.info()
-    ref = [_per_job(lat, d, info.slab) for lat, d in jobs[:3]]
-    assert info.n_candidates == 9 and info.from_cache == 0
-    assert info.slab in (2, 4, 8) and info.ctas_per_sm in (2, 4, 6)
-    ms = list(info.cand_ms)[:9]
+    n = info.n_candidates
+    kname = {1: "block", 2: "footprint"}
+    ref = [_per_job(lat, d, info.slab, kname[info.field_kernel], info.tile, info.stage_records)
+           for lat, d in jobs[:3]]
+    assert 8 <= n <= 16 and info.from_cache == 0
+    shapes = {(int(info.cand_kernel[i]), int(info.cand_tile[i])) for i in range(n)}
+    assert shapes >= {(1, 16), (2, 16), (2, 32)}
+    assert len({int(info.cand_slab[i]) for i in range(n)}) >= 2
+    if info.field_kernel == 2:
+        assert {int(info.cand_stage[i]) for i in range(n)} == {128, 256, 512}
+    ms = list(info.cand_ms)[:n]
     assert all(m > 0 for m in ms)
     best = int(np.argmin(ms))
-    assert (info.cand_slab[best], info.cand_ctas[best]) == (info.slab, info.ctas_per_sm)
+    assert (info.cand_slab[best], info.cand_ctas[best], info.cand_kernel[best],
+            info.cand_tile[best], info.cand_stage[best]) == \
+        (info.slab, info.ctas_per_sm, info.field_kernel, info.tile, info.stage_records)
     b.run()
     for j in range(3):
         assert torch.equal(b.sigma(j), ref[j][0])
         _same_contours(b.contours(j), ref[j][1])
     b2 = cs.Batch(jobs[:3], autotune=True)
     i2 = b2.info()
-    assert i2.from_cache == 1 and (i2.slab, i2.ctas_per_sm) == (info.slab, info.ctas_per_sm)
+    assert i2.from_cache == 1
+    assert (i2.slab, i2.ctas_per_sm, i2.field_kernel, i2.tile, i2.stage_records) == \
+        (info.slab, info.ctas_per_sm, info.field_kernel, info.tile, info.stage_records)
 
 
 def test_changed_sizes_are_reported_and_recoverable():
