@@ -902,7 +902,23 @@ def main():
                      "radii and the prepared arrays when resident); the workspace peak from "
                      "csl_last_stats"}
         del lat_h
+        # the same slice, contours to host memory, within a device-memory
+        # budget of 8 GB besides the lattice (chunks sized by the library)
+        budget = 8 << 30
+        lat.slice(**kw, workspace_budget=budget)
+        bst = cs.last_stats()
+        b_ms = _event_ms(lambda: lat.slice(**kw, workspace_budget=budget), 1, 0, stream)
+        line["memory_budget"] = {
+            "workload": cfg["name"], "budget_bytes": budget, "ms_per_step": b_ms,
+            "pixel_evals_per_s": px / (b_ms / 1e3), "chunks": int(bst.chunks),
+            "slice_workspace_peak_bytes": int(bst.device_bytes_peak),
+            "unbounded_workspace_peak_bytes": int(line.get("e2e", {}).get(
+                "slice_workspace_peak_bytes", 0)),
+            "basis": "csl_slice_layers with workspace_budget, contours copied to host memory "
+                     "chunk by chunk (pageable), one step timed with CUDA events; the "
+                     "unbounded figure is the end-to-end line's"}
         del lat
+        torch.cuda.empty_cache()
         line["at_10M"] = run_10m(args.steps, args.warmup)
         line["volume_fraction"] = run_vf(args.steps, args.warmup)
         line["batched_64"] = run_batch(args.steps, args.warmup)

@@ -177,6 +177,14 @@ typedef struct csl_slice_desc {
                                  image of each layer (Sec. 4, the DLP mask): bit i % 32 of word
                                  [k][j][i / 32] is set when pixel (i, j) of layer k is inside
                                  (Sigma >= C); bits past nx are 0 */
+    int64_t workspace_budget; /* 0: no limit. Else the bytes of device memory the call may hold
+                                 besides the lattice (the paper slices in bounded memory, Sec. 4,
+                                 6): one chunk in flight, a first chunk of two slabs measures the
+                                 workspace per layer, the next chunks are sized to fit, and each
+                                 chunk's contours go to the host as soon as they are done. Host
+                                 contours only (not with CSL_SLICE_CONTOURS_ON_DEVICE), a
+                                 device-resident lattice, no chunk_layers; the same results as
+                                 without a budget. CAPACITY when one slab does not fit */
 } csl_slice_desc;
 
 /*

@@ -44,7 +44,7 @@ class SliceDesc(ctypes.Structure):
                 ("flags", c_i32), ("x0", c_f64), ("y0", c_f64), ("pixel", c_f64),
                 ("sigma_out", c_vp), ("tile", c_i32), ("slab", c_i32), ("chunk_layers", c_i32),
                 ("field_kernel", ctypes.c_int16), ("stage_records", ctypes.c_int16),
-                ("mask_out", c_vp)]
+                ("mask_out", c_vp), ("workspace_budget", c_i64)]
 
 
 class Contours(ctypes.Structure):

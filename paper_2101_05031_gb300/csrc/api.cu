@@ -423,7 +423,18 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         cudaStream_t s = (cudaStream_t)stream;
         SlicePlan p = make_plan(L, d);
         p.fused = wants_fused(d, p);
+        // a workspace budget: one chunk in flight, chunks sized from a first
+        // chunk's measured workspace, contours to the host chunk by chunk
+        const bool budgeted = d.workspace_budget > 0;
+        if (budgeted) {
+            require_arg(!(d.flags & CSL_SLICE_CONTOURS_ON_DEVICE),
+                        "workspace_budget needs host contours");
+            require_arg(!L->host_resident, "workspace_budget needs a device-resident lattice");
+            require_arg(d.chunk_layers == 0, "workspace_budget sizes the chunks itself");
+            require_arg(!(d.flags & CSL_SLICE_TIME_KERNELS), "workspace_budget: no stage timing");
+        }
         device_bytes_peak_and_reset();
+        const int64_t live_at_start = device_bytes_live();
         launches_and_reset();
         csl_stats st = {};
         st.field_kernel = p.kernel == kFieldFootprint ? CSL_FIELD_FOOTPRINT : CSL_FIELD_BLOCK;
@@ -459,18 +470,21 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 cudaEventDestroy(ev0);
                 cudaEventDestroy(ev1);
             }
-            st.device_bytes_peak = device_bytes_peak_and_reset();
+            st.device_bytes_peak = device_bytes_peak_and_reset() - live_at_start;
             st.kernel_launches = launches_and_reset();
             t_stats = st;
         };
 
         const int64_t plane = (int64_t)d.nx * d.ny;
-        const int n_chunks = d.n_layers > 0 ? (int)ceil_div(d.n_layers, p.chunk) : 0;
+        // with a budget the first chunk is two slabs (a measurement), the
+        // others as many whole slabs as fit
+        const int chunk0 = budgeted ? std::min(p.chunk, 2 * p.S) : p.chunk;
+        const int n_chunks = d.n_layers > 0 ? (int)ceil_div(d.n_layers, chunk0) : 0;
         // Two chunks in flight (not when timing the stages): chunk k runs on
         // streams[k % 2] with its own Sigma and mask buffers, so that while the
         // host waits for a size read back by one chunk's binner or contour
         // stage, the other chunk's kernels keep the GPU busy.
-        const int n_par = (n_chunks > 1 && !time_kernels) ? 2 : 1;
+        const int n_par = (n_chunks > 1 && !time_kernels && !budgeted) ? 2 : 1;
         struct Side {
             cudaStream_t s2 = nullptr;
             cudaEvent_t fork = nullptr;
@@ -490,29 +504,37 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         }
         DevBuf sigma_ws[2], mask_ws[2];
         FusedVerts fv_ws[2];
-        const int chunk_alloc = std::min(p.chunk, std::max(d.n_layers, 1));
+        int chunk_alloc = std::min(chunk0, std::max(d.n_layers, 1));
         const int64_t mask_layer = mask_words_per_layer(d.nx, d.ny);
         const int64_t n_tiles = (int64_t)p.ntx * p.nty;
-        for (int b = 0; b < n_par; ++b) {
-            // without contours nothing reads the Sigma plane: the field kernel
-            // then writes only the mask (the binary image) unless sigma_out is
-            // set; the fused pass leaves vertex lists instead of a plane
-            if (!d.sigma_out && want_contours && !p.fused && d.n_layers > 0)
-                sigma_ws[b].alloc((size_t)chunk_alloc * plane * 4, streams[b]);
-            if ((want_contours || d.mask_out) && d.n_layers > 0)
-                mask_ws[b].alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
-            if (p.fused && d.n_layers > 0) {
-                FusedVerts& f = fv_ws[b];
-                f.tbase.alloc((size_t)chunk_alloc * n_tiles * 4, streams[b]);
-                f.roff.alloc((size_t)chunk_alloc * n_tiles * (p.T + 1) * 2, streams[b]);
-                f.saddle.alloc((size_t)chunk_alloc * mask_layer * 4, streams[b]);
-                f.counter.alloc(8, streams[b]);
-                // first guess: a crossing per 4 pixel-layers (grown on overflow)
-                f.cap = std::max<int64_t>((int64_t)1 << 20, (int64_t)chunk_alloc * plane / 4);
-                f.cap = std::min<int64_t>(f.cap, 0xffffffffLL);
-                f.verts.alloc((size_t)f.cap * 8, streams[b]);
+        // the per-chunk buffers for chunks of up to `layers` layers (grown in place)
+        auto chunk_buffers = [&](int layers) {
+            chunk_alloc = layers;
+            for (int b = 0; b < n_par; ++b) {
+                // without contours nothing reads the Sigma plane: the field kernel
+                // then writes only the mask (the binary image) unless sigma_out is
+                // set; the fused pass leaves vertex lists instead of a plane
+                if (!d.sigma_out && want_contours && !p.fused && d.n_layers > 0)
+                    sigma_ws[b].ensure((size_t)layers * plane * 4, streams[b]);
+                if ((want_contours || d.mask_out) && d.n_layers > 0)
+                    mask_ws[b].ensure((size_t)layers * mask_layer * 4, streams[b]);
+                if (p.fused && d.n_layers > 0) {
+                    FusedVerts& f = fv_ws[b];
+                    f.tbase.ensure((size_t)layers * n_tiles * 4, streams[b]);
+                    f.roff.ensure((size_t)layers * n_tiles * (p.T + 1) * 2, streams[b]);
+                    f.saddle.ensure((size_t)layers * mask_layer * 4, streams[b]);
+                    f.counter.ensure(8, streams[b]);
+                    // first guess: a crossing per 4 pixel-layers (grown on overflow)
+                    int64_t cap = std::max<int64_t>((int64_t)1 << 20, (int64_t)layers * plane / 4);
+                    cap = std::min<int64_t>(cap, 0xffffffffLL);
+                    if (cap > f.cap) {
+                        f.cap = cap;
+                        f.verts.ensure((size_t)f.cap * 8, streams[b]);
+                    }
+                }
             }
-        }
+        };
+        chunk_buffers(chunk_alloc);
 
         std::vector<ChunkContours> dev_chunks;
         // Host output: the vertices of each chunk are copied to the host while
@@ -533,7 +555,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 if (block) host_block_free(block);
             }
         } spec;
-        if (want_contours && !on_dev && d.n_layers > 0) {
+        if (want_contours && !on_dev && d.n_layers > 0 && !budgeted) {
             spec.block = host_block_take_largest(&spec.bytes);
             if (spec.block) {
                 spec.eid_off = vertex_block_eid_offset(spec.bytes, want_eid);
@@ -550,6 +572,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             const float* sigma = d.sigma_out ? d.sigma_out + (int64_t)g.first_layer * plane
                                              : sigma_ws[k % n_par].as<float>();   // null: fused
             ChunkContours cc;
+            cc.n_layers = g.n_layers;
             timed(st.contour_ms, [&] {
                 contours_chunk(g, L->C, sigma, mask_ws[k % n_par].as<uint32_t>(), want_eid, cc,
                                ks, nullptr, p.fused ? &fv_ws[k % n_par] : nullptr);
@@ -607,9 +630,38 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         }
         int prev = -1;
         ChunkGeom g_prev{};
-        for (int k = 0; k < n_chunks; ++k) {
-            const int first = k * p.chunk;
-            const int n = std::min(p.chunk, d.n_layers - first);
+        // a budget: chunks' contours copied to host memory as they finish
+        struct HostChunk {
+            int n = 0;
+            int64_t n_loops = 0, n_verts = 0;
+            std::vector<int64_t> layer_loops, loop_off;
+            std::vector<float> xy;
+            std::vector<int32_t> eid;
+        };
+        std::vector<HostChunk> host_chunks;
+        auto to_host = [&](cudaStream_t ks) {
+            ChunkContours& cc = dev_chunks.back();
+            HostChunk h;
+            h.n = cc.n_layers;
+            h.n_loops = cc.n_loops;
+            h.n_verts = cc.n_verts;
+            h.layer_loops.resize((size_t)h.n + 1);
+            h.loop_off.resize((size_t)h.n_loops + 1);
+            h.xy.resize((size_t)h.n_verts * 2);
+            read_to_host(h.layer_loops.data(), cc.layer_loops.get(), (h.n + 1) * 8, ks);
+            read_to_host(h.loop_off.data(), cc.loop_off.get(), (h.n_loops + 1) * 8, ks);
+            if (h.n_verts) read_to_host(h.xy.data(), cc.xy.get(), h.n_verts * 8, ks);
+            if (want_eid && h.n_verts) {
+                h.eid.resize((size_t)h.n_verts);
+                read_to_host(h.eid.data(), cc.eid.get(), h.n_verts * 4, ks);
+            }
+            host_chunks.push_back(std::move(h));
+            dev_chunks.pop_back();   // the device copies are freed here
+        };
+        int cur_chunk = chunk0;
+        int first = 0;
+        for (int k = 0; first < d.n_layers; ++k) {
+            const int n = std::min(cur_chunk, d.n_layers - first);
             ChunkGeom g = chunk_geom(L, d, p, first, n);
             cudaStream_t ks = streams[k % n_par];
             csl_lattice view;              // the window of a host-resident lattice
@@ -696,8 +748,30 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
                 }
             }
             ++st.chunks;
+            first += n;
             if (n_par == 1) {   // one set of buffers: this chunk's contours now
                 if (want_contours) contour_stage(k, g);
+                if (budgeted) {
+                    if (want_contours) to_host(ks);
+                    if (k == 0 && first < d.n_layers) {
+                        // the first chunk's workspace per layer sizes the others
+                        CSL_CUDA(cudaStreamSynchronize(ks));
+                        const int64_t w0 = device_bytes_peak() - live_at_start;
+                        if (w0 > d.workspace_budget)
+                            fail(CSL_ERR_CAPACITY,
+                                 "workspace_budget: a chunk of " + std::to_string(n) +
+                                     " layers needs " + std::to_string(w0) + " bytes");
+                        const double per_layer = (double)w0 / n;
+                        int c = (int)std::min<double>(0.9 * (double)d.workspace_budget / per_layer,
+                                                      1e9);
+                        // marching squares needs < 2^27 edge words per chunk
+                        const int64_t cap = (((int64_t)1 << 27) - 1) / (2 * mask_layer);
+                        c = (int)std::min<int64_t>(c, cap);
+                        c -= c % p.S;
+                        cur_chunk = std::max(c, p.S);
+                        if (cur_chunk > chunk_alloc) chunk_buffers(cur_chunk);
+                    }
+                }
                 continue;
             }
             // the previous chunk's contours, while this chunk's field runs
@@ -720,6 +794,28 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             return;
         }
 
+        if (budgeted) {   // assemble the host chunks
+            int64_t n_loops = 0, n_verts = 0;
+            for (auto& h : host_chunks) { n_loops += h.n_loops; n_verts += h.n_verts; }
+            csl_contours* c = new_host_contours(d.n_layers, n_loops, n_verts, want_eid);
+            int64_t lb = 0, vb = 0;
+            int layer = 0;
+            c->layer_loop_off[0] = 0;
+            c->loop_vert_off[0] = 0;
+            for (auto& h : host_chunks) {
+                for (int i = 1; i <= h.n; ++i) c->layer_loop_off[layer + i] = h.layer_loops[i] + lb;
+                for (int64_t i = 1; i <= h.n_loops; ++i) c->loop_vert_off[lb + i] = h.loop_off[i] + vb;
+                if (h.n_verts) memcpy(c->xy + 2 * vb, h.xy.data(), (size_t)h.n_verts * 8);
+                if (want_eid && h.n_verts)
+                    memcpy(c->edge_id + vb, h.eid.data(), (size_t)h.n_verts * 4);
+                lb += h.n_loops;
+                vb += h.n_verts;
+                layer += h.n;
+            }
+            finish_stats();
+            *out = c;
+            return;
+        }
         // Gather the chunks into the result: offsets are rebased on the device,
         // then every array is copied straight to its place (device or host).
         int64_t n_loops = 0, n_verts = 0;
@@ -754,7 +850,7 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             int64_t lb = 0, vb = 0;
             int layer = 0;
             for (auto& cc : dev_chunks) {
-                const int n = std::min(p.chunk, d.n_layers - layer);
+                const int n = cc.n_layers;
                 if (lb) {
                     k_add_i64<<<grid_for(n + 1, 256), 256, 0, s>>>(cc.layer_loops.as<int64_t>(),
                                                                    n + 1, lb);

@@ -71,6 +71,8 @@ class DevBuf {
 // Workspace accounting for csl_last_stats.
 void note_device_bytes(int64_t delta);
 int64_t device_bytes_peak_and_reset();
+int64_t device_bytes_live();   // bytes held now
+int64_t device_bytes_peak();   // the peak since the last reset
 
 void set_last_error(const std::string& m);
 const char* last_error_cstr();

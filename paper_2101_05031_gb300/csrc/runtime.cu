@@ -57,6 +57,9 @@ int64_t device_bytes_peak_and_reset() {
     return p;
 }
 
+int64_t device_bytes_live() { return g_live.load(); }
+int64_t device_bytes_peak() { return g_peak.load(); }
+
 [[noreturn]] static void alloc_error(cudaError_t e, size_t bytes) {
     cudaGetLastError();
     std::string m = "device allocation of " + std::to_string(bytes) + " bytes failed: " +

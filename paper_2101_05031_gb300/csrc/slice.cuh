@@ -136,6 +136,7 @@ void field_batch_run(FieldBatch& fb, int n_ctas, cudaStream_t s);
 // Contours of the chunk's layers (device arrays, layer-local edge ids).
 struct ChunkContours {
     int64_t n_verts = 0, n_loops = 0;
+    int32_t n_layers = 0;   // layers of the chunk (set by the slicing driver)
     DevBuf layer_loops;   // int64 [n_layers + 1] loop offsets per layer (chunk-local)
     DevBuf loop_off;      // int64 [n_loops + 1] vertex offsets (chunk-local)
     DevBuf xy;            // float2 [n_verts]

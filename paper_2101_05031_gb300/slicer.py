@@ -259,7 +259,7 @@ class Lattice:
     def slice(self, *, z0, dz, n_layers, x0, y0, nx, ny, pixel, sigma_out=None, mask_out=None,
               contours=True, on_device=False, edge_ids=False, slab=0, chunk_layers=0,
               time_kernels=False, count_pairs=False, stream=None, tile=0, field_kernel="auto",
-              stage_records=0, fused=False):
+              stage_records=0, fused=False, workspace_budget=0):
         """csl_slice_layers. sigma_out: optional CUDA float32 tensor
         [n_layers, ny, nx] that receives Sigma; mask_out: optional CUDA int32
         tensor [n_layers, ny, ceil(nx / 32)] that receives the bit-packed inside
@@ -268,7 +268,8 @@ class Lattice:
         per staged copy of the footprint kernel (0: 256); fused: with the
         footprint kernel, the fused field and contour pass (no Sigma plane; the
         same contours as the default, which writes a Sigma plane and runs
-        marching squares on it). Returns a ContourSet
+        marching squares on it); workspace_budget: bytes of device memory the
+        call may hold besides the lattice (0: no limit; host contours). Returns a ContourSet
         (host), a DeviceContours (on_device=True) or None (contours=False)."""
         if sigma_out is not None:
             if not (sigma_out.is_cuda and sigma_out.dtype == torch.float32
@@ -297,6 +298,7 @@ class Lattice:
             flags |= _lib.SLICE_FUSED
         d = self._desc(z0, dz, n_layers, x0, y0, nx, ny, pixel, flags, sigma_out, slab,
                        chunk_layers, mask_out, tile, field_kernel, stage_records)
+        d.workspace_budget = int(workspace_budget)
         out = ctypes.POINTER(_lib.Contours)()
         _lib.check(_lib.load().csl_slice_layers(self._h, ctypes.byref(d), _stream_ptr(stream),
                                                 ctypes.byref(out)))

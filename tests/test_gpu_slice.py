@@ -353,3 +353,31 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable(c1):
         assert b"gave up" in lib.csl_last_error()
     after, _ = gpu_slice(lat, cfg, n_layers=3)
     assert np.array_equal(before, after)
+
+
+def test_workspace_budget_bounds_memory_and_keeps_results():
+    """A device-memory budget: one chunk in flight, a first chunk of two slabs
+    measures the workspace per layer, the others are sized to fit. Contours
+    identical to the unbounded call; the workspace peak within the budget; a
+    budget that one slab cannot meet is refused."""
+    import paper_2101_05031_gb300 as cs
+    cfg = synth.config(2, small=True)
+    lat = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"])
+    kw = dict(z0=cfg["z0"], dz=0.05, n_layers=40, x0=cfg["x0"], y0=cfg["y0"], nx=cfg["nx"],
+              ny=cfg["ny"], pixel=cfg["pixel"], edge_ids=True, slab=2)
+    ref = lat.slice(**kw)
+    full = cs.last_stats()
+    assert full.chunks == 1
+    budget = full.device_bytes_peak // 3
+    got = lat.slice(**kw, workspace_budget=budget)
+    st = cs.last_stats()
+    assert st.chunks >= 3
+    assert 0 < st.device_bytes_peak <= budget
+    for a, b in ((ref.layer_loop_off, got.layer_loop_off), (ref.loop_vert_off, got.loop_vert_off),
+                 (ref.edge_id, got.edge_id)):
+        assert np.array_equal(a, b)
+    assert np.array_equal(ref.xy.view(np.uint32), got.xy.view(np.uint32))
+    with pytest.raises(cs.CslError, match="CAPACITY"):
+        lat.slice(**kw, workspace_budget=4096)
+    with pytest.raises(cs.CslError, match="INVALID_ARG"):
+        lat.slice(**kw, workspace_budget=budget, on_device=True)
