@@ -240,6 +240,8 @@ def radius_tuning(lat, cfg, iterations=20):
     loss.backward()
     g90 = float(torch.quantile(rw.grad.detach().abs()[::16].float(), 0.9))
     lr = 0.01 / max(g90, 1e-12)
+    with torch.no_grad():   # the update's kernels too (their first use loads a module)
+        (r0 - lr * rw.grad).clamp(0.1, 0.9 * R)
     r = r0.clone()
     losses = []
     stream = torch.cuda.current_stream()
@@ -321,9 +323,12 @@ def run_10m(steps, warmup):
         lat.slice(**kw, on_device=True).free()
 
     ms = _event_ms(step, steps, warmup, torch.cuda.current_stream())
+    st = cs.last_stats()
     return {"workload": cfg["name"], "struts": int(cfg["edges"].shape[0]),
             "pixel_evals_per_s": cfg["nx"] * cfg["ny"] * cfg["n_layers"] / (ms / 1e3),
-            "layers_per_s": cfg["n_layers"] / (ms / 1e3), "ms_per_step": ms}
+            "layers_per_s": cfg["n_layers"] / (ms / 1e3), "ms_per_step": ms,
+            "contours_per_step": {"loops": int(st.loops), "vertices": int(st.crossings)},
+            "chunks": int(st.chunks)}
 
 
 def run_batch(steps, warmup):
@@ -785,7 +790,7 @@ def main():
             "phase_ms_per_step": {"bin": bin_ms, "field": field_ms, "contours": contour_ms,
                                   "gather": output_ms, "sum": staged_ms,
                                   "basis": "one extra step with the stages run one after "
-                                           "another; the timed steps overlap two chunks"},
+                                           "another"},
             "setup_s": {"generate": t_gen, "upload_and_sort": t_up}}
 
     line["slice_workspace_peak_bytes"] = int(peak_main)
@@ -817,13 +822,19 @@ def main():
 
         e2e_peak = [0]
 
+        phase_wall = []
+
         def e2e_step():
+            t0 = time.perf_counter()
             L2 = cs.Lattice(pn, pe, pr, R=cfg["R"], C=cfg["C"])
+            t1 = time.perf_counter()
             cont = L2.slice(**kw)
+            t2 = time.perf_counter()
             e2e_peak[0] = cs.last_stats().device_bytes_peak
             nbytes = cont.layer_loop_off.nbytes + cont.loop_vert_off.nbytes + cont.xy.nbytes
             L2.close()
             del cont
+            phase_wall.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, (time.perf_counter() - t2) * 1e3))
             return nbytes
 
         e2e_step()   # untimed: the library's page-locked result blocks are allocated here
@@ -845,6 +856,8 @@ def main():
                        "unit": "pixel-evals/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": e2e_ms, "wall_ms_each_step": wall,
+                       "wall_ms_upload_slice_release": [
+                           [round(x, 1) for x in ph] for ph in phase_wall[1:]],
                        "slice_workspace_peak_bytes": int(e2e_peak[0])}
 
     if world == 1 and not args.no_extra:

@@ -138,9 +138,13 @@ __device__ __forceinline__ float2 fused_vertex(const FusedIn& F, const Dense& D,
 // values its vertices and saddles need (pixel rows J0 - 1 .. J0 + kEmitRows - 1,
 // columns 32 k0 - 1 .. 32 (k0 + kEmitWords) - 1) are staged into shared memory
 // first with coalesced loads, so that every Sigma row is read from DRAM about
-// once instead of as scattered words at each crossing.
+// once instead of as scattered words at each crossing. A staged row has a
+// pitch of kEmitPitch floats: pixel 32 k0 + c sits at column 4 + c (16-byte
+// aligned, so a thread moves 4 pixels with one vector load and store), pixel
+// 32 k0 - 1 at column 3.
 constexpr int kEmitRows = 8, kEmitWords = 32;
-constexpr int kEmitCols = 32 * kEmitWords + 1;
+constexpr int kEmitPitch = 32 * kEmitWords + 4;
+static_assert(32 * kEmitWords == 4 * 256, "one 4-pixel vector per thread and row");
 
 // grid: x over (band of kEmitRows rows J <= ny, segment of kEmitWords mask
 // words), y = layer. FUSED: vertices and saddle decisions from the fused pass
@@ -149,7 +153,7 @@ template <bool FUSED>
 __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma, const uint32_t* __restrict__ mask,
                        MsConst c, Dense D, FusedIn F, Xing* __restrict__ rec, uint32_t n_cap,
                        uint32_t* flag) {
-    __shared__ float s_sig[FUSED ? 1 : (kEmitRows + 1) * kEmitCols];
+    __shared__ __align__(16) float s_sig[FUSED ? 4 : (kEmitRows + 1) * kEmitPitch];
     const int layer = blockIdx.y;
     const int n_segs = (c.mwr + kEmitWords - 1) / kEmitWords;
     const int band = blockIdx.x / n_segs, seg = blockIdx.x - band * n_segs;
@@ -157,19 +161,38 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
     const int J = J0 + (int)(threadIdx.x / kEmitWords), k = k0 + (int)(threadIdx.x % kEmitWords);
     const uint32_t* m = mask + (int64_t)layer * c.mask_wpl;
     const float* sg = FUSED ? nullptr : sigma + (int64_t)layer * c.nx * c.ny;
-    if (!FUSED) {   // pixel (i, j) -> s_sig[(j - (J0 - 1)) * kEmitCols + i - (32 k0 - 1)]
-        const int i0 = 32 * k0 - 1, j0 = J0 - 1;
-        for (int q = threadIdx.x; q < (kEmitRows + 1) * kEmitCols; q += blockDim.x) {
-            const int r = q / kEmitCols, col = q - r * kEmitCols;
-            const int i = i0 + col, j = j0 + r;
-            s_sig[q] = (i >= 0 && j >= 0 && i < c.nx && j < c.ny) ? sg[(int64_t)j * c.nx + i]
-                                                                   : 0.0f;
+    if (!FUSED) {   // pixel (i, j) -> s_sig[(j - (J0 - 1)) * kEmitPitch + 4 + i - 32 k0]
+        const int ib = 32 * k0 + 4 * (int)threadIdx.x;   // this thread's 4 pixels of each row
+        // whole vectors need 16-byte aligned rows (nx % 4 == 0) and 4 pixels inside
+        const bool vec = (c.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(sg) & 15) == 0 &&
+                         ib + 3 < c.nx;
+#pragma unroll
+        for (int r = 0; r < kEmitRows + 1; ++r) {
+            const int j = J0 - 1 + r;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (j >= 0 && j < c.ny) {
+                const float* row = sg + (int64_t)j * c.nx;
+                if (vec) {
+                    v = __ldg(reinterpret_cast<const float4*>(row + ib));
+                } else {
+                    if (ib < c.nx) v.x = row[ib];
+                    if (ib + 1 < c.nx) v.y = row[ib + 1];
+                    if (ib + 2 < c.nx) v.z = row[ib + 2];
+                    if (ib + 3 < c.nx) v.w = row[ib + 3];
+                }
+                if (threadIdx.x == 0)   // the pixel left of the band (column 3)
+                    s_sig[r * kEmitPitch + 3] = (k0 > 0 && 32 * k0 - 1 < c.nx) ? row[32 * k0 - 1]
+                                                                              : 0.0f;
+            } else if (threadIdx.x == 0) {
+                s_sig[r * kEmitPitch + 3] = 0.0f;
+            }
+            *reinterpret_cast<float4*>(&s_sig[r * kEmitPitch + 4 + 4 * threadIdx.x]) = v;
         }
         __syncthreads();
     }
     // Sigma at padded sample (I, J) of this block (0 outside the grid, like the ring)
     auto value_s = [&](int I, int J2) -> float {
-        return s_sig[(J2 - J0) * kEmitCols + (I - 32 * k0)];
+        return s_sig[(J2 - J0) * kEmitPitch + (I - 32 * k0) + 3];
     };
     if (J > c.ny || k >= c.mwr) return;
     const bool last = k + 1 >= c.mwr;
@@ -282,22 +305,6 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
     }
 }
 
-// pred[succ[i]] = i (thread i writes next to its neighbours' targets: the
-// successors of consecutive crossings are close). A successor out of range is
-// reported through *status and nothing is written. (Writing these links in
-// the emit kernel beside the successors made the contour stage slower: the
-// emit kernel is bound by its dependent loads, and the scattered stores
-// lengthened it more than this streaming pass costs.)
-__global__ void k_pred(const Xing* __restrict__ rec, int64_t n, uint32_t* __restrict__ pred,
-                       uint32_t* status) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s = rec[i].succ;
-        if ((int64_t)s < n) pred[s] = (uint32_t)i;
-        else atomicOr(status, ST_CAPACITY);
-    }
-}
-
 // Splitters cut every loop into short segments: every local minimum
 // (pred > id < succ; the loop's smallest id is one) and a hashed 1-in-32
 // sample, so that a smooth loop with a single local minimum is cut too.
@@ -305,18 +312,27 @@ __device__ __forceinline__ bool is_splitter(uint32_t i, uint32_t pred_i, uint32_
     return (pred_i > i && succ_i > i) || ((i * 2654435761u) >> 27) == 0u;
 }
 
-// flag[i] = 1 for splitters; nxt[i] = successor | (splitter << 31), the only
-// array the segment walks read.
-__global__ void k_split_flags(const Xing* __restrict__ rec, const uint32_t* __restrict__ pred,
-                              int64_t n, uint32_t* __restrict__ flag,
-                              uint32_t* __restrict__ nxt) {
+// For the successor s of every crossing i (i is s's predecessor): flag[s] = 1
+// when s is a splitter, nxt[s] = succ(s) | (splitter << 31), the only array
+// the segment walks read. Thread i reads its own successor and its
+// successor's (records of one contour lie close together), so no separate
+// predecessor array is built. A successor out of range is reported through
+// *status and nothing is written for it; a crossing that is nobody's
+// successor keeps flag 0 (its loop then fails the coverage check).
+__global__ void k_split_flags(const Xing* __restrict__ rec, int64_t n,
+                              uint32_t* __restrict__ flag, uint32_t* __restrict__ nxt,
+                              uint32_t* status) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t q = (uint32_t)i;
+        const uint32_t q = rec[i].succ;
+        if ((int64_t)q >= n) {
+            atomicOr(status, ST_CAPACITY);
+            continue;
+        }
         const uint32_t sc = rec[q].succ;
-        const bool sp = is_splitter(q, pred[q], sc);
-        flag[i] = sp ? 1u : 0u;
-        nxt[i] = (sc & 0x7fffffffu) | (sp ? 0x80000000u : 0u);
+        const bool sp = is_splitter(q, (uint32_t)i, sc);
+        flag[q] = sp ? 1u : 0u;
+        nxt[q] = (sc & 0x7fffffffu) | (sp ? 0x80000000u : 0u);
     }
 }
 
@@ -753,14 +769,12 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         CSL_LAUNCH_CHECK("ms emit");
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
-    DevBuf pred((size_t)n_cross * 4, s), sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
+    DevBuf sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
     DevBuf nxt((size_t)n_cross * 4, s);
-    CSL_CUDA(cudaMemsetAsync(pred.get(), 0xff, (size_t)n_cross * 4, s));
+    CSL_CUDA(cudaMemsetAsync(sflag.get(), 0, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
-    k_pred<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, pred.as<uint32_t>(), status);
-    CSL_LAUNCH_CHECK("ms pred");
-    k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), pred.as<uint32_t>(), n_cross,
-                                     sflag.as<uint32_t>(), nxt.as<uint32_t>());
+    k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, sflag.as<uint32_t>(),
+                                     nxt.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms splitter flags");
     exclusive_scan_u32(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, status + 2, s);
     int64_t ns;
@@ -775,7 +789,6 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         ns = head2[2];
         if (rp) rp->plan->ns = ns;
     }
-    pred.release();
     DevBuf split_id((size_t)ns * 4, s), seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
     // a replay whose sizes changed leaves entries unwritten: make them valid ids
     if (replay) CSL_CUDA(cudaMemsetAsync(split_id.get(), 0, (size_t)ns * 4, s));

@@ -93,8 +93,12 @@ __global__ void k_sp_keep(const int64_t* __restrict__ loop_off, const int32_t* _
                 const int64_t v = a + q, p = a + q - 1, s = a + (q + 1) % n;
                 const int64_t ev = eid[v], ep = eid[p], es = eid[s];
                 // the two cells beside edge ev
-                const int64_t base = ev >> 1;
-                const int J = (int)(base / g.W), I = (int)(base % g.W);
+                // a valid ev is below 2 W H < 2^31: a 32-bit division (an
+                // invalid one is reported by k_sp_mark; the cell lookups below
+                // bound-check whatever I, J it gives)
+                const uint32_t base = (uint32_t)ev >> 1;
+                const int J = (int)(base / (uint32_t)g.W),
+                          I = (int)(base - (uint32_t)J * (uint32_t)g.W);
                 int I0, J0;
                 if (ev & 1) {
                     I0 = I - 1;

@@ -63,8 +63,10 @@ __global__ void k_sm_step(const int64_t* __restrict__ loop_off, const int32_t* _
             const int64_t p = v == a ? b - 1 : v - 1;
             const int64_t s = v == b - 1 ? a : v + 1;
             const float2 Pp = src[p], Ps = src[s];
-            const int64_t base = e >> 1;
-            const int J = (int)(base / g.W), I = (int)(base % g.W);
+            // e < 2 W H < 2^31: 32-bit division (a 64-bit one is a long
+            // emulated sequence per vertex)
+            const uint32_t base = (uint32_t)e >> 1;
+            const int J = (int)(base / (uint32_t)g.W), I = (int)(base - (uint32_t)J * (uint32_t)g.W);
             if (e & 1) {   // vertical edge: y moves
                 const double lo = g.y0 + ((double)J - 0.5) * g.px;
                 const double av = (double)P.y;
