@@ -30,7 +30,10 @@
  * (a cudaStream_t passed as void*; NULL = legacy default stream). Calls that
  * return host data synchronise that stream before returning.
  * Memory: the library allocates its own device memory with the stream-ordered
- * allocator (cudaMallocAsync) on that stream and frees it the same way.
+ * allocator (cudaMallocAsync) on that stream and frees it the same way; what
+ * outlives the call (a lattice, a batch) comes from the same pool on the
+ * legacy default stream, synchronised, and is freed after a device
+ * synchronisation. Freed memory stays in the pool for later calls.
  */
 #ifndef CSLICE_H
 #define CSLICE_H

@@ -50,7 +50,9 @@ class DevBuf {
     // stream-ordered (cudaMallocAsync / cudaFreeAsync on the same stream)
     void alloc(size_t bytes, cudaStream_t s);
     void ensure(size_t bytes, cudaStream_t s) { if (bytes > n_) alloc(bytes, s); }
-    // outlives any stream (cudaMalloc / cudaFree): for objects handed to the caller
+    // outlives any stream (from the same pool, allocated on the legacy stream and
+    // synchronised; freed after a device synchronisation): for objects handed
+    // to the caller
     void alloc_persistent(size_t bytes);
     void ensure_persistent(size_t bytes) { if (bytes > n_) alloc_persistent(bytes); }
     void release();

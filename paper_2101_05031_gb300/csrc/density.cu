@@ -6,8 +6,9 @@
 // its density at n^3 samples with the doubled radius (rho*) and the bisection
 // of its radius ratio, the smallest ratio per edge, the voxel-edge pairs (count,
 // scan, emit, radix sort by voxel), the per-voxel bisection of a common ratio
-// and the per-edge minimum. Host work: the topology of the subdivision (new
-// midpoints, halves, children, edge lookup), between levels.
+// and the per-edge minimum. The topology of the subdivision (new midpoints,
+// halves, children, edge numbering) is kept on the device too
+// (density_mesh.cu); the host validates the input and copies the result out.
 //
 // A density depends on the radius only through the weight, so each block
 // first sums the unit-weight segment integrals J(p) of the struts being tuned
@@ -20,11 +21,11 @@
 #include <string.h>
 
 #include <algorithm>
-#include <array>
 #include <chrono>
 #include <vector>
 
 #include "common.cuh"
+#include "density_mesh.cuh"
 #include "field_tile.cuh"
 
 namespace csl {
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int kDmThreads = 256;
 constexpr int kDmMaxSamples = 16 * 16 * 16;
-constexpr int kLocalEdges[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 
 struct DmConst {
     double r0, R, C;   // base radius, support, iso-value
@@ -277,14 +277,18 @@ k_dm_tet(const float4* __restrict__ tv, const double* __restrict__ target, int64
     }
 }
 
-// Step 3's rule per (leaf tetrahedron, final edge) pair: the smallest ratio.
-// Positive floats order as their bit patterns.
-__global__ void k_dm_edge_min(const int32_t* __restrict__ pair_tet,
-                              const int32_t* __restrict__ pair_seg, int64_t n,
-                              const float* __restrict__ tet_ratio, uint32_t* ratio_bits) {
+// Step 2's decision: a tetrahedron whose rho* stays below its target splits.
+__global__ void k_dm_split(const float* __restrict__ rho, const double* __restrict__ target,
+                           int64_t n, uint32_t* __restrict__ split) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        atomicMin(ratio_bits + pair_seg[i], __float_as_uint(tet_ratio[pair_tet[i]]));
+        split[i] = (double)rho[i] < target[i] ? 1u : 0u;
+}
+
+__global__ void k_dm_fill_u32(uint32_t* __restrict__ a, int64_t n, uint32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
 }
 
 // An edge in no leaf tetrahedron (none in a consistent mesh) keeps ratio 1.
@@ -484,159 +488,6 @@ __global__ void k_dm_radii(const float* __restrict__ ratio, int64_t n, float r0,
         radius[i] = r0 * ratio[i];
 }
 
-// ---- host: the tetrahedral lattice and its subdivision --------------------
-
-// Edge key (smaller node id << 32 | larger) -> edge id, open addressing with
-// linear probing (node ids < 2^30, so no key equals the empty marker).
-class EdgeMap {
-  public:
-    void reserve(size_t n) {
-        size_t cap = 64;
-        while (cap < 2 * n) cap <<= 1;
-        if (cap > keys_.size()) rehash(cap);
-    }
-    int32_t find(uint64_t k) const {
-        for (size_t i = slot(k);; i = (i + 1) & mask_) {
-            if (keys_[i] == k) return vals_[i];
-            if (keys_[i] == kEmpty) return -1;
-        }
-    }
-    void insert(uint64_t k, int32_t v) {   // k must be absent
-        if (2 * (n_ + 1) > keys_.size()) rehash(keys_.size() * 2);
-        size_t i = slot(k);
-        while (keys_[i] != kEmpty) i = (i + 1) & mask_;
-        keys_[i] = k;
-        vals_[i] = v;
-        ++n_;
-    }
-
-  private:
-    static constexpr uint64_t kEmpty = ~0ull;
-    size_t slot(uint64_t k) const {
-        k ^= k >> 33;   // a 64-bit finaliser mix before masking
-        k *= 0xff51afd7ed558ccdull;
-        k ^= k >> 33;
-        return (size_t)k & mask_;
-    }
-    void rehash(size_t cap) {
-        std::vector<uint64_t> ok;
-        std::vector<int32_t> ov;
-        ok.swap(keys_);
-        ov.swap(vals_);
-        keys_.assign(cap, kEmpty);
-        vals_.assign(cap, -1);
-        mask_ = cap - 1;
-        n_ = 0;
-        for (size_t i = 0; i < ok.size(); ++i)
-            if (ok[i] != kEmpty) insert(ok[i], ov[i]);
-    }
-    std::vector<uint64_t> keys_ = std::vector<uint64_t>(64, kEmpty);
-    std::vector<int32_t> vals_ = std::vector<int32_t>(64, -1);
-    size_t mask_ = 63, n_ = 0;
-};
-
-struct TetLattice {
-    std::vector<float> xyz;                 // 3 per node
-    std::vector<int2> edges;                // (smaller, larger) node id
-    std::vector<int32_t> mid;               // midpoint node once split, else -1
-    std::vector<int2> halves;               // the two halves once split
-    EdgeMap ids;
-    std::vector<int4> tets;
-    std::vector<std::array<int32_t, 6>> tet_edges;
-    std::vector<int32_t> depth;
-    std::vector<uint8_t> leaf;
-
-    static uint64_t key(int32_t a, int32_t b) {
-        const uint32_t lo = (uint32_t)std::min(a, b), hi = (uint32_t)std::max(a, b);
-        return ((uint64_t)lo << 32) | hi;
-    }
-    int32_t add_edge(int32_t a, int32_t b) {
-        const uint64_t k = key(a, b);
-        const int32_t found = ids.find(k);
-        if (found >= 0) return found;
-        const int32_t e = (int32_t)edges.size();
-        edges.push_back(make_int2(std::min(a, b), std::max(a, b)));
-        mid.push_back(-1);
-        halves.push_back(make_int2(-1, -1));
-        ids.insert(k, e);
-        return e;
-    }
-    std::array<int32_t, 6> edges_of(const int4& t) {
-        const int32_t v[4] = {t.x, t.y, t.z, t.w};
-        std::array<int32_t, 6> r;
-        for (int e = 0; e < 6; ++e) r[e] = add_edge(v[kLocalEdges[e][0]], v[kLocalEdges[e][1]]);
-        return r;
-    }
-    void add_tet(const int4& t, int32_t d) {
-        tets.push_back(t);
-        tet_edges.push_back(edges_of(t));
-        depth.push_back(d);
-        leaf.push_back(1);
-    }
-    int32_t split(int32_t e) {
-        if (mid[e] >= 0) return mid[e];
-        const int2 ab = edges[e];
-        const int32_t m = (int32_t)(xyz.size() / 3);
-        for (int k = 0; k < 3; ++k)
-            xyz.push_back((float)(((double)xyz[3 * ab.x + k] + (double)xyz[3 * ab.y + k]) * 0.5));
-        mid[e] = m;
-        const int32_t h0 = add_edge(ab.x, m);
-        const int32_t h1 = add_edge(m, ab.y);
-        halves[e] = make_int2(h0, h1);
-        return m;
-    }
-    double len2(int32_t i, int32_t j) const {
-        const double dx = (double)xyz[3 * i] - (double)xyz[3 * j];
-        const double dy = (double)xyz[3 * i + 1] - (double)xyz[3 * j + 1];
-        const double dz = (double)xyz[3 * i + 2] - (double)xyz[3 * j + 2];
-        return dx * dx + dy * dy + dz * dz;
-    }
-    // 1:8 subdivision: four corner tetrahedra, then four around the inner
-    // octahedron's shortest diagonal (the first of the three on ties).
-    void subdivide(int32_t t, std::vector<int32_t>& kids) {
-        const int4 tv = tets[t];
-        const std::array<int32_t, 6> te = tet_edges[t];
-        int32_t m[6];
-        for (int e = 0; e < 6; ++e) m[e] = split(te[e]);
-        const int32_t m01 = m[0], m02 = m[1], m03 = m[2], m12 = m[3], m13 = m[4], m23 = m[5];
-        int4 ch[8] = {make_int4(tv.x, m01, m02, m03), make_int4(m01, tv.y, m12, m13),
-                      make_int4(m02, m12, tv.z, m23), make_int4(m03, m13, m23, tv.w)};
-        const int32_t diag[3][2] = {{m01, m23}, {m02, m13}, {m03, m12}};
-        const int32_t ring[3][4] = {{m02, m03, m13, m12}, {m01, m03, m23, m12}, {m01, m02, m23, m13}};
-        int best = 0;
-        double best_l2 = len2(diag[0][0], diag[0][1]);
-        for (int i = 1; i < 3; ++i) {
-            const double l2 = len2(diag[i][0], diag[i][1]);
-            if (l2 < best_l2) {
-                best = i;
-                best_l2 = l2;
-            }
-        }
-        for (int i = 0; i < 4; ++i)
-            ch[4 + i] = make_int4(diag[best][0], diag[best][1], ring[best][i], ring[best][(i + 1) & 3]);
-        leaf[t] = 0;
-        const int32_t d = depth[t] + 1;
-        for (int i = 0; i < 8; ++i) {
-            kids.push_back((int32_t)tets.size());
-            add_tet(ch[i], d);
-        }
-    }
-    void leaf_segments(int32_t e, std::vector<int32_t>& out) const {
-        int32_t stack[64];
-        int sp = 0;
-        stack[sp++] = e;
-        while (sp) {
-            const int32_t x = stack[--sp];
-            if (halves[x].x < 0) {
-                out.push_back(x);
-            } else {
-                stack[sp++] = halves[x].y;
-                stack[sp++] = halves[x].x;
-            }
-        }
-    }
-};
-
 // Centroids of the n-fold Kuhn subdivision of {1 >= x1 >= x2 >= x3 >= 0}:
 // the cube cells' simplices c + (3 e_a + 2 e_b + e_c) / 4 that lie in it.
 std::vector<float4> kuhn_table(int n) {
@@ -756,161 +607,81 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         const int tet_threads = 32 * tet_warps;
         const size_t tet_smem = (size_t)tet_warps * n_samples * sizeof(float);
 
-        // the mesh and its edges, numbered in (smaller, larger) node-id order
-        TetLattice lat;
-        lat.xyz.assign(nodes, nodes + 3 * n_nodes);
-        {
-            std::vector<uint64_t> keys;
-            keys.reserve((size_t)n_tets * 6);
-            for (int64_t t = 0; t < n_tets; ++t) {
-                const int32_t* v = tets + 4 * t;
-                for (int e = 0; e < 6; ++e)
-                    keys.push_back(TetLattice::key(v[kLocalEdges[e][0]], v[kLocalEdges[e][1]]));
-            }
-            std::sort(keys.begin(), keys.end());
-            keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-            lat.ids.reserve(keys.size() * 4);
-            lat.edges.reserve(keys.size() * 4);
-            lat.mid.reserve(keys.size() * 4);
-            lat.halves.reserve(keys.size() * 4);
-            for (uint64_t k : keys) lat.add_edge((int32_t)(k >> 32), (int32_t)(k & 0xffffffffu));
-            for (int64_t t = 0; t < n_tets; ++t) {
-                const int32_t* v = tets + 4 * t;
-                lat.add_tet(make_int4(v[0], v[1], v[2], v[3]), 0);
-            }
-        }
-
+        // the mesh on the device: its edges numbered in (smaller, larger) node order
         host.stop();
+        DevMesh mesh;
+        mesh_init(mesh, nodes, n_nodes, tets, n_tets, s);
         DevBuf d_tgt((size_t)n_vox * sizeof(float), s);
         CSL_CUDA(cudaMemcpyAsync(d_tgt.get(), vox->target, (size_t)n_vox * sizeof(float),
                                  cudaMemcpyHostToDevice, s));
         DevBuf d_coef;
         upload(d_coef, kuhn_table(p->tet_n), s);
 
-        // Steps 1-3 level by level: targets, rho* and the ratio of the new
-        // tetrahedra on the device, the subdivision on the host
-        std::vector<double> target(lat.tets.size());
-        std::vector<float> rho_star(lat.tets.size()), tet_ratio(lat.tets.size());
-        std::vector<int32_t> cand(n_tets);
-        for (int64_t t = 0; t < n_tets; ++t) cand[t] = (int32_t)t;
-        int64_t n_split = 0;
-        DevBuf d_tv, d_target, d_rho, d_ratio;
-        std::vector<float4> h_tv;
-        std::vector<double> h_target;
-        std::vector<float> h_rho, h_ratio;
-        for (int d = 0; d <= p->max_depth && !cand.empty(); ++d) {
-            host.start();
-            const int64_t nc = (int64_t)cand.size();
-            h_tv.resize((size_t)nc * 4);
-            for (int64_t i = 0; i < nc; ++i) {
-                const int4 t = lat.tets[cand[i]];
-                const int32_t v[4] = {t.x, t.y, t.z, t.w};
-                for (int k = 0; k < 4; ++k)
-                    h_tv[4 * i + k] = make_float4(lat.xyz[3 * v[k]], lat.xyz[3 * v[k] + 1],
-                                                  lat.xyz[3 * v[k] + 2], 0.0f);
-            }
-            host.stop();
-            upload(d_tv, h_tv, s);
-            d_target.ensure((size_t)nc * sizeof(double), s);
-            d_rho.ensure((size_t)nc * sizeof(float), s);
-            d_ratio.ensure((size_t)nc * sizeof(float), s);
+        // Steps 1-3 level by level on the device: targets, rho* and the ratio of
+        // the level's tetrahedra (the input, then the children of the last
+        // level's splits: a contiguous range of ids), then the subdivision.
+        // Values are kept per tetrahedron id.
+        DevBuf d_target, d_rho, d_ratio, d_tv, d_split;
+        auto per_tet = [&](int64_t used, int64_t need) {
+            auto keep = [&](DevBuf& b, size_t el) {
+                if ((size_t)need * el <= b.size()) return;
+                DevBuf nb((size_t)std::max<int64_t>(need, 1) * el, s);
+                if (used)
+                    CSL_CUDA(cudaMemcpyAsync(nb.get(), b.get(), (size_t)used * el,
+                                             cudaMemcpyDeviceToDevice, s));
+                b = std::move(nb);
+            };
+            keep(d_target, sizeof(double));
+            keep(d_rho, sizeof(float));
+            keep(d_ratio, sizeof(float));
+        };
+        per_tet(0, n_tets);
+        int64_t n_split = 0, t0 = 0, nc = n_tets;
+        for (int d = 0; d <= p->max_depth && nc > 0; ++d) {
+            d_tv.ensure((size_t)nc * 4 * sizeof(float4), s);
+            mesh_corners(mesh, t0, nc, d_tv.as<float4>(), s);
+            double* tgt_d = d_target.as<double>() + t0;
+            float* rho_d = d_rho.as<float>() + t0;
+            float* rat_d = d_ratio.as<float>() + t0;
             k_dm_target<<<grid_for(nc * 32, 256), 256, 0, s>>>(d_tv.as<float4>(), nc, g,
-                                                               d_tgt.as<float>(),
-                                                               d_target.as<double>());
+                                                               d_tgt.as<float>(), tgt_d);
             CSL_LAUNCH_CHECK("density targets");
             k_dm_tet<<<grid_for(nc * 32, tet_threads), tet_threads, tet_smem, s>>>(
-                d_tv.as<float4>(), d_target.as<double>(), nc, d_coef.as<float4>(), n_samples, c,
-                d_rho.as<float>(), d_ratio.as<float>());
+                d_tv.as<float4>(), tgt_d, nc, d_coef.as<float4>(), n_samples, c, rho_d, rat_d);
             CSL_LAUNCH_CHECK("tetrahedron densities");
-            download(h_target, d_target, nc, s);
-            download(h_rho, d_rho, nc, s);
-            download(h_ratio, d_ratio, nc, s);
-            host.start();
-            std::vector<int32_t> next;
-            for (int64_t i = 0; i < nc; ++i) {
-                const int32_t t = cand[i];
-                target[t] = h_target[i];
-                rho_star[t] = h_rho[i];
-                tet_ratio[t] = h_ratio[i];
-                if (d < p->max_depth && (double)h_rho[i] < h_target[i]) {
-                    if ((int64_t)lat.tets.size() + 8 >= (1ll << 27))
-                        fail(CSL_ERR_CAPACITY, "more than 2^27 tetrahedra");
-                    lat.subdivide(t, next);
-                    ++n_split;
-                }
-            }
-            target.resize(lat.tets.size());
-            rho_star.resize(lat.tets.size());
-            tet_ratio.resize(lat.tets.size());
-            cand.swap(next);
-            host.stop();
+            if (d == p->max_depth) break;
+            d_split.ensure((size_t)nc * 4, s);
+            k_dm_split<<<grid_for(nc, 256), 256, 0, s>>>(rho_d, tgt_d, nc, d_split.as<uint32_t>());
+            CSL_LAUNCH_CHECK("split flags");
+            const int64_t before = mesh.n_tets;
+            const int64_t ns = mesh_subdivide(mesh, t0, nc, d_split.as<uint32_t>(), s);
+            n_split += ns;
+            per_tet(before, mesh.n_tets);
+            t0 = before;
+            nc = 8 * ns;
         }
-        host.start();
 
         // the final edges (unsplit, in creation order) and the leaves
-        const int64_t n_e = (int64_t)lat.edges.size();
-        std::vector<int32_t> seg_of(n_e, -1), segs;
-        for (int64_t e = 0; e < n_e; ++e)
-            if (lat.halves[e].x < 0) {
-                seg_of[e] = (int32_t)segs.size();
-                segs.push_back((int32_t)e);
-            }
-        const int64_t n_seg = (int64_t)segs.size();
+        MeshFinal fin;
+        mesh_finalize(mesh, fin, s);
+        const int64_t n_seg = fin.n_seg, n_leaf = fin.n_leaf;
         if (n_seg >= (1ll << 31)) fail(CSL_ERR_CAPACITY, "too many edges");
-        std::vector<int32_t> leaves;
-        for (int64_t t = 0; t < (int64_t)lat.tets.size(); ++t)
-            if (lat.leaf[t]) leaves.push_back((int32_t)t);
-        const int64_t n_leaf = (int64_t)leaves.size();
 
         // Step 3's per-edge minimum over the leaves containing the edge
-        std::vector<int32_t> pair_tet, pair_seg, tmp;
-        std::vector<float> leaf_ratio(n_leaf);
-        for (int64_t i = 0; i < n_leaf; ++i) {
-            const int32_t t = leaves[i];
-            leaf_ratio[i] = tet_ratio[t];
-            for (int e = 0; e < 6; ++e) {
-                tmp.clear();
-                lat.leaf_segments(lat.tet_edges[t][e], tmp);
-                for (int32_t x : tmp) {
-                    pair_tet.push_back((int32_t)i);
-                    pair_seg.push_back(seg_of[x]);
-                }
-            }
-        }
-        host.stop();
-        DevBuf d_pt, d_ps, d_lr, d_r3((size_t)std::max<int64_t>(n_seg, 1) * 4, s);
-        upload(d_pt, pair_tet, s);
-        upload(d_ps, pair_seg, s);
-        upload(d_lr, leaf_ratio, s);
-        {
-            std::vector<uint32_t> inf(n_seg, 0x7f800000u);
-            if (n_seg)
-                CSL_CUDA(cudaMemcpyAsync(d_r3.get(), inf.data(), n_seg * 4, cudaMemcpyHostToDevice, s));
-            const int64_t np = (int64_t)pair_tet.size();
-            if (np) {
-                k_dm_edge_min<<<grid_for(np, 256), 256, 0, s>>>(d_pt.as<int32_t>(), d_ps.as<int32_t>(),
-                                                                np, d_lr.as<float>(),
-                                                                d_r3.as<uint32_t>());
-                CSL_LAUNCH_CHECK("edge ratio minimum");
-            }
-            if (n_seg) {
-                k_dm_ratio_fix<<<grid_for(n_seg, 256), 256, 0, s>>>(d_r3.as<uint32_t>(), n_seg);
-                CSL_LAUNCH_CHECK("edge ratio default");
-            }
+        DevBuf d_r3((size_t)std::max<int64_t>(n_seg, 1) * 4, s);
+        if (n_seg) {
+            k_dm_fill_u32<<<grid_for(n_seg, 256), 256, 0, s>>>(d_r3.as<uint32_t>(), n_seg,
+                                                               0x7f800000u);
+            CSL_LAUNCH_CHECK("edge ratio start");
+            mesh_edge_min(mesh, fin, d_ratio.as<float>(), d_r3.as<uint32_t>(), s);
+            k_dm_ratio_fix<<<grid_for(n_seg, 256), 256, 0, s>>>(d_r3.as<uint32_t>(), n_seg);
+            CSL_LAUNCH_CHECK("edge ratio default");
         }
 
         // Step 4: voxel-edge pairs, the per-voxel ratio, the per-edge minimum
-        host.start();
-        std::vector<float4> h_sa(n_seg), h_sb(n_seg);
-        for (int64_t i = 0; i < n_seg; ++i) {
-            const int2 ab = lat.edges[segs[i]];
-            h_sa[i] = make_float4(lat.xyz[3 * ab.x], lat.xyz[3 * ab.x + 1], lat.xyz[3 * ab.x + 2], 0.f);
-            h_sb[i] = make_float4(lat.xyz[3 * ab.y], lat.xyz[3 * ab.y + 1], lat.xyz[3 * ab.y + 2], 0.f);
-        }
-        host.stop();
-        DevBuf d_sa, d_sb;
-        upload(d_sa, h_sa, s);
-        upload(d_sb, h_sb, s);
+        DevBuf d_sa((size_t)std::max<int64_t>(n_seg, 1) * 16, s),
+            d_sb((size_t)std::max<int64_t>(n_seg, 1) * 16, s);
+        mesh_segment_points(mesh, fin, d_sa.as<float4>(), d_sb.as<float4>(), s);
         const double reach = R * (1.0 + 1e-6) + 1e-6 * vox->h;
         DevBuf d_vr((size_t)n_vox * 4, s), d_rf((size_t)std::max<int64_t>(n_seg, 1) * 4, s);
         if (n_seg)
@@ -969,40 +740,38 @@ extern "C" csl_status csl_density_match(const float* nodes, int64_t n_nodes, con
         download(h_r3, d_r3, n_seg, s);
         download(h_vr, d_vr, n_vox, s);
 
-        // the result, in page-locked host blocks
+        // the result, gathered on the device and copied into page-locked host blocks
+        DevBuf g_edges((size_t)std::max<int64_t>(n_seg, 1) * 8, s),
+            g_tets((size_t)std::max<int64_t>(n_leaf, 1) * 16, s),
+            g_depth((size_t)std::max<int64_t>(n_leaf, 1) * 4, s),
+            g_target((size_t)std::max<int64_t>(n_leaf, 1) * 8, s),
+            g_rho((size_t)std::max<int64_t>(n_leaf, 1) * 4, s),
+            g_ratio((size_t)std::max<int64_t>(n_leaf, 1) * 4, s);
+        mesh_gather_final(mesh, fin, g_edges.as<int32_t>(), g_tets.as<int32_t>(),
+                          g_depth.as<int32_t>(), d_target.as<double>(), g_target.as<double>(),
+                          d_rho.as<float>(), g_rho.as<float>(), d_ratio.as<float>(),
+                          g_ratio.as<float>(), s);
         host.start();
-        std::vector<int32_t> h_edges((size_t)n_seg * 2), h_tets((size_t)n_leaf * 4), h_depth(n_leaf);
-        std::vector<double> h_tt(n_leaf);
-        std::vector<float> h_rs(n_leaf);
-        for (int64_t i = 0; i < n_seg; ++i) {
-            h_edges[2 * i] = lat.edges[segs[i]].x;
-            h_edges[2 * i + 1] = lat.edges[segs[i]].y;
-        }
-        for (int64_t i = 0; i < n_leaf; ++i) {
-            const int32_t t = leaves[i];
-            const int4 v = lat.tets[t];
-            h_tets[4 * i] = v.x;
-            h_tets[4 * i + 1] = v.y;
-            h_tets[4 * i + 2] = v.z;
-            h_tets[4 * i + 3] = v.w;
-            h_depth[i] = lat.depth[t];
-            h_tt[i] = target[t];
-            h_rs[i] = rho_star[t];
-        }
         csl_dm_result* r = (csl_dm_result*)calloc(1, sizeof(csl_dm_result));
         if (!r) fail(CSL_ERR_OOM, "result");
-        r->n_nodes = (int64_t)(lat.xyz.size() / 3);
-        r->nodes = (float*)host_copy(lat.xyz.data(), lat.xyz.size() * 4);
+        auto to_block = [&](const DevBuf& b, size_t bytes) {
+            void* h = host_block_alloc(bytes ? bytes : 16);
+            if (!h) fail(CSL_ERR_OOM, "host result block");
+            if (bytes) read_to_host(h, b.get(), bytes, s);
+            return h;
+        };
+        r->n_nodes = mesh.n_nodes;
+        r->nodes = (float*)to_block(mesh.xyz, (size_t)mesh.n_nodes * 12);
         r->n_edges = n_seg;
-        r->edges = (int32_t*)host_copy(h_edges.data(), h_edges.size() * 4);
+        r->edges = (int32_t*)to_block(g_edges, (size_t)n_seg * 8);
         r->radius = (float*)host_copy(h_rad.data(), h_rad.size() * 4);
         r->step3_ratio = (float*)host_copy(h_r3.data(), h_r3.size() * 4);
         r->n_tets = n_leaf;
-        r->tets = (int32_t*)host_copy(h_tets.data(), h_tets.size() * 4);
-        r->tet_depth = (int32_t*)host_copy(h_depth.data(), h_depth.size() * 4);
-        r->tet_target = (double*)host_copy(h_tt.data(), h_tt.size() * 8);
-        r->tet_rho_star = (float*)host_copy(h_rs.data(), h_rs.size() * 4);
-        r->tet_ratio = (float*)host_copy(leaf_ratio.data(), leaf_ratio.size() * 4);
+        r->tets = (int32_t*)to_block(g_tets, (size_t)n_leaf * 16);
+        r->tet_depth = (int32_t*)to_block(g_depth, (size_t)n_leaf * 4);
+        r->tet_target = (double*)to_block(g_target, (size_t)n_leaf * 8);
+        r->tet_rho_star = (float*)to_block(g_rho, (size_t)n_leaf * 4);
+        r->tet_ratio = (float*)to_block(g_ratio, (size_t)n_leaf * 4);
         r->n_voxels = n_vox;
         r->voxel_ratio = (float*)host_copy(h_vr.data(), h_vr.size() * 4);
         r->n_subdivided = n_split;

@@ -744,7 +744,12 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     // the successor bit trick of k_split_flags needs ids below 2^31
     if (n_cross >= ((int64_t)1 << 31)) fail(CSL_ERR_CAPACITY, "marching squares: too many crossings");
     DevBuf rec((size_t)n_cross * sizeof(Xing), s);
-    CSL_CUDA(cudaMemsetAsync(rec.get(), 0xff, (size_t)n_cross * sizeof(Xing), s));
+    // Every record is written whole by k_emit: x, y and the edge id by the cell
+    // that owns the edge, the successor by the cell the contour enters through
+    // it (each crossing edge is the entry side of exactly one of its two cells).
+    // A replay (planned sizes) may leave records unwritten when its sizes
+    // changed: there they start as invalid ids, so that no walk follows them.
+    if (rp) CSL_CUDA(cudaMemsetAsync(rec.get(), 0xff, (size_t)n_cross * sizeof(Xing), s));
 
     Dense D{ew.as<uint32_t>(), prefix.as<uint32_t>(), c.edge_wpl, c.ewr};
     {

@@ -101,9 +101,15 @@ void DevBuf::alloc(size_t bytes, cudaStream_t s) {
 
 void DevBuf::alloc_persistent(size_t bytes) {
     release();
+    keep_pool_memory();
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    // From the stream-ordered pool too (what a freed lattice or batch left
+    // there is reused without a round trip to the driver, which maps every
+    // page again): ordered on the legacy default stream and complete before
+    // this returns, so that any stream may use it.
+    cudaError_t e = cudaMallocAsync(&p, bytes, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) alloc_error(e, bytes);
     p_ = p;
     n_ = bytes;
@@ -120,8 +126,12 @@ void DevBuf::release() {
         owned_ = true;
         return;
     }
-    if (persistent_) cudaFree(p_);
-    else cudaFreeAsync(p_, s_);
+    if (persistent_) {   // any stream may still use it: wait for the device, as cudaFree does
+        cudaDeviceSynchronize();
+        cudaFreeAsync(p_, 0);
+    } else {
+        cudaFreeAsync(p_, s_);
+    }
     note_device_bytes(-(int64_t)n_);
     p_ = nullptr;
     n_ = 0;

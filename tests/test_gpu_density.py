@@ -54,6 +54,29 @@ def test_subdivision_topology_matches(small):
     assert len(set(ref["depth"].tolist())) == 3   # all three levels occur
 
 
+def test_medium_mesh_topology_matches():
+    """A 4^3-cube mesh (384 tetrahedra): every input tetrahedron splits at
+    level 0 and 32 of the children again at level 1, so edges split at an
+    earlier level by a neighbour and faces shared by two splits of one level
+    both occur; nodes, edges (creation order), leaves and depths bit-exact."""
+    from synth.tets import SEED_BASE, graded_target_grid, kuhn_tet_mesh
+    nodes, tets = kuhn_tet_mesh((4, 4, 4), 4.0, 0.1, seed=SEED_BASE + 9)
+    grid = graded_target_grid((0.0, 0.0, 0.0), (16.0, 16.0, 16.0), 16.0 / 5.0,
+                              scale=(0.03, 0.5), period=16.0)
+    cfg = dict(nodes=nodes, tets=tets, grid=grid, r_min=0.1, tet_n=2, vox_m=2, max_depth=2,
+               iters=24)
+    ref = D.density_match(nodes, tets, grid, r_min=0.1, tet_n=2, vox_m=2, max_depth=2, iters=24)
+    margins = np.array([abs(m) for _, m, _ in ref["decisions"]])
+    assert margins.min() > 1e-4          # no near tie in this seeded case
+    got = _run_gpu(cfg)
+    assert got["n_subdivided"] == sum(1 for *_, s in ref["decisions"] if s) == 416
+    assert np.array_equal(got["nodes"], ref["nodes"])
+    assert np.array_equal(got["edges"], ref["edges"])
+    assert np.array_equal(got["tets"], ref["tets"])
+    assert np.array_equal(got["depth"], ref["depth"])
+    assert np.bincount(got["depth"]).tolist() == [0, 3040, 256]
+
+
 def test_targets_and_rho_star(small):
     cfg, ref, got = small
     assert np.max(np.abs(got["target"] - ref["target"])) <= 1e-12
