@@ -795,23 +795,6 @@ def main():
 
     line["slice_workspace_peak_bytes"] = int(peak_main)
     line["plan"] = plan
-    if world == 1 and not args.no_extra and plan["field_kernel"] == "footprint":
-        # the same slice with the fused field and contour pass (no Sigma plane):
-        # time per step and workspace, beside the default (Sigma plane)
-        kw_u = dict(kw, fused=True)
-        lat.slice(**kw_u, on_device=True).free()
-        peak_u = cs.last_stats().device_bytes_peak
-        u_ms = _event_ms(lambda: lat.slice(**kw_u, on_device=True).free(), args.steps, 1,
-                         stream)
-        line["fused_vs_unfused"] = {
-            "fused_ms_per_step": u_ms, "unfused_ms_per_step": t_max / args.steps,
-            "fused_workspace_peak_bytes": int(peak_u),
-            "unfused_workspace_peak_bytes": int(peak_main),
-            "basis": "the same steps through csl_slice_layers with CSL_SLICE_FUSED (each "
-                     "tile's crossing vertices from shared memory, no Sigma plane) and without "
-                     "(the default: Sigma plane, marching squares reads it); contours kept on "
-                     "the device; workspace = largest device memory the call held at once"}
-
     if not args.no_e2e:
         # end to end through the public API: pinned host inputs, upload + prepare,
         # slice, contours copied back to host memory
@@ -827,6 +810,7 @@ def main():
         def e2e_step():
             t0 = time.perf_counter()
             L2 = cs.Lattice(pn, pe, pr, R=cfg["R"], C=cfg["C"])
+            torch.cuda.synchronize()   # (the upload returns synchronised; phase attribution)
             t1 = time.perf_counter()
             cont = L2.slice(**kw)
             t2 = time.perf_counter()
@@ -859,6 +843,24 @@ def main():
                        "wall_ms_upload_slice_release": [
                            [round(x, 1) for x in ph] for ph in phase_wall[1:]],
                        "slice_workspace_peak_bytes": int(e2e_peak[0])}
+
+    if world == 1 and not args.no_extra and plan["field_kernel"] == "footprint":
+        # the same slice with the fused field and contour pass (no Sigma plane):
+        # time per step and workspace, beside the default (Sigma plane); after the
+        # end-to-end line, whose lattice uploads it would otherwise precede
+        kw_u = dict(kw, fused=True)
+        lat.slice(**kw_u, on_device=True).free()
+        peak_u = cs.last_stats().device_bytes_peak
+        u_ms = _event_ms(lambda: lat.slice(**kw_u, on_device=True).free(), args.steps, 1,
+                         stream)
+        line["fused_vs_unfused"] = {
+            "fused_ms_per_step": u_ms, "unfused_ms_per_step": t_max / args.steps,
+            "fused_workspace_peak_bytes": int(peak_u),
+            "unfused_workspace_peak_bytes": int(peak_main),
+            "basis": "the same steps through csl_slice_layers with CSL_SLICE_FUSED (each "
+                     "tile's crossing vertices from shared memory, no Sigma plane) and without "
+                     "(the default: Sigma plane, marching squares reads it); contours kept on "
+                     "the device; workspace = largest device memory the call held at once"}
 
     if world == 1 and not args.no_extra:
         # self-support metrics (Eq. 11-14) of the same lattice, printing along z

@@ -34,17 +34,21 @@ struct ScanOut {
     uint32_t max_dz;
 };
 
+// Box of the nodes, largest radius and input checks. Each thread keeps its
+// own minima and maxima over its grid-stride items; a warp reduces them and
+// one lane applies them (a few atomics per warp instead of one per item).
 __global__ void k_scan_inputs(const float* __restrict__ nodes, int64_t n_nodes,
                               const int32_t* __restrict__ edges, const float* __restrict__ radius,
                               int64_t n_edges, ScanOut* out) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t st = 0;
+    uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u}, mr = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += stride) {
         for (int k = 0; k < 3; ++k) {
             float v = nodes[3 * i + k];
             if (!isfinite(v)) { st |= ST_NONFINITE; continue; }
-            atomicMin(&out->lo[k], ord_enc(v));
-            atomicMax(&out->hi[k], ord_enc(v));
+            lo[k] = min(lo[k], ord_enc(v));
+            hi[k] = max(hi[k], ord_enc(v));
         }
     }
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_edges; j += stride) {
@@ -53,9 +57,23 @@ __global__ void k_scan_inputs(const float* __restrict__ nodes, int64_t n_nodes,
         float r = radius[j];
         if (!isfinite(r)) st |= ST_NONFINITE;
         else if (!(r > 0.0f)) st |= ST_BAD_RADIUS;
-        else atomicMax(&out->max_r, ord_enc(r));
+        else mr = max(mr, ord_enc(r));
     }
-    if (st) atomicOr(&out->status, st);
+    const unsigned all = 0xffffffffu;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = __reduce_min_sync(all, lo[k]);
+        hi[k] = __reduce_max_sync(all, hi[k]);
+    }
+    mr = __reduce_max_sync(all, mr);
+    st = __reduce_or_sync(all, st);
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 3; ++k) {
+            if (lo[k] != 0xffffffffu) atomicMin(&out->lo[k], lo[k]);
+            if (hi[k] != 0u) atomicMax(&out->hi[k], hi[k]);
+        }
+        if (mr) atomicMax(&out->max_r, mr);
+        if (st) atomicOr(&out->status, st);
+    }
 }
 
 __global__ void k_prep_keys(const float* __restrict__ nodes, const int32_t* __restrict__ edges,
