@@ -578,8 +578,11 @@ csl_status csl_simplify_contours(const csl_contours* in, int32_t nx, int32_t ny,
  * (x0 + pixel/2, y0 + pixel/2)): in each of `iterations` Jacobi steps its
  * free coordinate a (x on a horizontal edge, y on a vertical one) becomes
  * a + lambda (m - a), m the mean of that coordinate at its loop neighbours,
- * in FP64, clamped to the edge's [margin, 1 - margin] part and rounded to
- * float; the other coordinate, the edge ids and all offsets are unchanged;
+ * clamped to the edge's [margin, 1 - margin] part, in float32 with every
+ * operation rounded on its own (m = 0.5 (a_p + a_s); a + lambda (m - a); the
+ * edge's first sample lo = (x0 - pixel/2) + I pixel; lo + margin pixel and
+ * lo + (1 - margin) pixel, lambda and the two margins rounded once from
+ * double); the other coordinate, the edge ids and all offsets are unchanged;
  * loops of fewer than 3 vertices stay as they are. Every segment stays
  * inside its grid cell (or the 1 x 2 block of a vertex that simplification
  * dropped), so no two segments can come to cross. c: device contours with

@@ -8,9 +8,12 @@
 // (I, J) sits at (x0 + (I - 1/2) px, y0 + (J - 1/2) px). A vertex moves only
 // along its own edge: in each of K Jacobi iterations its free coordinate a
 // (x on a horizontal edge, y on a vertical one) becomes a + lam (m - a), m the
-// mean of the same coordinate of its loop predecessor and successor, in FP64,
-// clamped to [lo + mu px, lo + (1 - mu) px] (lo: the edge's first sample) and
-// rounded to float. Loops of fewer than 3 vertices stay as they are. Each
+// mean of the same coordinate of its loop predecessor and successor, clamped
+// to [lo + mu px, lo + (1 - mu) px] (lo: the edge's first sample), in float32
+// with every operation rounded on its own, in the order m = 0.5 (a_p + a_s),
+// a + lam (m - a), lo = c0 + I px (c0 = x0 - px / 2, or the y and row
+// counterparts) and the two bounds, so that results are the same bit for bit
+// wherever the same operations run. Loops of fewer than 3 vertices stay as they are. Each
 // segment joins vertices on two edges of one cell (or of the 1 x 2 block of a
 // vertex that simplification dropped) and every vertex stays strictly inside
 // its edge, so every segment stays in its cell; a saddle cell's two segments
@@ -30,8 +33,8 @@ namespace {
 struct SmConst {
     int32_t W;
     int64_t n_ids;        // 2 W H
-    double x0, y0, px, lam;
-    double m_lo, m_hi;    // mu px and (1 - mu) px
+    float cx0, cy0, px, lam;   // x0 - px / 2, y0 - px / 2 (rounded once from FP64)
+    float m_lo, m_hi;          // mu px and (1 - mu) px
 };
 
 __global__ void k_sm_loop_of(const int64_t* __restrict__ loop_off, int64_t n_loops,
@@ -67,19 +70,15 @@ __global__ void k_sm_step(const int64_t* __restrict__ loop_off, const int32_t* _
             // emulated sequence per vertex)
             const uint32_t base = (uint32_t)e >> 1;
             const int J = (int)(base / (uint32_t)g.W), I = (int)(base - (uint32_t)J * (uint32_t)g.W);
-            if (e & 1) {   // vertical edge: y moves
-                const double lo = g.y0 + ((double)J - 0.5) * g.px;
-                const double av = (double)P.y;
-                const double m = 0.5 * ((double)Pp.y + (double)Ps.y);
-                const double an = fmin(fmax(av + g.lam * (m - av), lo + g.m_lo), lo + g.m_hi);
-                P.y = (float)an;
-            } else {       // horizontal edge: x moves
-                const double lo = g.x0 + ((double)I - 0.5) * g.px;
-                const double av = (double)P.x;
-                const double m = 0.5 * ((double)Pp.x + (double)Ps.x);
-                const double an = fmin(fmax(av + g.lam * (m - av), lo + g.m_lo), lo + g.m_hi);
-                P.x = (float)an;
-            }
+            const bool vert = e & 1;   // vertical edge: y moves; horizontal: x moves
+            const float lo = __fadd_rn(vert ? g.cy0 : g.cx0,
+                                       __fmul_rn((float)(vert ? J : I), g.px));
+            const float av = vert ? P.y : P.x;
+            const float m = __fmul_rn(0.5f, __fadd_rn(vert ? Pp.y : Pp.x, vert ? Ps.y : Ps.x));
+            const float an = __fadd_rn(av, __fmul_rn(g.lam, __fsub_rn(m, av)));
+            const float a = fminf(fmaxf(an, __fadd_rn(lo, g.m_lo)), __fadd_rn(lo, g.m_hi));
+            if (vert) P.y = a;
+            else P.x = a;
         }
         dst[v] = P;
     }
@@ -115,12 +114,12 @@ extern "C" csl_status csl_smooth_contours(csl_contours* c, double x0, double y0,
         SmConst g;
         g.W = nx + 2;
         g.n_ids = 2 * (int64_t)(nx + 2) * (ny + 2);
-        g.x0 = x0;
-        g.y0 = y0;
-        g.px = pixel;
-        g.lam = lambda;
-        g.m_lo = margin * pixel;
-        g.m_hi = (1.0 - margin) * pixel;
+        g.cx0 = (float)(x0 - 0.5 * pixel);
+        g.cy0 = (float)(y0 - 0.5 * pixel);
+        g.px = (float)pixel;
+        g.lam = (float)lambda;
+        g.m_lo = (float)(margin * pixel);
+        g.m_hi = (float)((1.0 - margin) * pixel);
         DevBuf d_bad(4, s), d_vloop((size_t)n * 4, s), d_tmp((size_t)n * 8, s);
         CSL_CUDA(cudaMemsetAsync(d_bad.get(), 0, 4, s));
         k_sm_check<<<grid_for(n, 256), 256, 0, s>>>(c->edge_id, n, g.n_ids, d_bad.as<uint32_t>());

@@ -58,7 +58,11 @@ def test_margin_one_half_gives_edge_midpoints():
     W = cfg["nx"] + 2
     for v in range(len(eid)):
         axis, lo = M.edge_axis_and_lo(int(eid[v]), W, cfg["x0"], cfg["y0"], cfg["pixel"])
-        assert out[v, axis] == np.float32(lo + 0.5 * cfg["pixel"])
+        mid = lo + 0.5 * cfg["pixel"]
+        # the midpoint in FP64, up to the float32 roundings of the bound (c0, the
+        # product, two sums: at most 2 ulp of the coordinate)
+        ulp = float(np.spacing(np.float32(abs(mid) + cfg["pixel"])))
+        assert abs(float(out[v, axis]) - mid) <= 2.0 * ulp
         assert out[v, 1 - axis] == xy32[v, 1 - axis]
 
 
@@ -124,8 +128,12 @@ def test_loops_stay_on_their_edges_and_do_not_cross(k, simplify):
     for v in range(len(eid)):
         axis, lo = M.edge_axis_and_lo(int(eid[v]), W, cfg["x0"], cfg["y0"], cfg["pixel"])
         assert out[v, 1 - axis] == xy32[v, 1 - axis]
-        assert np.float32(lo + mu * cfg["pixel"]) <= out[v, axis]
-        assert out[v, axis] <= np.float32(lo + (1.0 - mu) * cfg["pixel"])
+        # inside the margin up to the float32 roundings of the bounds (2 ulp),
+        # strictly inside the edge (what keeps every segment in its cell)
+        a = float(out[v, axis])
+        ulp = float(np.spacing(np.float32(abs(lo) + cfg["pixel"])))
+        assert lo + mu * cfg["pixel"] - 2.0 * ulp <= a <= lo + (1.0 - mu) * cfg["pixel"] + 2.0 * ulp
+        assert lo < a < lo + cfg["pixel"]
     moved = np.any(out != xy32, axis=1)
     assert moved.sum() > 0.5 * len(eid)
     assert _crossings(*_segments(off, out)) == 0
