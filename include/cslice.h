@@ -205,7 +205,10 @@ typedef struct csl_slice_desc {
 /* Host arrays (on_device = 0) share one page-locked block, taken from a
  * per-process cache so that device-to-host copies run at the link's speed;
  * csl_contours_free returns the block to the cache (free blocks above 64 GiB
- * in total are released). */
+ * in total are released). Device arrays from csl_slice_layers are written in
+ * place chunk by chunk: loop_vert_off, xy and edge_id grow behind reserved
+ * address ranges (the driver's virtual memory management), so no copy of the
+ * whole result is made; csl_contours_free releases them. */
 typedef struct csl_contours {
     int32_t n_layers;
     int32_t on_device;        /* 1: the arrays below are device pointers           */

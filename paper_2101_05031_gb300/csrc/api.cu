@@ -328,11 +328,10 @@ void csl_lattice_free(csl_lattice* L) { delete L; }
 
 void csl_contours_free(csl_contours* c) {
     if (!c) return;
-    if (c->on_device) {
-        cudaFree(c->layer_loop_off);
-        cudaFree(c->loop_vert_off);
-        cudaFree(c->xy);
-        cudaFree(c->edge_id);
+    if (c->on_device) {   // arrays grown in place (slicing) go back through their registry
+        for (void* p : {(void*)c->layer_loop_off, (void*)c->loop_vert_off, (void*)c->xy,
+                        (void*)c->edge_id})
+            if (p && !growmap_free(p)) cudaFree(p);
     } else {
         host_block_free(c->layer_loop_off);   // offsets block
         host_block_free(c->xy);               // vertex block (edge ids included)
@@ -574,6 +573,28 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             }
         }
         bool spec_all = spec.block != nullptr;   // every chunk's vertices went to the block
+        // Device contours are assembled in place: every chunk writes its
+        // vertices, edge ids and loop offsets into arrays that grow behind
+        // fixed address ranges (physical memory mapped as they grow), so no
+        // gather copy follows the last chunk and no second copy is held.
+        GrowMap gm_xy, gm_eid, gm_loop;
+        ChunkDest dest;
+        bool in_place = on_dev && want_contours && d.n_layers > 0 && growmap_available();
+        if (in_place) {
+            size_t free_b = 0, total_b = 0;
+            CSL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            gm_xy.reserve(total_b);
+            if (want_eid) gm_eid.reserve(total_b / 2);
+            gm_loop.reserve(total_b);
+            dest.xy = static_cast<float2*>(gm_xy.base());
+            dest.eid = want_eid ? static_cast<int32_t*>(gm_eid.base()) : nullptr;
+            dest.loop_off = static_cast<int64_t*>(gm_loop.base());
+            dest.make_room = [&](int64_t verts, int64_t loop_entries) {
+                gm_xy.ensure((size_t)verts * 8);
+                if (want_eid) gm_eid.ensure((size_t)verts * 4);
+                gm_loop.ensure((size_t)loop_entries * 8);
+            };
+        }
         auto contour_stage = [&](int k, const ChunkGeom& g) {
             cudaStream_t ks = streams[k % n_par];
             const float* sigma = d.sigma_out ? d.sigma_out + (int64_t)g.first_layer * plane
@@ -582,10 +603,13 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
             cc.n_layers = g.n_layers;
             timed(st.contour_ms, [&] {
                 contours_chunk(g, L->C, sigma, mask_ws[k % n_par].as<uint32_t>(), want_eid, cc,
-                               ks, nullptr, p.fused ? &fv_ws[k % n_par] : nullptr);
+                               ks, nullptr, p.fused ? &fv_ws[k % n_par] : nullptr,
+                               in_place ? &dest : nullptr);
             });
             st.crossings += cc.n_verts;
             st.loops += cc.n_loops;
+            dest.v_base += cc.n_verts;
+            dest.l_base += cc.n_loops;
             if (budgeted) {   // to_host() copies this chunk
             } else if (spec_all && spec.copied + cc.n_verts <= spec.cap) {
                 if (cc.n_verts) {
@@ -862,6 +886,33 @@ csl_status csl_slice_layers(csl_lattice* L, const csl_slice_desc* desc, void* st
         int64_t n_loops = 0, n_verts = 0;
         for (auto& cc : dev_chunks) { n_loops += cc.n_loops; n_verts += cc.n_verts; }
         csl_contours* c = nullptr;
+        if (in_place) {   // the arrays are complete: hand them over, offsets per layer only
+            c = new csl_contours();
+            memset(c, 0, sizeof(*c));
+            c->n_layers = d.n_layers;
+            c->on_device = 1;
+            c->n_loops = n_loops;
+            c->n_verts = n_verts;
+            if (cudaMalloc((void**)&c->layer_loop_off, (size_t)(d.n_layers + 1) * 8) != cudaSuccess) {
+                cudaGetLastError();
+                delete c;
+                fail(CSL_ERR_OOM, "device allocation of the contours failed");
+            }
+            int layer = 0;
+            for (auto& cc : dev_chunks) {   // rebased already; entry 0 repeats the last end
+                CSL_CUDA(cudaMemcpyAsync(c->layer_loop_off + layer, cc.layer_loops.get(),
+                                         (size_t)(cc.n_layers + 1) * 8, cudaMemcpyDeviceToDevice, s));
+                layer += cc.n_layers;
+            }
+            CSL_CUDA(cudaStreamSynchronize(s));
+            c->xy = static_cast<float*>(gm_xy.hand_over());
+            c->edge_id = want_eid ? static_cast<int32_t*>(gm_eid.hand_over()) : nullptr;
+            c->loop_vert_off = static_cast<int64_t*>(gm_loop.hand_over());
+            dev_chunks.clear();
+            finish_stats();
+            *out = c;
+            return;
+        }
         if (on_dev) {
             c = new csl_contours();
             memset(c, 0, sizeof(*c));

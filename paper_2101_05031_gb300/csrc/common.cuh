@@ -70,6 +70,32 @@ class DevBuf {
     bool owned_ = true;
 };
 
+// A device array that grows in place (growmap.cu): reserve() takes a range of
+// virtual addresses, ensure(n) maps physical memory behind its first n bytes
+// (the base address never moves). hand_over() passes the memory to a registry
+// from which growmap_free(base) releases it (csl_contours_free); otherwise the
+// destructor releases it. Both wait for the device first.
+class GrowMap {
+  public:
+    GrowMap() = default;
+    ~GrowMap();
+    GrowMap(const GrowMap&) = delete;
+    GrowMap& operator=(const GrowMap&) = delete;
+    void reserve(size_t bytes);
+    void ensure(size_t bytes);
+    void* base() const { return reinterpret_cast<void*>(va_); }
+    void* hand_over();
+
+  private:
+    void free_all();
+    unsigned long long va_ = 0;
+    size_t reserved_ = 0, mapped_ = 0, gran_ = 0;
+    int dev_ = 0;
+    std::vector<std::pair<unsigned long long, size_t>> handles_;   // (handle, bytes)
+};
+bool growmap_available();
+bool growmap_free(void* base);   // true when base came from hand_over()
+
 // Workspace accounting for csl_last_stats.
 void note_device_bytes(int64_t delta);
 int64_t device_bytes_peak_and_reset();

@@ -621,7 +621,7 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
                                  const uint32_t* __restrict__ seg_len,
                                  const uint32_t* __restrict__ rank_start,
                                  const int64_t* __restrict__ scan, int64_t ns, int64_t n,
-                                 int64_t n_loops, int64_t* __restrict__ loop_off,
+                                 int64_t n_loops, int64_t vofs, int64_t* __restrict__ loop_off,
                                  float2* __restrict__ oxy, int32_t* __restrict__ oeid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < ns;
@@ -641,7 +641,7 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
             const uint32_t h = spos[ht];                 // the head splitter of this loop
             if ((int64_t)h >= ns) continue;
             const int64_t voff = scan[h] & 0xffffffffLL;
-            if (h == (uint32_t)t && (scan[h] >> 32) < n_loops) loop_off[scan[h] >> 32] = voff;
+            if (h == (uint32_t)t && (scan[h] >> 32) < n_loops) loop_off[scan[h] >> 32] = vofs + voff;
             const int64_t b = voff + (int64_t)rank_start[t];
             const int64_t l = seg_len[t];
             if (b < 0 || b + l > n) continue;           // only if the links were inconsistent
@@ -668,23 +668,31 @@ __global__ void k_write_segments(const Xing* __restrict__ rec, const uint32_t* _
 }
 
 // layer_loops[l] = loops whose head lies before the first crossing of layer l
+// (+ lofs); the chunk's closing vertex offset (+ vofs)
 __global__ void k_layer_loops(const uint32_t* __restrict__ prefix, int64_t edge_wpl, int n_layers,
                               const uint32_t* __restrict__ spos, const int64_t* __restrict__ scan,
-                              int64_t n_cross, int64_t ns, int64_t n_loops,
-                              int64_t* __restrict__ layer_loops, int64_t* __restrict__ loop_off) {
+                              int64_t n_cross, int64_t ns, int64_t n_loops, int64_t lofs,
+                              int64_t vofs, int64_t* __restrict__ layer_loops,
+                              int64_t* __restrict__ loop_off) {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l > n_layers) return;
     const int64_t first = l < n_layers ? (int64_t)prefix[(int64_t)l * edge_wpl] : n_cross;
     const int64_t sp = first < n_cross ? (int64_t)spos[first] : ns;
-    layer_loops[l] = sp < ns ? (scan[sp] >> 32) : n_loops;
-    if (l == 0) loop_off[n_loops] = n_cross;
+    layer_loops[l] = lofs + (sp < ns ? (scan[sp] >> 32) : n_loops);
+    if (l == 0) loop_off[n_loops] = vofs + n_cross;
+}
+
+__global__ void k_fill_i64(int64_t* __restrict__ a, int64_t n, int64_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
 }
 
 }  // namespace
 
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
                     bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp,
-                    const FusedVerts* fv) {
+                    const FusedVerts* fv, const ChunkDest* dest) {
     const bool replay = rp && rp->replay;
     MsConst c;
     c.nx = g.nx;
@@ -736,10 +744,19 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     out.n_verts = n_cross;
     out.layer_loops.ensure((size_t)(g.n_layers + 1) * 8, s);
     if (n_cross == 0) {
-        CSL_CUDA(cudaMemsetAsync(out.layer_loops.get(), 0, (size_t)(g.n_layers + 1) * 8, s));
         out.n_loops = 0;
-        out.loop_off.ensure(8, s);
-        CSL_CUDA(cudaMemsetAsync(out.loop_off.get(), 0, 8, s));
+        if (dest) {   // no loops: every layer starts at the running loop count
+            dest->make_room(dest->v_base, dest->l_base + 1);
+            k_fill_i64<<<1, 128, 0, s>>>(out.layer_loops.as<int64_t>(), g.n_layers + 1,
+                                         dest->l_base);
+            CSL_LAUNCH_CHECK("ms empty layers");
+            k_fill_i64<<<1, 32, 0, s>>>(dest->loop_off + dest->l_base, 1, dest->v_base);
+            CSL_LAUNCH_CHECK("ms empty chunk");
+        } else {
+            CSL_CUDA(cudaMemsetAsync(out.layer_loops.get(), 0, (size_t)(g.n_layers + 1) * 8, s));
+            out.loop_off.ensure(8, s);
+            CSL_CUDA(cudaMemsetAsync(out.loop_off.get(), 0, 8, s));
+        }
         if (rp && !replay) rp->plan->ns = rp->plan->nl = rp->plan->n_loops = 0;
         return;
     }
@@ -897,18 +914,35 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         if (rp) rp->plan->n_loops = n_loops;
     }
     out.n_loops = n_loops;
-    out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
-    out.xy.ensure((size_t)n_cross * 8, s);
-    if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
+    // where the vertices and loop offsets go: the chunk's own arrays, or the
+    // caller's growing result at its running bases
+    int64_t* o_loop;
+    float2* o_xy;
+    int32_t* o_eid;
+    int64_t vofs = 0, lofs = 0;
+    if (dest) {
+        dest->make_room(dest->v_base + n_cross, dest->l_base + n_loops + 1);
+        vofs = dest->v_base;
+        lofs = dest->l_base;
+        o_loop = dest->loop_off + lofs;
+        o_xy = dest->xy + vofs;
+        o_eid = want_eid ? dest->eid + vofs : nullptr;
+    } else {
+        out.loop_off.ensure((size_t)(n_loops + 1) * 8, s);
+        out.xy.ensure((size_t)n_cross * 8, s);
+        if (want_eid) out.eid.ensure((size_t)n_cross * 4, s);
+        o_loop = out.loop_off.as<int64_t>();
+        o_xy = out.xy.as<float2>();
+        o_eid = want_eid ? out.eid.as<int32_t>() : nullptr;
+    }
     k_write_segments<<<gs, 256, 0, s>>>(rec.as<Xing>(), cm.as<uint32_t>(), spos.as<uint32_t>(),
                                         split_id.as<uint32_t>(), seg_len.as<uint32_t>(),
                                         rank_start.as<uint32_t>(), scan.as<int64_t>(), ns, n_cross,
-                                        n_loops, out.loop_off.as<int64_t>(), out.xy.as<float2>(),
-                                        want_eid ? out.eid.as<int32_t>() : nullptr);
+                                        n_loops, vofs, o_loop, o_xy, o_eid);
     CSL_LAUNCH_CHECK("ms write");
     k_layer_loops<<<(unsigned)ceil_div(g.n_layers + 1, 128), 128, 0, s>>>(
         prefix.as<uint32_t>(), c.edge_wpl, g.n_layers, spos.as<uint32_t>(), scan.as<int64_t>(),
-        n_cross, ns, n_loops, out.layer_loops.as<int64_t>(), out.loop_off.as<int64_t>());
+        n_cross, ns, n_loops, lofs, vofs, out.layer_loops.as<int64_t>(), o_loop);
     CSL_LAUNCH_CHECK("ms layer loops");
 }
 

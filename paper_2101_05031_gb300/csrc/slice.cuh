@@ -1,6 +1,7 @@
 // Internal interfaces of the slicing pipeline (binner, field, contours).
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "lattice.cuh"
@@ -142,12 +143,26 @@ struct ChunkContours {
     DevBuf xy;            // float2 [n_verts]
     DevBuf eid;           // int32 [n_verts]
 };
+// A result assembled in place (device contours of a whole slice): a chunk
+// writes its vertices from v_base and its loop offsets from l_base of these
+// arrays, with the bases added to the offsets (and its layer_loops rebased by
+// l_base), after make_room(vertices, loop entries) has made the arrays reach
+// v_base + its vertices and l_base + its loops + 1.
+struct ChunkDest {
+    float2* xy = nullptr;
+    int32_t* eid = nullptr;       // when edge ids are wanted
+    int64_t* loop_off = nullptr;
+    int64_t v_base = 0, l_base = 0;
+    std::function<void(int64_t, int64_t)> make_room;
+};
+
 // Contours of a chunk. In a replay (rp->replay), out's arrays must already
 // hold rp->plan's sizes; they are filled in place.
 // With fv (the fused pass's vertex lists) sigma is not read and may be null.
+// With dest, out keeps only layer_loops (rebased) and the counts.
 void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint32_t* mask,
                     bool want_eid, ChunkContours& out, cudaStream_t s, const Replay* rp = nullptr,
-                    const FusedVerts* fv = nullptr);
+                    const FusedVerts* fv = nullptr, const ChunkDest* dest = nullptr);
 
 // Slicing request resolution (api.cu): tile / slab / chunk sizes and the
 // binner's rounding margin; the geometry of one chunk; argument checks that

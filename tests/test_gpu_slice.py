@@ -259,6 +259,36 @@ def test_device_contours_match_host(c1):
         assert np.array_equal(a, b)
 
 
+def test_device_contours_assembled_in_place(c1):
+    """Device contours are written chunk by chunk into arrays that grow in
+    place: the same as the host result with chunks that have crossings and
+    chunks that have none (layers below the lattice), with and without edge
+    ids; and their memory comes back when they are freed."""
+    cfg, lat = c1
+    z0 = cfg["z0"] - 6 * cfg["dz"]          # the first 6 layers lie below the lattice
+    kw = dict(z0=z0, dz=cfg["dz"], n_layers=14, x0=0, y0=0, nx=200, ny=200, pixel=0.1,
+              chunk_layers=2, slab=2)
+    for eid in (True, False):
+        host = lat.slice(edge_ids=eid, **kw)
+        dev = lat.slice(edge_ids=eid, on_device=True, **kw)
+        got = dev.to_host()
+        dev.free()
+        assert host.layer_loop_off[4] == 0 and host.layer_loop_off[-1] > 0
+        assert np.array_equal(got.layer_loop_off, host.layer_loop_off)
+        assert np.array_equal(got.loop_vert_off, host.loop_vert_off)
+        assert np.array_equal(got.xy, host.xy)
+        assert (got.edge_id is None) == (not eid)
+        if eid:
+            assert np.array_equal(got.edge_id, host.edge_id)
+    lat.slice(edge_ids=True, on_device=True, **kw).free()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        lat.slice(edge_ids=True, on_device=True, **kw).free()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+
+
 def test_host_results_streamed_into_cached_blocks(c1):
     """Host results reuse page-locked blocks: a later call copies each chunk's
     vertices into the largest cached block while it computes the next chunks
