@@ -628,6 +628,9 @@ def main():
                     help="records per staged copy of the footprint kernel (0: 256)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 10M-strut and volume-fraction lines")
+    ap.add_argument("--host-contours", action="store_true",
+                    help="timed steps return the contours in host memory instead of leaving "
+                         "them on the device")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the untimed pass that counts nonzero terms (profiling runs)")
     ap.add_argument("--only", choices=["10M", "vf", "batched", "hatch", "density", "support",
@@ -676,6 +679,10 @@ def main():
     t_up = time.perf_counter() - t_up
 
     def step(flags_time=False):
+        if args.host_contours:   # the contours copied to host memory (pinned blocks)
+            c = lat.slice(**kw, time_kernels=flags_time)
+            st = cs.last_stats()
+            return st, (len(c.loop_vert_off) - 1, c.xy.shape[0])
         c = lat.slice(**kw, on_device=True, time_kernels=flags_time)
         st = cs.last_stats()
         n = (c.n_loops, c.n_verts)
@@ -783,6 +790,7 @@ def main():
             "config": {"workload": cfg["name"], "struts": int(cfg["edges"].shape[0]),
                        "pixel_mm": cfg["pixel"], "layers": cfg["n_layers"],
                        "l2": "inputs larger than L2 (32-byte records x struts)",
+                       "contours": "host memory" if args.host_contours else "device memory",
                        "parallelism": f"{world} GPU(s), layers offset per rank"},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof,
             "roofline_hbm_stages": secondary,
