@@ -142,6 +142,12 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
                         cudaStream_t s);
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                         cudaStream_t s);
+// Numbering of flagged items, the flag being the top bit of word[i]:
+// pos[i] = flagged items before i (every i), list[pos[i]] = i for flagged i
+// (while pos[i] < list_cap; beyond it *status |= ST_CAPACITY), *total_dev =
+// flagged items.
+void scan_flags_list(const uint32_t* word, int64_t n, uint32_t* pos, uint32_t* list,
+                     int64_t list_cap, uint32_t* total_dev, uint32_t* status, cudaStream_t s);
 // Exclusive scan of uint32 counts into int64 offsets.
 void exclusive_scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                                cudaStream_t s);

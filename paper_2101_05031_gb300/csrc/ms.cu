@@ -312,16 +312,16 @@ __device__ __forceinline__ bool is_splitter(uint32_t i, uint32_t pred_i, uint32_
     return (pred_i > i && succ_i > i) || ((i * 2654435761u) >> 27) == 0u;
 }
 
-// For the successor s of every crossing i (i is s's predecessor): flag[s] = 1
-// when s is a splitter, nxt[s] = succ(s) | (splitter << 31), the only array
-// the segment walks read. Thread i reads its own successor and its
-// successor's (records of one contour lie close together), so no separate
-// predecessor array is built. A successor out of range is reported through
-// *status and nothing is written for it; a crossing that is nobody's
-// successor keeps flag 0 (its loop then fails the coverage check).
+// For the successor s of every crossing i (i is s's predecessor): nxt[s] =
+// succ(s) | (s is a splitter) << 31, the only array the segment walks read
+// and the one whose top bits number the splitters. Thread i reads its own
+// successor and its successor's (records of one contour lie close together),
+// so no separate predecessor array is built. A successor out of range is
+// reported through *status and nothing is written for it; a crossing that is
+// nobody's successor keeps nxt = 0, no splitter (its loop then fails the
+// coverage check).
 __global__ void k_split_flags(const Xing* __restrict__ rec, int64_t n,
-                              uint32_t* __restrict__ flag, uint32_t* __restrict__ nxt,
-                              uint32_t* status) {
+                              uint32_t* __restrict__ nxt, uint32_t* status) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t q = rec[i].succ;
@@ -331,21 +331,8 @@ __global__ void k_split_flags(const Xing* __restrict__ rec, int64_t n,
         }
         const uint32_t sc = rec[q].succ;
         const bool sp = is_splitter(q, (uint32_t)i, sc);
-        flag[q] = sp ? 1u : 0u;
         nxt[q] = (sc & 0x7fffffffu) | (sp ? 0x80000000u : 0u);
     }
-}
-
-// spos: exclusive scan of flag. split_id[spos[i]] = i for splitters.
-__global__ void k_split_list(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ spos,
-                             int64_t n, int64_t ns_cap, uint32_t* __restrict__ split_id,
-                             uint32_t* status) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flag[i]) {
-            if ((int64_t)spos[i] < ns_cap) split_id[spos[i]] = (uint32_t)i;
-            else atomicOr(status, ST_CAPACITY);
-        }
 }
 
 // Each splitter walks its segment up to the next splitter (nxt: successor |
@@ -793,14 +780,21 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         CSL_LAUNCH_CHECK("ms emit");
     }
     // ---- loops: splitters, segments, pointer jumping on the splitter graph
-    DevBuf sflag((size_t)n_cross * 4, s), spos((size_t)n_cross * 4, s);
-    DevBuf nxt((size_t)n_cross * 4, s);
-    CSL_CUDA(cudaMemsetAsync(sflag.get(), 0, (size_t)n_cross * 4, s));
+    // nxt[i] = succ(i) | splitter << 31 (0 for a crossing nobody points to);
+    // one scan over its top bits numbers the splitters (spos, for every
+    // crossing) and lists them (split_id) in the same pass
+    DevBuf spos((size_t)n_cross * 4, s), nxt((size_t)n_cross * 4, s);
+    CSL_CUDA(cudaMemsetAsync(nxt.get(), 0, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
-    k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, sflag.as<uint32_t>(),
-                                     nxt.as<uint32_t>(), status);
+    k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, nxt.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms splitter flags");
-    exclusive_scan_u32(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, status + 2, s);
+    // the list's room: every crossing, or a replay's planned count
+    const int64_t ns_cap = replay ? rp->plan->ns : n_cross;
+    DevBuf split_id((size_t)std::max<int64_t>(ns_cap, 1) * 4, s);
+    // a replay whose sizes changed leaves entries unwritten: make them valid ids
+    if (replay) CSL_CUDA(cudaMemsetAsync(split_id.get(), 0, (size_t)ns_cap * 4, s));
+    scan_flags_list(nxt.as<uint32_t>(), n_cross, spos.as<uint32_t>(), split_id.as<uint32_t>(),
+                    ns_cap, status + 2, status, s);
     int64_t ns;
     if (replay) {
         ns = rp->plan->ns;
@@ -813,18 +807,12 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
         ns = head2[2];
         if (rp) rp->plan->ns = ns;
     }
-    DevBuf split_id((size_t)ns * 4, s), seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
-    // a replay whose sizes changed leaves entries unwritten: make them valid ids
-    if (replay) CSL_CUDA(cudaMemsetAsync(split_id.get(), 0, (size_t)ns * 4, s));
+    DevBuf seg_next((size_t)ns * 4, s), seg_len((size_t)ns * 4, s);
     const unsigned gs = grid_for(ns, 256);
-    k_split_list<<<gx, 256, 0, s>>>(sflag.as<uint32_t>(), spos.as<uint32_t>(), n_cross, ns,
-                                    split_id.as<uint32_t>(), status);
-    CSL_LAUNCH_CHECK("ms splitter list");
     k_segments<<<gs, 256, 0, s>>>(nxt.as<uint32_t>(), spos.as<uint32_t>(),
                                   split_id.as<uint32_t>(), ns, n_cross, seg_next.as<uint32_t>(),
                                   seg_len.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms segments");
-    sflag.release();
     nxt.release();
     // short splitter cycles by walking them; long ones by pointer jumping
     DevBuf cm((size_t)ns * 4, s), long_list((size_t)ns * 4, s), long_pos((size_t)ns * 4, s);

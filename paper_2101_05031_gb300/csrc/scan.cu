@@ -119,6 +119,61 @@ __global__ void __launch_bounds__(kThreads) k_block_scan(const T* in, U* out, in
     if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = carry + block_total;
 }
 
+// Flag counts per tile, the flag being the top bit of each word.
+__global__ void __launch_bounds__(kThreads) k_flag_sums(const uint32_t* __restrict__ in, int64_t n,
+                                                        uint32_t* __restrict__ sums) {
+    __shared__ uint32_t warp_tot[kThreads / 32];
+    uint32_t v[kItems];
+    load_items(in, n, (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems, v);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) acc += v[i] >> 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) warp_tot[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += warp_tot[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// pos: exclusive scan of the flags of one tile per block (plus the tile's
+// offset); list[pos[i]] = i for every flagged i.
+__global__ void __launch_bounds__(kThreads) k_flag_scan_list(const uint32_t* __restrict__ in,
+                                                             uint32_t* __restrict__ pos, int64_t n,
+                                                             const uint32_t* __restrict__ offsets,
+                                                             uint32_t* __restrict__ list,
+                                                             int64_t list_cap, uint32_t* total,
+                                                             uint32_t* status) {
+    __shared__ uint32_t block_total;
+    const int64_t first = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    uint32_t v[kItems];
+    load_items(in, n, first, v);
+    uint32_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) mine += v[i] >> 31;
+    const uint32_t off = block_exclusive<uint32_t>(mine, &block_total);
+    const uint32_t carry = offsets ? offsets[blockIdx.x] : 0u;
+    uint32_t r[kItems];
+    uint32_t run = carry + off;
+    bool over = false;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        r[i] = run;
+        if ((v[i] >> 31) && first + i < n) {
+            if ((int64_t)run < list_cap) list[run] = (uint32_t)(first + i);
+            else over = true;
+        }
+        run += v[i] >> 31;
+    }
+    store_items(pos, n, first, r);
+    if (over) atomicOr(status, ST_CAPACITY);
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = carry + block_total;
+}
+
 template <class T, class U>
 void scan_impl(const T* in, U* out, int64_t n, U* total_dev, cudaStream_t s) {
     if (n <= 0) {
@@ -144,6 +199,25 @@ void scan_impl(const T* in, U* out, int64_t n, U* total_dev, cudaStream_t s) {
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
                         cudaStream_t s) {
     scan_impl<uint32_t, uint32_t>(in, out, n, total_dev, s);
+}
+
+void scan_flags_list(const uint32_t* word, int64_t n, uint32_t* pos, uint32_t* list,
+                     int64_t list_cap, uint32_t* total_dev, uint32_t* status, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) CSL_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
+        return;
+    }
+    const int64_t nb = ceil_div(n, kTile);
+    DevBuf sums((size_t)nb * 4, s);
+    if (nb > 1) {
+        k_flag_sums<<<(unsigned)nb, kThreads, 0, s>>>(word, n, sums.as<uint32_t>());
+        CSL_LAUNCH_CHECK("flag sums");
+        scan_impl<uint32_t, uint32_t>(sums.as<uint32_t>(), sums.as<uint32_t>(), nb, nullptr, s);
+    }
+    k_flag_scan_list<<<(unsigned)nb, kThreads, 0, s>>>(word, pos, n,
+                                                       nb > 1 ? sums.as<uint32_t>() : nullptr,
+                                                       list, list_cap, total_dev, status);
+    CSL_LAUNCH_CHECK("flag scan");
 }
 
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
