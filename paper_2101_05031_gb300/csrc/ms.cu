@@ -66,9 +66,10 @@ __device__ __forceinline__ uint32_t spread16(uint32_t x) {
     return x;
 }
 
-// grid: x over (row J, mask word k), y = layer
+// grid: x over (row J, mask word k), y = layer. cnt: the crossings of each
+// edge word (the input of the numbering scan).
 __global__ void k_edge_words(const uint32_t* __restrict__ mask, MsConst c,
-                             uint32_t* __restrict__ ew) {
+                             uint32_t* __restrict__ ew, uint32_t* __restrict__ cnt) {
     const int layer = blockIdx.y;
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (uint32_t)c.H * (uint32_t)c.mwr) return;
@@ -82,13 +83,9 @@ __global__ void k_edge_words(const uint32_t* __restrict__ mask, MsConst c,
     uint2 out;
     out.x = spread16(h) | (spread16(v) << 1);
     out.y = spread16(h >> 16) | (spread16(v >> 16) << 1);
-    reinterpret_cast<uint2*>(ew + (int64_t)layer * c.edge_wpl + (int64_t)J * c.ewr)[k] = out;
-}
-
-__global__ void k_popc(const uint32_t* __restrict__ words, int64_t n, uint32_t* __restrict__ cnt) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        cnt[i] = __popc(words[i]);
+    const int64_t row = (int64_t)layer * c.edge_wpl + (int64_t)J * c.ewr;
+    reinterpret_cast<uint2*>(ew + row)[k] = out;
+    reinterpret_cast<uint2*>(cnt + row)[k] = make_uint2(__popc(out.x), __popc(out.y));
 }
 
 // Crossing numbering: the crossing on the edge with bit `bit` of edge word w
@@ -161,6 +158,28 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
     const int J = J0 + (int)(threadIdx.x / kEmitWords), k = k0 + (int)(threadIdx.x % kEmitWords);
     const uint32_t* m = mask + (int64_t)layer * c.mask_wpl;
     const float* sg = FUSED ? nullptr : sigma + (int64_t)layer * c.nx * c.ny;
+    // this thread's mask words, edge words and prefix sums (of its row, the
+    // next word and the row above), loaded before the staging so that their
+    // latency overlaps it; the other prefixes follow from these
+    const bool live = J <= c.ny && k < c.mwr;
+    const bool last = k + 1 >= c.mwr;
+    uint32_t in0 = 0u, in1 = 0u, up = 0u, up1 = 0u;
+    uint32_t e0 = 0u, e1 = 0u, e2 = 0u, p0 = 0u, u0 = 0u, u1 = 0u, q0 = 0u;
+    if (live) {
+        in0 = m[(int64_t)J * c.mwr + k];
+        in1 = last ? 0u : m[(int64_t)J * c.mwr + k + 1];
+        up = m[(int64_t)(J + 1) * c.mwr + k];          // J + 1 <= ny + 1 < H
+        up1 = last ? 0u : m[(int64_t)(J + 1) * c.mwr + k + 1];
+        const int64_t wb = layer * D.edge_wpl + (int64_t)J * D.ewr + 2 * k;
+        const int64_t wu = wb + D.ewr;
+        e0 = D.ew[wb];
+        e1 = D.ew[wb + 1];
+        e2 = last ? 0u : D.ew[wb + 2];
+        p0 = D.prefix[wb];
+        u0 = D.ew[wu];
+        u1 = D.ew[wu + 1];
+        q0 = D.prefix[wu];
+    }
     if (!FUSED) {   // pixel (i, j) -> s_sig[(j - (J0 - 1)) * kEmitPitch + 4 + i - 32 k0]
         const int ib = 32 * k0 + 4 * (int)threadIdx.x;   // this thread's 4 pixels of each row
         // whole vectors need 16-byte aligned rows (nx % 4 == 0) and 4 pixels inside
@@ -194,25 +213,17 @@ __global__ void __launch_bounds__(256, 6) k_emit(const float* __restrict__ sigma
     auto value_s = [&](int I, int J2) -> float {
         return s_sig[(J2 - J0) * kEmitPitch + (I - 32 * k0) + 3];
     };
-    if (J > c.ny || k >= c.mwr) return;
-    const bool last = k + 1 >= c.mwr;
-    const uint32_t in0 = m[(int64_t)J * c.mwr + k];
-    const uint32_t in1 = last ? 0u : m[(int64_t)J * c.mwr + k + 1];
-    const uint32_t up = m[(int64_t)(J + 1) * c.mwr + k];          // J + 1 <= ny + 1 < H
-    const uint32_t up1 = last ? 0u : m[(int64_t)(J + 1) * c.mwr + k + 1];
+    if (!live) return;
     const uint32_t hb = in0 ^ ((in0 >> 1) | (in1 << 31));          // bottom side of cell I
     const uint32_t vb = in0 ^ up;                                  // left side
     const uint32_t vr = (vb >> 1) | ((in1 ^ up1) << 31);           // right side
     const uint32_t ht = up ^ ((up >> 1) | (up1 << 31));            // top side
     uint32_t active = hb | vb | vr | ht;
     if (!active) return;
-    // edge words (and their prefix sums) of this row's 32 samples, the next
-    // sample, and the row above: every crossing id below comes from registers
-    const int64_t wb = layer * D.edge_wpl + (int64_t)J * D.ewr + 2 * k;
-    const int64_t wu = wb + D.ewr;
-    const uint32_t e0 = D.ew[wb], e1 = D.ew[wb + 1], p0 = D.prefix[wb], p1 = D.prefix[wb + 1];
-    const uint32_t e2 = last ? 0u : D.ew[wb + 2], p2 = last ? 0u : D.prefix[wb + 2];
-    const uint32_t u0 = D.ew[wu], u1 = D.ew[wu + 1], q0 = D.prefix[wu], q1 = D.prefix[wu + 1];
+    // the prefix of a word is its left neighbour's plus that word's crossings:
+    // every crossing id below comes from registers
+    const uint32_t p1 = p0 + __popc(e0), p2 = last ? 0u : p1 + __popc(e1);
+    const uint32_t q1 = q0 + __popc(u0);
     while (active) {
         const int b = __ffs(active) - 1;
         active &= active - 1u;
@@ -317,9 +328,10 @@ __device__ __forceinline__ bool is_splitter(uint32_t i, uint32_t pred_i, uint32_
 // and the one whose top bits number the splitters. Thread i reads its own
 // successor and its successor's (records of one contour lie close together),
 // so no separate predecessor array is built. A successor out of range is
-// reported through *status and nothing is written for it; a crossing that is
-// nobody's successor keeps nxt = 0, no splitter (its loop then fails the
-// coverage check).
+// reported through *status and nothing is written for it. Every crossing is
+// somebody's successor (the entry crossing of its exit cell), so every entry
+// is written; in a replay whose sizes changed, entries left out keep the 0
+// they were cleared to (no splitter).
 __global__ void k_split_flags(const Xing* __restrict__ rec, int64_t n,
                               uint32_t* __restrict__ nxt, uint32_t* status) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -472,11 +484,16 @@ constexpr int kShortCycle = 16;
 constexpr uint32_t kNil = 0xffffffffu;
 
 // cm[t] = the cycle's smallest splitter id when t's cycle closes within
-// kShortCycle steps; otherwise t is appended to the long list.
+// kShortCycle steps; otherwise t is appended to the long list. The head of a
+// short cycle (the splitter holding its smallest id) then walks it once more:
+// rank_start = crossings of the loop before each segment, loop_len at the head.
 __global__ void k_short_cycles(const uint32_t* __restrict__ split_id,
-                               const uint32_t* __restrict__ seg_next, int64_t ns,
+                               const uint32_t* __restrict__ seg_next,
+                               const uint32_t* __restrict__ seg_len, int64_t ns,
                                uint32_t* __restrict__ cm, uint32_t* __restrict__ long_list,
-                               uint32_t* __restrict__ long_pos, uint32_t* __restrict__ n_long) {
+                               uint32_t* __restrict__ long_pos, uint32_t* __restrict__ n_long,
+                               uint32_t* __restrict__ rank_start,
+                               uint32_t* __restrict__ loop_len) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ns;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -494,6 +511,16 @@ __global__ void k_short_cycles(const uint32_t* __restrict__ split_id,
             is_long = v != (uint32_t)t;
             cm[t] = is_long ? kNil : mn;
             long_pos[t] = kNil;
+            if (!is_long && mn == split_id[t]) {   // the head: rank the cycle's segments
+                uint32_t acc = 0, w = (uint32_t)t;
+                int m = 0;
+                do {
+                    rank_start[w] = acc;
+                    acc += seg_len[w];
+                    w = seg_next[w];
+                } while (w != (uint32_t)t && ++m < kShortCycle);
+                loop_len[t] = acc;
+            }
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, is_long);
         uint32_t pos = 0;
@@ -504,26 +531,6 @@ __global__ void k_short_cycles(const uint32_t* __restrict__ split_id,
             long_list[q] = (uint32_t)t;
             long_pos[t] = q;
         }
-    }
-}
-
-// The head of each short cycle walks it: rank_start = crossings of the loop
-// before the segment, loop_len at the head.
-__global__ void k_short_ranks(const uint32_t* __restrict__ cm, const uint32_t* __restrict__ split_id,
-                              const uint32_t* __restrict__ seg_next,
-                              const uint32_t* __restrict__ seg_len, int64_t ns,
-                              uint32_t* __restrict__ rank_start, uint32_t* __restrict__ loop_len) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (cm[t] == kNil || cm[t] != split_id[t]) continue;   // long, or not a head
-        uint32_t acc = 0, v = (uint32_t)t;
-        int n = 0;
-        do {
-            rank_start[v] = acc;
-            acc += seg_len[v];
-            v = seg_next[v];
-        } while (v != (uint32_t)t && ++n < kShortCycle);
-        loop_len[t] = acc;
     }
 }
 
@@ -711,11 +718,9 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     {
         const int64_t n_thr = (int64_t)c.H * c.mwr;
         dim3 grid((unsigned)ceil_div(n_thr, 256), (unsigned)g.n_layers);
-        k_edge_words<<<grid, 256, 0, s>>>(mask, c, ew.as<uint32_t>());
+        k_edge_words<<<grid, 256, 0, s>>>(mask, c, ew.as<uint32_t>(), prefix.as<uint32_t>());
         CSL_LAUNCH_CHECK("ms edge words");
     }
-    k_popc<<<grid_for(n_words, 256), 256, 0, s>>>(ew.as<uint32_t>(), n_words, prefix.as<uint32_t>());
-    CSL_LAUNCH_CHECK("ms popc");
     exclusive_scan_u32(prefix.as<uint32_t>(), prefix.as<uint32_t>(), n_words, status + 1, s);
     int64_t n_cross;
     if (replay) {
@@ -784,7 +789,10 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     // one scan over its top bits numbers the splitters (spos, for every
     // crossing) and lists them (split_id) in the same pass
     DevBuf spos((size_t)n_cross * 4, s), nxt((size_t)n_cross * 4, s);
-    CSL_CUDA(cudaMemsetAsync(nxt.get(), 0, (size_t)n_cross * 4, s));
+    // every crossing is the successor of the crossing through which the
+    // contour enters its cell, so every entry is written; a replay whose sizes
+    // changed may leave some out: there they start as 0 (no splitter)
+    if (rp) CSL_CUDA(cudaMemsetAsync(nxt.get(), 0, (size_t)n_cross * 4, s));
     const unsigned gx = grid_for(n_cross, 256);
     k_split_flags<<<gx, 256, 0, s>>>(rec.as<Xing>(), n_cross, nxt.as<uint32_t>(), status);
     CSL_LAUNCH_CHECK("ms splitter flags");
@@ -818,14 +826,11 @@ void contours_chunk(const ChunkGeom& g, double C, const float* sigma, const uint
     DevBuf cm((size_t)ns * 4, s), long_list((size_t)ns * 4, s), long_pos((size_t)ns * 4, s);
     DevBuf rank_start((size_t)ns * 4, s), loop_len((size_t)ns * 4, s);
     if (replay) CSL_CUDA(cudaMemsetAsync(long_list.get(), 0, (size_t)ns * 4, s));
-    k_short_cycles<<<gs, 256, 0, s>>>(split_id.as<uint32_t>(), seg_next.as<uint32_t>(), ns,
-                                      cm.as<uint32_t>(), long_list.as<uint32_t>(),
-                                      long_pos.as<uint32_t>(), n_long);
+    k_short_cycles<<<gs, 256, 0, s>>>(split_id.as<uint32_t>(), seg_next.as<uint32_t>(),
+                                      seg_len.as<uint32_t>(), ns, cm.as<uint32_t>(),
+                                      long_list.as<uint32_t>(), long_pos.as<uint32_t>(), n_long,
+                                      rank_start.as<uint32_t>(), loop_len.as<uint32_t>());
     CSL_LAUNCH_CHECK("ms short cycles");
-    k_short_ranks<<<gs, 256, 0, s>>>(cm.as<uint32_t>(), split_id.as<uint32_t>(),
-                                     seg_next.as<uint32_t>(), seg_len.as<uint32_t>(), ns,
-                                     rank_start.as<uint32_t>(), loop_len.as<uint32_t>());
-    CSL_LAUNCH_CHECK("ms short ranks");
     int64_t nl;
     if (replay) {
         nl = rp->plan->nl;
