@@ -33,6 +33,7 @@ struct BinConst {
     float fx0, fy0, inv_tile, mxy, mz;
     float halo;   // 0, or the pixel size: the low corner also reaches the tile below
     int32_t ntx, nty, n_tiles;
+    int32_t tb;   // > 0: entries carry slab << tb | tile and are sorted by the tile bits
 };
 
 struct SlabInfo {
@@ -165,7 +166,7 @@ __global__ void k_bin_emit(const float4* __restrict__ bxy, const float* __restri
         if (sl.cand_off + i >= cap_cand) continue;   // a replay whose sizes changed (flagged)
         int64_t p = pair_off[sl.cand_off + i];
         if (p + (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1) > cap_pairs) continue;
-        uint32_t kbase = (uint32_t)s * (uint32_t)c.n_tiles;
+        const uint32_t kbase = c.tb ? (uint32_t)s << c.tb : (uint32_t)s * (uint32_t)c.n_tiles;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
                 keys[p] = kbase + (uint32_t)(ty * c.ntx + tx);
@@ -175,13 +176,17 @@ __global__ void k_bin_emit(const float4* __restrict__ bxy, const float* __restri
     }
 }
 
-__global__ void k_list_bounds(const uint32_t* __restrict__ keys, int64_t n,
+// [start, end) of every (slab, tile) run, at the bin index slab * n_tiles +
+// tile (keys in either form of BinConst::tb).
+__global__ void k_list_bounds(const uint32_t* __restrict__ keys, int64_t n, int tb, int n_tiles,
                               uint32_t* __restrict__ start, uint32_t* __restrict__ end) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-        if (i == 0 || keys[i - 1] != k) start[k] = (uint32_t)i;
-        if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+        const uint32_t k = keys[i];
+        const uint32_t b =
+            tb ? (k >> tb) * (uint32_t)n_tiles + (k & ((1u << tb) - 1u)) : k;
+        if (i == 0 || keys[i - 1] != k) start[b] = (uint32_t)i;
+        if (i == n - 1 || keys[i + 1] != k) end[b] = (uint32_t)(i + 1);
     }
 }
 
@@ -222,6 +227,13 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     c.ntx = g.ntx;
     c.nty = g.nty;
     c.n_tiles = n_tiles;
+    // The entries are emitted slab by slab, so a stable sort by the tile alone
+    // leaves every (slab, tile) run contiguous (tiles in order, slabs in order
+    // within a tile) with its records in emission order: the same lists as a
+    // sort by (slab, tile), in fewer passes. Keys then carry slab << tb | tile.
+    const int tb = bits_for(n_tiles);
+    c.tb = ((int64_t)g.n_slabs << tb) <= 0xffffffffLL && tb < bits_for(n_keys) ? std::max(tb, 1)
+                                                                              : 0;
 
     std::vector<SlabInfo> hs(g.n_slabs);
     DevBuf slabs(sizeof(SlabInfo) * g.n_slabs, s);
@@ -292,10 +304,10 @@ void bin_chunk(const csl_lattice* L, const ChunkGeom& g, SlabBins& out, cudaStre
     {
         DevBuf tk((size_t)n_pairs * 4, s), tv((size_t)n_pairs * 4, s);
         radix_sort_pairs(out.keys.as<uint32_t>(), out.vals.as<uint32_t>(), tk.as<uint32_t>(),
-                         tv.as<uint32_t>(), n_pairs, bits_for(n_keys), s);
+                         tv.as<uint32_t>(), n_pairs, c.tb ? c.tb : bits_for(n_keys), s);
     }
-    k_list_bounds<<<grid_for(n_pairs, 256), 256, 0, s>>>(out.keys.as<uint32_t>(), n_pairs,
-                                                        out.tile_start.as<uint32_t>(),
+    k_list_bounds<<<grid_for(n_pairs, 256), 256, 0, s>>>(out.keys.as<uint32_t>(), n_pairs, c.tb,
+                                                        n_tiles, out.tile_start.as<uint32_t>(),
                                                         out.tile_end.as<uint32_t>());
     CSL_LAUNCH_CHECK("list bounds");
     // the records themselves in entry order, so that the field kernel stages a
