@@ -180,24 +180,42 @@ __global__ void k_po_vol0(const int4* __restrict__ tets, int64_t n, const double
 // One colour: a warp per vertex of the list (no two share an edge). The
 // lanes share the edge terms and the incident tetrahedra's checks; the trials
 // of the backtracking run in order.
+//
+// A vertex's move depends only on its own position and its neighbours' (all
+// the vertices of its tetrahedra) besides constants; so a vertex that did not
+// move at its last visit (calm_at: that colour step) and whose star has not
+// moved since (moved_at of it and of its neighbours older than that step)
+// would not move now either, and is skipped: the result of the sequential
+// sweep exactly, without re-evaluating the calm part of the mesh.
 __global__ void __launch_bounds__(kPoThreads)
 k_po_move(const int32_t* __restrict__ list, int64_t n, double* __restrict__ pos,
           const double* __restrict__ o, const double* __restrict__ tau0,
           const int64_t* __restrict__ e_off, const int32_t* __restrict__ nbr,
           const double* __restrict__ rad, const int64_t* __restrict__ vt_off,
           const int32_t* __restrict__ vt, const int4* __restrict__ tets,
-          const double* __restrict__ vol0, PoConst c, unsigned int* moves) {
+          const double* __restrict__ vol0, PoConst c, int32_t step,
+          int32_t* __restrict__ moved_at, int32_t* __restrict__ calm_at, unsigned int* moves) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const int32_t v = list[i];
         const int64_t eb = e_off[v], ee = e_off[v + 1];
+        const int32_t ca = calm_at[v];
+        if (ca >= 0 && moved_at[v] < ca) {   // calm before: has the star moved since?
+            bool moved = false;
+            for (int64_t q = eb + lane; q < ee; q += 32) moved |= moved_at[nbr[q]] > ca;
+            if (!__any_sync(0xffffffffu, moved)) continue;
+        }
         double* pv = pos + 3 * (int64_t)v;
         const double p0 = pv[0], p1 = pv[1], p2 = pv[2];
         double grad[3];
         const double J0 = warp_J(p0, p1, p2, nbr, rad, eb, ee, pos, c, grad);
         const double gn = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
-        if (gn == 0.0) continue;
+        bool went = false;
+        if (gn == 0.0) {
+            if (lane == 0) calm_at[v] = step;
+            continue;
+        }
         const double u[3] = {grad[0] / gn, grad[1] / gn, grad[2] / gn};
         const double* ov = o + 3 * (int64_t)v;
         const double rb = c.ball * tau0[v];
@@ -225,11 +243,14 @@ k_po_move(const int32_t* __restrict__ list, int64_t n, double* __restrict__ pos,
                     pv[0] = cand[0];
                     pv[1] = cand[1];
                     pv[2] = cand[2];
+                    moved_at[v] = step;
                     atomicAdd(moves, 1u);
                 }
+                went = true;
                 break;
             }
         }
+        if (!went && lane == 0) calm_at[v] = step;
     }
 }
 
@@ -475,6 +496,11 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
         DevBuf d_pos, d_o, d_tau, d_eoff, d_nbr, d_rad, d_vtoff, d_vt, d_tets, d_vol0, d_list;
         DevBuf d_edges, d_er, d_part((size_t)152 * 2 * 4 * sizeof(double), s), d_tot(64, s);
         DevBuf d_moves(16, s);
+        // colour step of each vertex's last move and of its last visit without one
+        DevBuf d_moved_at(std::max<size_t>((size_t)n_nodes * 4, 16), s),
+            d_calm_at(std::max<size_t>((size_t)n_nodes * 4, 16), s);
+        CSL_CUDA(cudaMemsetAsync(d_moved_at.get(), 0xff, d_moved_at.size(), s));
+        CSL_CUDA(cudaMemsetAsync(d_calm_at.get(), 0xff, d_calm_at.size(), s));
         upload(d_pos, h_pos, s);
         upload(d_o, h_pos, s);
         upload(d_eoff, e_off, s);
@@ -512,7 +538,8 @@ extern "C" csl_status csl_support_optimize(float* nodes, int64_t n_nodes, const 
                     d_list.as<int32_t>() + b, n, d_pos.as<double>(), d_o.as<double>(),
                     d_tau.as<double>(), d_eoff.as<int64_t>(), d_nbr.as<int32_t>(),
                     d_rad.as<double>(), d_vtoff.as<int64_t>(), d_vt.as<int32_t>(),
-                    d_tets.as<int4>(), d_vol0.as<double>(), c, d_moves.as<unsigned int>());
+                    d_tets.as<int4>(), d_vol0.as<double>(), c, round * n_col + k,
+                    d_moved_at.as<int32_t>(), d_calm_at.as<int32_t>(), d_moves.as<unsigned int>());
                 CSL_LAUNCH_CHECK("vertex moves");
             }
             unsigned int moved = 0;
