@@ -420,7 +420,9 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                     __syncwarp();   // the next group overwrites the footprints
                 }
             }
-            __syncthreads();   // the next chunk reuses s_rec
+            // the next chunk reuses s_rec; after the last one each warp goes on to
+            // its own plane (no other warp's data) without waiting
+            if (c0 + (uint32_t)c.K < end) __syncthreads();
         }
     }
     if (COUNT) {   // n_pairs[0]: nonzero terms, n_pairs[1]: evaluated terms
