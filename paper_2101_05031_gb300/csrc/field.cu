@@ -160,7 +160,10 @@ __device__ __forceinline__ bool field_tile(const csl_rec* __restrict__ recs,
                     }
                 }
             }
-            __syncthreads();   // the next chunk (or tile) reuses s_rec and s_mask
+            // the next chunk reuses s_rec and s_mask; after the last one each warp
+            // goes on to its own pixels without waiting (a persistent caller
+            // synchronises before the next item)
+            if (c0 + (uint32_t)kFieldThreads < end) __syncthreads();
         }
     }
     if (COUNT) {   // n_pairs[0]: nonzero terms, n_pairs[1]: evaluated terms
