@@ -68,15 +68,28 @@ struct FpConst {
     float fx0, fy0;      // grid origin as the contour stage takes it (float)
 };
 
-// One (record, layer) footprint, 16 bytes: the span of row (or column) u
-// starts at ceil(c0 + u c1); w1 = record (< 2^14) | interior << 14 | mode << 15
-// | W << 16 | passes << 24,
-// geom = u0 | n_rows << 8 | v0 << 16 | v1 << 24 (u: rows in row mode, v: the
-// pixels along them, [v0, v1] the clipped box).
+// One (record, layer) footprint with the constants its walk uses, built by
+// one lane per record (so the set-up is paid once per 16 records and layer
+// rather than once per footprint by the whole warp), 80 bytes: the span of
+// row (or column) u starts at ceil(c0 + u c1) and is W pixels wide, clipped to
+// [v0, v1]; weff = min(W, v1 - v0 + 1); inv_w = 1 / weff (approximate: the
+// row index floor((k + 1/2) inv_w) is exact with it for these small
+// integers); pixel coordinates relative to v_s are dx = i px + ox, dy = j px
+// + oy, dz (and dz u_z); wI = w / R^4 (times 16/15 for the interior closed
+// form); bits = record (< 2^14) | interior << 14 | mode << 15.
 struct __align__(16) Foot {
-    float c0, c1;
-    uint32_t w1, geom;
+    float inv_w, weff, u0, n_rows;
+    float c0, c1, v0, v1;
+    float Wf, ox, oy, dz;
+    float dzuz, wI, ux, uy;
+    float uz, len;
+    uint32_t bits, passes;
 };
+static_assert(sizeof(Foot) == 80, "Foot is five 16-byte words");
+
+// records per footprint-building round (one lane each); the warp's queue holds
+// one round's footprints
+constexpr int kFootGroup = 16;
 
 // Footprint of record (A, B) in layer plane zl of a T x T tile; false when
 // the edge's support misses the tile in that plane.
@@ -134,19 +147,35 @@ __device__ __forceinline__ bool make_foot(const float4 A, const float4 B, float 
         f.c1 = 0.0f;
         W = v1 - v0 + 1;
     }
-    W = min(W, 255);
     const int weff = min(W, v1 - v0 + 1);
     const int n_rows = u1 - u0 + 1;
-    const int passes = (n_rows * weff + 31) >> 5;
-    f.w1 = (uint32_t)rec | ((uint32_t)interior << 14) | ((uint32_t)rows << 15) |
-           ((uint32_t)W << 16) | ((uint32_t)passes << 24);
-    f.geom = (uint32_t)u0 | ((uint32_t)n_rows << 8) | ((uint32_t)v0 << 16) | ((uint32_t)v1 << 24);
+    f.weff = (float)weff;
+    f.inv_w = __fdividef(1.0f, f.weff);
+    f.u0 = (float)u0;
+    f.n_rows = (float)n_rows;
+    f.v0 = (float)v0;
+    f.v1 = (float)v1;
+    f.Wf = (float)W;
+    f.ox = fmaf(0.5f, c.fpx, -ax);
+    f.oy = fmaf(0.5f, c.fpx, -ay);
+    f.dz = zl - az;
+    f.dzuz = f.dz * uz;
+    f.wI = interior ? B.w * (16.0f / 15.0f) : B.w;
+    f.ux = ux;
+    f.uy = uy;
+    f.uz = uz;
+    f.len = len;
+    f.bits = (uint32_t)rec | ((uint32_t)interior << 14) | ((uint32_t)rows << 15);
+    f.passes = (uint32_t)((n_rows * weff + 31) >> 5);
     return true;
 }
 
-template <int T>
-constexpr int plane_pitch() {   // row pitch of a Sigma plane in shared memory (floats)
-    return T + 8;
+// Row pitch of a Sigma plane in shared memory (floats): T + 1 puts the rows of
+// a column-mode footprint in distinct banks; the fused pass's planes have T + 1
+// rows, so its pitch keeps the planes 16-byte multiples.
+template <int T, bool FUSED>
+constexpr int plane_pitch() {
+    return FUSED ? T + 8 : T + 1;
 }
 
 // The passes of one footprint: lane k of pass p takes index p * 32 + k of the
@@ -157,53 +186,40 @@ constexpr int plane_pitch() {   // row pitch of a Sigma plane in shared memory (
 // pixel within R has its whole chord [t0 - w, t0 + w] on the edge, where the
 // quartic's integral is (16/15) w^5 (the 3-point rule's value at m = 0, h = w).
 template <int T, bool ROWS, bool INTERIOR, bool COUNT, bool FUSED>
-__device__ __forceinline__ void walk_foot(const Foot& fq, const float4 A, const float4 B,
-                                          const float2 An, float zl, float* __restrict__ sig_l,
-                                          const FpConst& c, int lane, uint32_t& n_nonzero,
-                                          uint32_t& n_eval) {
-    constexpr float P = (float)plane_pitch<T>();
-    const float Wf = (float)((fq.w1 >> 16) & 0xffu);
-    const int passes = (int)(fq.w1 >> 24);
-    const float u0 = (float)(fq.geom & 0xffu);
-    const float n_rows = (float)((fq.geom >> 8) & 0xffu);
-    const float v0 = (float)((fq.geom >> 16) & 0xffu);
-    const float v1 = (float)(fq.geom >> 24);
-    const float weff = fminf(Wf, v1 - v0 + 1.0f);
-    const float inv_w = __fdividef(1.0f, weff);   // floor((k + 1/2) / weff) is exact with it
-    const float half_w = 0.5f * inv_w;
-    const float ox = fmaf(0.5f, c.fpx, -A.x), oy = fmaf(0.5f, c.fpx, -A.y);
+__device__ __forceinline__ void walk_foot(const Foot& fq, const float2 An,
+                                          float* __restrict__ sig_l, const FpConst& c, int lane,
+                                          uint32_t& n_nonzero, uint32_t& n_eval) {
+    constexpr float P = (float)plane_pitch<T, FUSED>();
+    const float half_w = 0.5f * fq.inv_w;
     // the fused pass's halo (column T, row T) in the next tiles' frames (An: v_s
     // relative to their corners), so that its values are the ones those tiles
     // compute for their first column and row, bit for bit
     const float oxn = FUSED ? fmaf(0.5f, c.fpx, -An.x) : 0.0f;
     const float oyn = FUSED ? fmaf(0.5f, c.fpx, -An.y) : 0.0f;
-    const float dz = zl - A.z;
-    const float dzuz = dz * B.y;
-    const float wI = INTERIOR ? B.w * (16.0f / 15.0f) : B.w;
-    for (int p = 0; p < passes; ++p) {
-        const float idx = (float)(p * 32 + lane);
-        const float rr = floorf(fmaf(idx, inv_w, half_w));
-        const float kk = fmaf(-rr, weff, idx);
-        const float u = u0 + rr;
+    float idx = (float)lane;
+    for (uint32_t p = 0; p < fq.passes; ++p, idx += 32.0f) {
+        const float rr = floorf(fmaf(idx, fq.inv_w, half_w));
+        const float kk = fmaf(-rr, fq.weff, idx);
+        const float u = fq.u0 + rr;
         const float s = ceilf(fmaf(u, fq.c1, fq.c0));
-        const float v = fmaxf(s, v0) + kk;
-        const bool valid = rr < n_rows && v <= v1 && v < s + Wf;
+        const float v = fmaxf(s, fq.v0) + kk;
+        const bool valid = rr < fq.n_rows && v <= fq.v1 && v < s + fq.Wf;
         const float xi = ROWS ? v : u, yj = ROWS ? u : v;
-        float dx = fmaf(xi, c.fpx, ox), dy = fmaf(yj, c.fpx, oy);
+        float dx = fmaf(xi, c.fpx, fq.ox), dy = fmaf(yj, c.fpx, fq.oy);
         if (FUSED) {
             if (xi == (float)T) dx = fmaf(0.0f, c.fpx, oxn);
             if (yj == (float)T) dy = fmaf(0.0f, c.fpx, oyn);
         }
-        const float t0 = fmaf(dx, A.w, fmaf(dy, B.x, dzuz));
-        const float ex = fmaf(-t0, A.w, dx);
-        const float ey = fmaf(-t0, B.x, dy);
-        const float ez = fmaf(-t0, B.y, dz);
+        const float t0 = fmaf(dx, fq.ux, fmaf(dy, fq.uy, fq.dzuz));
+        const float ex = fmaf(-t0, fq.ux, dx);
+        const float ey = fmaf(-t0, fq.uy, dy);
+        const float ez = fmaf(-t0, fq.uz, fq.dz);
         const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float h2 = fmaxf(c.R2 - d2, 0.0f);
-        const float I = INTERIOR ? (h2 * h2) * sqrt_approx(h2) : segment_term_R4(t0, h2, B.z);
+        const float I = INTERIOR ? (h2 * h2) * sqrt_approx(h2) : segment_term_R4(t0, h2, fq.len);
         if (valid) {
             float* q2 = sig_l + (int)fmaf(yj, P, xi);
-            *q2 = fmaf(wI, I, *q2);
+            *q2 = fmaf(fq.wI, I, *q2);
         }
         if (COUNT) {   // every lane of the pass is evaluated
             n_nonzero += valid && I > 0.0f;
@@ -227,7 +243,7 @@ template <int T>
 __device__ __forceinline__ void fused_epilogue(const float* __restrict__ sig_l, const FpConst& c,
                                                int tx, int ty, int tile, int64_t lg, int lane,
                                                unsigned char* scratch) {
-    constexpr int P = plane_pitch<T>();
+    constexpr int P = plane_pitch<T, true>();
     uint64_t* s_in = reinterpret_cast<uint64_t*>(scratch);           // rows -1 .. T
     uint16_t* s_roff = reinterpret_cast<uint16_t*>(scratch + (T + 2) * 8);
     const int gx = tx * T, gy = ty * T;
@@ -333,7 +349,7 @@ __device__ __forceinline__ void fused_epilogue(const float* __restrict__ sig_l, 
 }
 
 // One (tile, slab) of the field. Shared memory: S Sigma planes of T rows,
-// then K staged records, then 32 footprints per warp.
+// then K staged records, then kFootGroup footprints per warp.
 template <int T, int S, bool COUNT, bool FUSED>
 __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                                               const uint32_t* __restrict__ tstart,
@@ -343,7 +359,7 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
                                               unsigned long long* __restrict__ n_pairs, int tile,
                                               int slab, unsigned char* smem, uint64_t* bar,
                                               uint32_t& phase) {
-    constexpr int P = plane_pitch<T>();
+    constexpr int P = plane_pitch<T, FUSED>();
     constexpr int ROWS = FUSED ? T + 1 : T;   // the fused pass also evaluates the next row
     float* s_sig = reinterpret_cast<float*>(smem);
     float4* s_rec = reinterpret_cast<float4*>(smem + (size_t)S * ROWS * P * sizeof(float));
@@ -362,7 +378,7 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
     float* sig_l = s_sig + l * ROWS * P;
     for (int q = lane; q < ROWS * P / 4; q += 32)
         reinterpret_cast<float4*>(sig_l)[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    Foot* my_foot = s_foot + warp * 32;
+    Foot* my_foot = s_foot + warp * kFootGroup;
     uint32_t n_nonzero = 0, n_eval = 0;
     const float zl = (float)l * c.fdz;
 
@@ -396,25 +412,25 @@ __device__ __forceinline__ bool field_tile_fp(const csl_rec* __restrict__ recs,
             }
             __syncthreads();
             if (l < nl) {
-                for (int r0 = 0; r0 < cnt; r0 += 32) {
+                for (int r0 = 0; r0 < cnt; r0 += kFootGroup) {
                     const int r = r0 + lane;
                     Foot f;
-                    const bool ok = r < cnt && make_foot<T, FUSED ? T : T - 1>(
-                                                   s_rec[2 * r], s_rec[2 * r + 1], zl, r, c, f);
+                    const bool ok = lane < kFootGroup && r < cnt &&
+                                    make_foot<T, FUSED ? T : T - 1>(s_rec[2 * r], s_rec[2 * r + 1],
+                                                                    zl, r, c, f);
                     const uint32_t ball = __ballot_sync(0xffffffffu, ok);
                     if (ok) my_foot[__popc(ball & ((1u << lane) - 1u))] = f;
                     __syncwarp();
                     const int n = __popc(ball);
                     for (int q = 0; q < n; ++q) {
                         const Foot fq = my_foot[q];
-                        const int rec = (int)(fq.w1 & 0x3fffu);
-                        const float4 A = s_rec[2 * rec], B = s_rec[2 * rec + 1];
-                        const float2 An = FUSED ? s_recn[rec] : make_float2(0.0f, 0.0f);
-                        switch ((fq.w1 >> 14) & 3u) {   // interior | rows << 1, warp-uniform
-                            case 0: walk_foot<T, false, false, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            case 1: walk_foot<T, false, true, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            case 2: walk_foot<T, true, false, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
-                            default: walk_foot<T, true, true, COUNT, FUSED>(fq, A, B, An, zl, sig_l, c, lane, n_nonzero, n_eval); break;
+                        const float2 An =
+                            FUSED ? s_recn[fq.bits & 0x3fffu] : make_float2(0.0f, 0.0f);
+                        switch ((fq.bits >> 14) & 3u) {   // interior | rows << 1, warp-uniform
+                            case 0: walk_foot<T, false, false, COUNT, FUSED>(fq, An, sig_l, c, lane, n_nonzero, n_eval); break;
+                            case 1: walk_foot<T, false, true, COUNT, FUSED>(fq, An, sig_l, c, lane, n_nonzero, n_eval); break;
+                            case 2: walk_foot<T, true, false, COUNT, FUSED>(fq, An, sig_l, c, lane, n_nonzero, n_eval); break;
+                            default: walk_foot<T, true, true, COUNT, FUSED>(fq, An, sig_l, c, lane, n_nonzero, n_eval); break;
                         }
                     }
                     __syncwarp();   // the next group overwrites the footprints
@@ -546,9 +562,9 @@ k_field_fp_batch(const FpJob* __restrict__ jobs, const uint2* __restrict__ items
 
 template <int T, int S, bool FUSED>
 size_t fp_smem_bytes(int K) {
-    return (size_t)S * (FUSED ? T + 1 : T) * plane_pitch<T>() * sizeof(float) +
+    return (size_t)S * (FUSED ? T + 1 : T) * plane_pitch<T, FUSED>() * sizeof(float) +
            (size_t)K * sizeof(csl_rec) + (FUSED ? (size_t)K * sizeof(float2) : 0) +
-           (size_t)S * 32 * sizeof(Foot);
+           (size_t)S * kFootGroup * sizeof(Foot);
 }
 
 template <int T, int S, bool COUNT, bool FUSED>
