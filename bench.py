@@ -41,8 +41,8 @@ NCU_FIELD = {
               "dram_bytes_per_pixel_layer": 1.2835e9 / (64 * 2000 * 2000),
               "profile": "profiles/k_field_graded-10M.txt"},
     "footprint": {"kernel": "k_field_fp",
-                  "executed_frac": (2 * 2876.6 + 1136.9 + 1613.3) / (152 * 128 * 2),
-                  "dram_bytes_per_pixel_layer": (0.717973e9 + 4.252283e9) / (264 * 2000 * 2000),
+                  "executed_frac": (2 * 3131.6 + 1369.7 + 1618.9) / (152 * 128 * 2),
+                  "dram_bytes_per_pixel_layer": (0.729793e9 + 4.292423e9) / (264 * 2000 * 2000),
                   "profile": "profiles/k_field_fp_graded-10M.txt"},
 }
 HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
