@@ -71,3 +71,26 @@ def test_streamed_lattice_serves_slicing_only():
     with pytest.raises(cs.CslError) as e:
         st.support_metrics()
     assert e.value.code == 6
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_streamed_chunk_buffers_reused_equal_resident(on_device):
+    """Two chunks in flight with the library's own Sigma and mask buffers:
+    chunk k + 2 reuses chunk k's buffers once its contours (on their own
+    stream) are done. Ten 2-layer chunks, contours (host or device output)
+    bit-identical to the device-resident lattice's."""
+    import paper_2101_05031_gb300 as cs
+    cfg = synth.config(1)
+    res = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"])
+    st = cs.Lattice(cfg["nodes"], cfg["edges"], cfg["radius"], R=cfg["R"], host_resident=True,
+                    batch_edges=300)
+    kw = dict(z0=cfg["z0"], dz=cfg["dz"], n_layers=20, x0=cfg["x0"], y0=cfg["y0"],
+              nx=cfg["nx"], ny=cfg["ny"], pixel=cfg["pixel"], edge_ids=True, slab=2,
+              chunk_layers=2, on_device=on_device)
+    a = res.slice(**kw)
+    b = st.slice(**kw)
+    if on_device:
+        a, b = a.to_host(), b.to_host()
+    for f in ("layer_loop_off", "loop_vert_off", "xy", "edge_id"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    assert a.xy.shape[0] > 0
