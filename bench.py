@@ -45,6 +45,22 @@ NCU_FIELD = {
                   "dram_bytes_per_pixel_layer": (0.729793e9 + 4.292423e9) / (264 * 2000 * 2000),
                   "profile": "profiles/k_field_fp_graded-10M.txt"},
 }
+# The volume fraction's FP32 work beyond the field term: per sample, the
+# sigmoid and the mean (forward), the sigmoid and alpha (the adjoint's pass 1);
+# per term of the adjoint's pass 2 (coordinates, the clipped chord, the 3-point
+# moments M0..M2 and I, and the 7 partials), counting FMA as 2 and add, sub and
+# mul as 1, as written in its kernel.
+VF_FLOPS_PER_SAMPLE = 4
+VF_GRAD_FLOPS_PER_SAMPLE = 8
+VF_GRAD_FLOPS_PER_TERM = 124
+# Executed FP32 fractions of the volume-fraction kernels from one ncu capture
+# each on the 1M-strut Freudenthal lattice: FFMA (2 flops), FADD and FMUL
+# thread instructions per cycle over the FP32 peak per cycle.
+NCU_VF = {"forward": {"kernel": "k_field",
+                      "executed_frac": (2 * 4094.3 + 1978.2 + 3107.9) / (152 * 128 * 2)},
+          "backward": {"kernel": "k_vf_grad",
+                       "executed_frac": (2 * 2256.0 + 1117.7 + 2062.3) / (152 * 128 * 2)},
+          "profile": "profiles/k_vf_grad_freudenthal-1M.txt"}
 HBM_GBS = 6772.9       # measured copy bandwidth of the GPU
 # algorithmic bytes of the HBM-bound stages
 BIN_BYTES_PER_WINDOW_RECORD = 24   # xy box (16) + z range (8) of a record read per slab window
@@ -288,6 +304,46 @@ def run_vf(steps, warmup):
     fwd = _event_ms(lambda: volume_fraction(lat, cells, out=vf), steps, warmup, stream)
     bwd = _event_ms(lambda: volume_fraction_backward(lat, cells, g), steps, warmup, stream)
     samples = d[0] * d[1] * d[2] * cells["m"] ** 3
+    # FP32 roofline. The m^3 samples of every cell are the pixels of a grid of
+    # pitch h/m whose layers lie every h/m from half a pitch above the origin,
+    # so the slicing kernel's exact counting pass on that grid counts the
+    # nonzero (sample, strut) terms the forward evaluates (36 flops each, plus
+    # the sigmoid and the mean per sample). The backward recomputes them (its
+    # pass 1) and then evaluates the moments and the 7 partials only where the
+    # sigmoid has not saturated, a thin shell around the iso-surface whose
+    # term count the library does not report: its algorithmic figure here is
+    # pass 1 alone (a lower bound), beside ncu's executed FP32 fraction.
+    m = cells["m"]
+    pitch = cells["h"] / m
+    lat.slice(z0=cells["origin"][2] + 0.5 * pitch, dz=pitch, n_layers=d[2] * m,
+              x0=cells["origin"][0], y0=cells["origin"][1], nx=d[0] * m, ny=d[1] * m,
+              pixel=pitch, contours=False, count_pairs=True)
+    pairs = int(cs.last_stats().contributing_pairs)
+    peak = N_SM * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    f_fwd = pairs * F_PAIR + samples * VF_FLOPS_PER_SAMPLE
+    f_bwd1 = pairs * F_PAIR + samples * VF_GRAD_FLOPS_PER_SAMPLE
+    roof = {
+        "forward": {"bound": "alu", "achieved": f_fwd / (fwd / 1e3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "frac": f_fwd / (fwd / 1e3) / 1e12 / peak,
+                    "nonzero_terms": pairs, "flops_per_term": F_PAIR,
+                    "flops_per_sample": VF_FLOPS_PER_SAMPLE,
+                    "duration_basis": "CUDA events around the whole forward call (binning, "
+                                      "field kernel, per-cell mean)",
+                    "executed_frac_ncu": NCU_VF["forward"]["executed_frac"],
+                    "executed_kernel": NCU_VF["forward"]["kernel"]},
+        "backward": {"bound": "alu", "achieved_lower_bound": f_bwd1 / (bwd / 1e3) / 1e12,
+                     "peak": peak, "unit": "TFLOP/s",
+                     "frac_lower_bound": f_bwd1 / (bwd / 1e3) / 1e12 / peak,
+                     "flops_per_term_pass2": VF_GRAD_FLOPS_PER_TERM,
+                     "lower_bound_basis": "pass 1 only (Sigma recomputed: 36 flops per nonzero "
+                                          "term, sigmoid and alpha per sample); pass 2's "
+                                          f"{VF_GRAD_FLOPS_PER_TERM} flops per term where the "
+                                          "sigmoid has not saturated are not counted",
+                     "executed_frac_ncu": NCU_VF["backward"]["executed_frac"],
+                     "executed_kernel": NCU_VF["backward"]["kernel"]},
+        "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (max SM clock)",
+        "executed_basis": "ncu FFMA + FADD + FMUL thread instructions per cycle of one launch "
+                          f"({NCU_VF['profile']})"}
     # the FP64 oracle on a sample of 2 cells in the middle of the grid (one host core)
     import oracle
     n_cells = d[0] * d[1] * d[2]
@@ -303,7 +359,8 @@ def run_vf(steps, warmup):
     tuning = radius_tuning(lat, cfg, iterations=20)
     return {"workload": cfg["name"], "forward_ms": fwd, "backward_ms": bwd,
             "backward_forward_ratio": bwd / fwd, "samples_per_s_forward": samples / (fwd / 1e3),
-            "samples_per_s_backward": samples / (bwd / 1e3), "radius_tuning": tuning,
+            "samples_per_s_backward": samples / (bwd / 1e3), "roofline": roof,
+            "radius_tuning": tuning,
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "2 cells of the 64^3 grid",
                              "forward_s_per_cell": of / 2, "backward_s_per_cell": ob / 2,
                              "forward_full_grid_s_extrapolated": of / 2 * n_cells,
