@@ -37,8 +37,8 @@ F_PAIR = 36            # FP32 flops of one (pixel, layer, edge) term in the fiel
 # write) per pixel-layer (scaled by pixel-layers to a launch of the timed
 # workload). None where no capture of the current kernel exists.
 NCU_FIELD = {
-    "block": {"kernel": "k_field", "executed_frac": 8422.3 / (152 * 128 * 2),
-              "dram_bytes_per_pixel_layer": 1.2835e9 / (64 * 2000 * 2000),
+    "block": {"kernel": "k_field", "executed_frac": (2 * 2564.8 + 1382.6 + 2056.6) / (152 * 128 * 2),
+              "dram_bytes_per_pixel_layer": (1.212995e9 + 4.259346e9) / (264 * 2000 * 2000),
               "profile": "profiles/k_field_graded-10M.txt"},
     "footprint": {"kernel": "k_field_fp",
                   "executed_frac": (2 * 3131.6 + 1369.7 + 1618.9) / (152 * 128 * 2),
